@@ -1,0 +1,321 @@
+"""Benchmark: BFS GTEPS on R-MAT scale 22 (edge factor 16, seed 2, 16 random
+non-isolated sources), with the HBM roofline fraction of the BFS level loop,
+an end-to-end number through the C ABI with host buffers, and the CPU oracle
+as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gr|reference]
+
+A step is 16 BFS traversals (one per source) with depth and parent outputs.
+TEPS follow the paper's convention (Sec. 6, Table 3): edges of the whole
+graph (directed CSR entries) per traversal time. The L2 cache is flushed by
+writing a 256 MB buffer before every step, outside the timed events.
+Under torchrun (N > 1) every rank runs the same 16 traversals on its own GPU
+(replicas, weak scaling) and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SCALE, EDGE_FACTOR, GRAPH_SEED, SOURCE_SEED, NUM_SOURCES = 22, 16, 2, 2, 16
+WORKLOAD = "rmat22_bfs"
+METRIC = "BFS GTEPS (R-MAT s22, 16 sources)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gr", choices=["gr", "reference"])
+    ap.add_argument("--cpu-sample-sources", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs():
+    import graphgen as gg
+    r, c = gg.rmat(SCALE, EDGE_FACTOR, seed=GRAPH_SEED)
+    srcs = gg.sources(r, NUM_SOURCES, seed=SOURCE_SEED)
+    return r, c, srcs
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bfs_bytes(r, depth_list, m):
+    """Algorithmic bytes of one BFS: each column index of the reached
+    vertices read once (4 B), the row offsets once (4 B each), and a depth
+    and a parent write per reached vertex (8 B)."""
+    out = []
+    deg = np.diff(r).astype(np.int64)
+    n = r.size - 1
+    for d in depth_list:
+        reached = d >= 0
+        m_reached = int(deg[reached].sum())
+        out.append(4 * m_reached + 4 * (n + 1) + 8 * int(reached.sum()))
+    return out
+
+
+def cpu_baseline(r, c, srcs, m, k):
+    import oracle
+    t0 = time.perf_counter()
+    for s in srcs[:k]:
+        oracle.bfs(r, c, int(s))
+    dt = time.perf_counter() - t0
+    return {"value": m * k / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{k} of the {NUM_SOURCES} sources, single-threaded queue BFS, "
+                      f"{dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    r, c, srcs = make_inputs()
+    m = int(c.size)
+    import oracle
+    oracle.bfs(r, c, int(srcs[0]))  # warm the page cache / build
+    per_step = max(1, min(len(srcs), 2))  # bounded sample per step
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; steps below are timed
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for j in range(per_step):
+            oracle.bfs(r, c, int(srcs[(k * per_step + j) % len(srcs)]))
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = m * per_step * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph": f"R-MAT s{SCALE} ef{EDGE_FACTOR} seed {GRAPH_SEED}",
+                       "n": int(r.size - 1), "m": m,
+                       "sources_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} traversals per step"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gr(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1501_05387_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1501_05387_gb300 import gr
+
+    r, c, srcs = make_inputs()
+    n, m = int(r.size - 1), int(c.size)
+    g = gr.gr_graph_create(r, c)
+    dev = torch.device("cuda", local)
+    depth = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
+    parent = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for i, s in enumerate(srcs):
+            if events is not None:
+                events[i][0].record(stream)
+            gr.gr_bfs(g, int(s), depth[i], parent[i])
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    depth_host = [d.cpu().numpy() for d in depth]
+    levels = []
+    for s in srcs:  # levels per traversal (for the launch count)
+        gr.gr_bfs(g, int(s), depth[0], None)
+        levels.append(gr.gr_bfs_stats(g)[0])
+    launches_per_step = sum(1 + 4 * lv for lv in levels)
+
+    clocks = ClockSampler(local)
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+           for _ in srcs] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(ev[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    per_bfs = np.array([[a.elapsed_time(b) for a, b in ev[k]] for k in range(args.steps)])  # ms
+    step_ms = per_bfs.sum(axis=1)
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * m * len(srcs) * args.steps / total_s / 1e9
+
+    # roofline of the BFS level loop (one gr_bfs call = one launch of the
+    # device-side while-loop graph)
+    bytes_per_bfs = bfs_bytes(r, depth_host, m)
+    mean_bfs_s = float(per_bfs.mean()) / 1e3
+    achieved = float(np.mean(bytes_per_bfs)) / mean_bfs_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "kernel": "gr_bfs level loop (CUDA graph)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "frac_of_nominal_8TBs": achieved / 8000.0,
+                "algorithmic_bytes_per_launch": float(np.mean(bytes_per_bfs)),
+                "traffic": None}
+
+    # end to end: the same traversals through the C ABI with host outputs
+    hd = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
+    hp = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
+    for i, s in enumerate(srcs):
+        gr.gr_bfs(g, int(s), hd[i], hp[i])
+    torch.cuda.synchronize()
+    e2e_times = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, s in enumerate(srcs):
+            gr.gr_bfs(g, int(s), hd[i], hp[i])
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": world * m * len(srcs) * args.steps / e2e_total / 1e9, "unit": "GTEPS",
+           "h2d_bytes_per_step": 4 * len(srcs),
+           "d2h_bytes_per_step": 2 * 4 * n * len(srcs)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(r, c, srcs, m, args.cpu_sample_sources)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup),
+                "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD,
+                           "graph": f"R-MAT s{SCALE} ef{EDGE_FACTOR} (a,b,c)=(0.57,0.19,0.19) seed {GRAPH_SEED}",
+                           "n": n, "m": m, "sources": [int(s) for s in srcs],
+                           "outputs": "depth+parent int32",
+                           "l2": "256 MB flush before each step (outside the events)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+                "bfs_ms": {"mean": float(per_bfs.mean()), "p50": float(np.median(per_bfs)),
+                           "p99": float(np.percentile(per_bfs, 99)),
+                           "min": float(per_bfs.min()), "max": float(per_bfs.max())},
+                "levels": levels, "wall_s_timed_loop": wall}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gr(args)
+
+
+if __name__ == "__main__":
+    main()

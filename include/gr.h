@@ -1,0 +1,130 @@
+/*
+ * gr — frontier-operator graph primitives for one GB300 (sm_103a).
+ *
+ * A C ABI over hand-written CUDA kernels implementing the data-centric
+ * frontier model of Wang et al., "Gunrock: A High-Performance Graph
+ * Processing Library on the GPU" (PPoPP'16): the advance, filter and
+ * direction-optimising pull operators (Sec. 4.1, 4.4, 4.5) and the five
+ * primitives built on them (Sec. 5): BFS, SSSP, BC, CC and PageRank.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Graph: CSR as in Sec. 3 — row offsets R (int32, n+1 entries, R[0] = 0,
+ *   non-decreasing, R[n] = m) and column indices C (int32, m entries, each
+ *   in [0, n)), optional per-edge weights W (uint32, m entries). Undirected
+ *   graphs are given symmetrised (both (u,v) and (v,u) stored), as the paper
+ *   converts all its datasets (Sec. 6). Self-loops and duplicate entries are
+ *   accepted. m must not exceed INT32_MAX.
+ * Output pointers: device memory or page-locked host memory of the stated
+ *   length, owned by the caller. Host outputs are filled by a copy at the
+ *   end of the call's work on `stream`; device outputs are written in stream
+ *   order. A call returns once its work is enqueued, except where a
+ *   "(host)" scalar output forces a stream synchronisation.
+ * stream: a cudaStream_t passed as void*; NULL is the legacy default stream.
+ * Concurrency: calls on one gr_graph share its scratch memory; the library
+ *   orders them on the device (a later call on another stream waits for the
+ *   earlier one). Independent concurrent queries go through gr_server.
+ * Errors: every call returns a gr_status; nothing is thrown across the ABI.
+ *   GR_EINVAL for bad arguments (checked before any device work),
+ *   GR_ENOMEM when device allocation fails, GR_ECUDA for other CUDA errors,
+ *   GR_ETIMEOUT when a bounded device-side wait gave up (the graph stays
+ *   usable). gr_last_error() returns this thread's last message.
+ */
+#ifndef GR_H
+#define GR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gr_status {
+  GR_OK = 0,
+  GR_EINVAL = 1,
+  GR_ENOMEM = 2,
+  GR_ECUDA = 3,
+  GR_ETIMEOUT = 4,
+  GR_EBUSY = 5
+} gr_status;
+
+/* Opaque graph handle: owns device copies of R, C, W, derived per-graph data
+ * (degree statistics, isolated-vertex bitmap, symmetry flag) and scratch. */
+typedef struct gr_graph gr_graph;
+
+/* Traversal direction policy (Sec. 4.5 "Push vs. pull traversal"). */
+enum {
+  GR_DIR_AUTO = 0, /* tuned push<->pull switching (needs a symmetric graph) */
+  GR_DIR_PUSH = 1, /* push (top-down) advance on every level */
+  GR_DIR_PULL = 2  /* push on the source's level, pull on every later level */
+};
+
+/* Level-loop driver. */
+enum {
+  GR_MODE_AUTO = 0,       /* chosen by the tuner from the graph's shape */
+  GR_MODE_LAUNCH = 1,     /* host enqueues batches of level kernels that
+                             exit early once the traversal is done */
+  GR_MODE_GRAPH = 2,      /* one CUDA graph whose device-side while loop
+                             runs one level per iteration */
+  GR_MODE_PERSISTENT = 3  /* one cooperative kernel runs every level with a
+                             bounded-spin grid barrier (push only) */
+};
+
+/* Options; pass NULL for tuned defaults. Zero in a field means "tuned". */
+typedef struct gr_opts {
+  int32_t direction;  /* GR_DIR_* */
+  int32_t mode;       /* GR_MODE_* */
+  int32_t block;      /* threads per block of the advance kernels (0: tuned) */
+  int32_t chunk;      /* merge-path items per block chunk (0: tuned) */
+  float alpha;        /* push->pull when frontier edges > unexplored/alpha */
+  float beta;         /* pull->push when frontier vertices < n/beta */
+  uint32_t delta;     /* SSSP near/far bucket width (0: tuned,
+                         UINT32_MAX: no split, one bucket) */
+  int32_t max_iters;  /* cap on device-side iterations (0: default) */
+} gr_opts;
+
+/* Create a graph from a CSR (Sec. 3; Alg. 1 operates on such a graph).
+ * n >= 1 vertices, m >= 0 entries. row_off[n+1], col[m] and, if not NULL,
+ * w[m] are host pointers when inputs_on_device == 0 and device pointers
+ * otherwise; they are validated, copied and not retained. On success *out
+ * holds a new handle to release with gr_graph_destroy. */
+gr_status gr_graph_create(int32_t n, int64_t m, const int32_t *row_off,
+                          const int32_t *col, const uint32_t *w,
+                          int inputs_on_device, void *stream, gr_graph **out);
+
+/* Release a graph and all device memory it owns (synchronises its work). */
+gr_status gr_graph_destroy(gr_graph *g);
+
+/* Per-graph statistics computed at creation (host scalars; any may be NULL):
+ * vertex count, entry count, maximum degree, number of degree-0 vertices,
+ * whether the CSR is symmetric (every (u,v) has a (v,u)), and whether
+ * weights are present. */
+gr_status gr_graph_info(const gr_graph *g, int32_t *n, int64_t *m,
+                        int32_t *max_degree, int32_t *num_isolated,
+                        int32_t *symmetric, int32_t *has_weights);
+
+/* Breadth-first search from src (Sec. 5.1): depth[n] (int32) receives the
+ * hop count from src, -1 where unreached; parent[n] (int32, may be NULL)
+ * receives a valid BFS parent of each reached vertex (parent[src] = src),
+ * -1 where unreached. Depth is unique; the parent is any vertex one level up
+ * that has an edge to the child. Push levels run the load-balanced advance
+ * (Sec. 4.4) fused with the visited-bitmap filter (Sec. 4.1, 4.5
+ * "Idempotent vs. non-idempotent"); pull levels run the bitmap pull advance
+ * (Sec. 4.5). */
+gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
+                 const gr_opts *opts, void *stream);
+
+/* Number of levels (including the source's) and of pull levels of the last
+ * completed gr_bfs on this graph (host scalars; synchronises). */
+gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels);
+
+/* This thread's last error message ("" if none). The pointer stays valid
+ * until this thread's next gr_* call. */
+const char *gr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GR_H */

@@ -1,0 +1,182 @@
+// Internal definitions shared by the library's translation units: the graph
+// object, error reporting, scratch buffers and warp/block primitives.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gr.h"
+
+namespace gr {
+
+// ------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+void clear_error();
+gr_status fail(gr_status st, const std::string &msg);
+gr_status cuda_fail(cudaError_t e, const char *what);
+
+#define GR_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ::gr::cuda_fail(e_, #call); \
+  } while (0)
+
+#define GR_TRY(expr)                        \
+  do {                                      \
+    gr_status s_ = (expr);                  \
+    if (s_ != GR_OK) return s_;             \
+  } while (0)
+
+// Device-side error codes written into control blocks.
+enum : int32_t { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2 };
+
+// Iteration limit of every device-side spin wait; after it the waiting
+// thread records kDevTimeout and leaves the wait.
+constexpr int64_t kSpinLimit = 1ll << 24;
+
+// ------------------------------------------------------------ buffers
+// Owning device allocation (cudaMalloc/cudaFree), move-only.
+struct DevMem {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem &) = delete;
+  DevMem &operator=(const DevMem &) = delete;
+  ~DevMem() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  gr_status alloc(size_t nbytes, const char *what);
+  template <class T>
+  T *as() const { return (T *)p; }
+};
+
+struct PinnedMem {
+  void *p = nullptr;
+  ~PinnedMem() {
+    if (p) cudaFreeHost(p);
+  }
+  gr_status alloc(size_t nbytes, const char *what);
+  template <class T>
+  T *as() const { return (T *)p; }
+};
+
+struct BfsWorkspace;
+struct SsspWorkspace;
+struct CcWorkspace;
+struct PrWorkspace;
+struct BatchWorkspace;
+
+}  // namespace gr
+
+// The opaque handle of the C ABI.
+struct gr_graph {
+  int device = 0;
+  int num_sms = 0;
+  int32_t n = 0;
+  int64_t m = 0;
+  int32_t nwords = 0;  // ceil(n / 32): words of one vertex bitmap
+  gr::DevMem row_off, col, w;
+  gr::DevMem isolated_bits;  // bit v set iff deg(v) == 0
+  gr::DevMem degree;         // int32 deg(v), used by PageRank
+  int32_t max_degree = 0;
+  int32_t num_isolated = 0;
+  bool symmetric = false;
+  bool rows_sorted = false;
+  bool has_weights = false;
+
+  std::mutex mu;  // serialises host-side enqueueing on this graph
+  cudaEvent_t last_done = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool has_last = false;
+
+  // lazily created scratch, one per primitive (freed by destroy_workspaces)
+  gr::BfsWorkspace *bfs = nullptr;
+  gr::SsspWorkspace *sssp = nullptr;
+  gr::CcWorkspace *cc = nullptr;
+  gr::PrWorkspace *pr = nullptr;
+  gr::BatchWorkspace *batch = nullptr;
+
+  gr::DevMem stage[2];  // device staging for host output pointers
+
+  ~gr_graph();
+};
+
+namespace gr {
+
+// Begin/end of a call that uses the graph's scratch on `s`: orders the call
+// after the previous call on the graph when that ran on another stream.
+gr_status begin_call(gr_graph *g, cudaStream_t s);
+gr_status end_call(gr_graph *g, cudaStream_t s);
+
+// Output pointer handling: returns a device pointer to write to. If `user`
+// is host memory, a staging buffer of `bytes` is used and *needs_copy set.
+gr_status resolve_output(gr_graph *g, int slot, void *user, size_t bytes,
+                         void **dev, bool *needs_copy);
+
+const gr_opts &default_opts();
+
+// Per-primitive scratch release, defined next to each primitive.
+void free_bfs(BfsWorkspace *);
+
+// ------------------------------------------------------ device helpers
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <class T>
+__device__ __forceinline__ T warp_incl_sum(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane_id() >= o) v += t;
+  }
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide exclusive sum; `smem` holds >= 33 elements. Returns the
+// exclusive prefix of this thread and writes the block total to *total.
+template <class T>
+__device__ __forceinline__ T block_excl_sum(T v, T *smem, T *total) {
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  T incl = warp_incl_sum(v);
+  if (lane == 31) smem[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    T x = lane < nw ? smem[lane] : T(0);
+    T xi = warp_incl_sum(x);
+    if (lane < nw) smem[lane] = xi - x;
+    if (lane == nw - 1) smem[32] = xi;
+  }
+  __syncthreads();
+  T res = smem[wid] + incl - v;
+  *total = smem[32];
+  __syncthreads();
+  return res;
+}
+
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *smem) {
+  T total;
+  block_excl_sum(v, smem, &total);
+  return total;
+}
+
+__device__ __forceinline__ bool test_bit(const uint32_t *bits, int32_t v) {
+  return (bits[v >> 5] >> (v & 31)) & 1u;
+}
+
+}  // namespace gr

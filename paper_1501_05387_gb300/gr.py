@@ -1,0 +1,192 @@
+"""Python binding of libgr.so, the C ABI declared in include/gr.h.
+
+Argument marshalling only: every step of every primitive runs in the CUDA
+library. Functions keep the C names; tensors (torch, CUDA or pinned host) or
+numpy arrays are passed as raw pointers together with the current torch
+stream. A missing libgr.so raises ImportError: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is not built; run paper_1501_05387_gb300.build.build() "
+        "(or __graft_entry__.build()) first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+GR_OK, GR_EINVAL, GR_ENOMEM, GR_ECUDA, GR_ETIMEOUT, GR_EBUSY = range(6)
+STATUS_NAMES = {0: "GR_OK", 1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA",
+                4: "GR_ETIMEOUT", 5: "GR_EBUSY"}
+GR_DIR_AUTO, GR_DIR_PUSH, GR_DIR_PULL = 0, 1, 2
+GR_MODE_AUTO, GR_MODE_LAUNCH, GR_MODE_GRAPH, GR_MODE_PERSISTENT = 0, 1, 2, 3
+
+
+class gr_opts(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("delta", ctypes.c_uint32), ("max_iters", ctypes.c_int32)]
+
+
+class GrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.gr_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+_P = ctypes.POINTER
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("gr_last_error", [], ctypes.c_char_p)
+_sig("gr_graph_create", [_i32, _i64, _vp, _vp, _vp, ctypes.c_int, _vp, _P(_vp)])
+_sig("gr_graph_destroy", [_vp])
+_sig("gr_graph_info", [_vp, _P(_i32), _P(_i64), _P(_i32), _P(_i32), _P(_i32), _P(_i32)])
+_sig("gr_bfs", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
+_sig("gr_bfs_stats", [_vp, _P(_i32), _P(_i32)])
+
+
+def _check(status: int, where: str):
+    if status != GR_OK:
+        raise GrError(status, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=None):
+    """Raw pointer of a contiguous torch tensor or numpy array (or None)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {x.dtype}")
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _on_device(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, gr_opts):
+        return ctypes.byref(opts)
+    o = gr_opts()
+    for k, v in dict(opts).items():
+        setattr(o, k, v)
+    return ctypes.byref(o)
+
+
+class Graph:
+    """Owning wrapper of a gr_graph handle."""
+
+    def __init__(self, handle: int, n: int, m: int):
+        self.handle = handle
+        self.n = n
+        self.m = m
+
+    def close(self):
+        if self.handle:
+            _lib.gr_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def gr_graph_create(row_off, col, w=None, stream=None) -> Graph:
+    """Create a graph from a CSR held in numpy arrays (host) or torch tensors
+    (all on the device or all on the host)."""
+    n = int(row_off.shape[0]) - 1
+    m = int(col.shape[0])
+    dev = _on_device(row_off)
+    if dev != _on_device(col) or (w is not None and dev != _on_device(w)):
+        raise ValueError("row_off, col and w must all be on the host or all on the device")
+    out = _vp()
+    st = _lib.gr_graph_create(n, m, _ptr(row_off, np.int32), _ptr(col, np.int32),
+                              _ptr(w, np.uint32), int(dev), _stream(stream),
+                              ctypes.byref(out))
+    _check(st, "gr_graph_create")
+    return Graph(out.value, n, m)
+
+
+def gr_graph_destroy(g: Graph):
+    g.close()
+
+
+def gr_graph_info(g: Graph) -> dict:
+    n, mx, iso, sym, hw = _i32(), _i32(), _i32(), _i32(), _i32()
+    m = _i64()
+    _check(_lib.gr_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(mx),
+                              ctypes.byref(iso), ctypes.byref(sym), ctypes.byref(hw)),
+           "gr_graph_info")
+    return {"n": n.value, "m": m.value, "max_degree": mx.value,
+            "num_isolated": iso.value, "symmetric": bool(sym.value),
+            "has_weights": bool(hw.value)}
+
+
+def gr_bfs(g: Graph, src: int, depth, parent=None, opts=None, stream=None):
+    """BFS from src into depth[n] (and parent[n] if given), int32."""
+    _check(_lib.gr_bfs(g.handle, int(src), _ptr(depth, np.int32), _ptr(parent, np.int32),
+                       _opts(opts), _stream(stream)), "gr_bfs")
+
+
+def gr_bfs_stats(g: Graph):
+    lv, pl = _i32(), _i32()
+    _check(_lib.gr_bfs_stats(g.handle, ctypes.byref(lv), ctypes.byref(pl)), "gr_bfs_stats")
+    return lv.value, pl.value
+
+
+def gr_last_error() -> str:
+    return _lib.gr_last_error().decode(errors="replace")

@@ -32,8 +32,9 @@ def edge_sources(row_off: np.ndarray) -> np.ndarray:
     return np.repeat(np.arange(n, dtype=np.int32), np.diff(row_off))
 
 
-def validate_bfs(row_off, col, src, depth, parent, symmetric=True, keys=None):
-    """Raise AssertionError unless (depth, parent) is a valid BFS tree."""
+def validate_bfs(row_off, col, src, depth, parent, symmetric=True, keys=None, su=None):
+    """Raise AssertionError unless (depth, parent) is a valid BFS tree.
+    keys / su: precomputed edge_keys / edge_sources for large graphs."""
     n = row_off.shape[0] - 1
     depth = np.asarray(depth)
     parent = np.asarray(parent)
@@ -52,7 +53,8 @@ def validate_bfs(row_off, col, src, depth, parent, symmetric=True, keys=None):
     if vs.size:
         assert np.all(has_edges(keys, n, p, vs)), "(parent, v) is not an edge"
     # every edge spans at most one level and never leaves the reached set
-    su = edge_sources(row_off)
+    if su is None:
+        su = edge_sources(row_off)
     du = depth[su]
     dv = depth[col]
     both = (du >= 0) & (dv >= 0)

@@ -21,5 +21,5 @@ def cuda_lib():
         pytest.fail("GPU test collected on a machine without CUDA")
     from paper_1501_05387_gb300 import build as grbuild
     grbuild.build()
-    import paper_1501_05387_gb300 as gr
+    from paper_1501_05387_gb300 import gr
     return gr
