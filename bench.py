@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--impl", default="gr", choices=["gr", "reference"])
     ap.add_argument("--cpu-sample-sources", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scale", type=int, default=SCALE,
+                    help="R-MAT scale (profiling runs only; the metric is quoted at 22)")
+    ap.add_argument("--mode", default="auto", choices=["auto", "graph", "launch"],
+                    help="BFS level-loop driver (profiling runs: 'launch' exposes "
+                         "every kernel to ncu)")
     return ap.parse_args()
 
 
@@ -52,9 +58,9 @@ def dist_env():
     return rank, world, local
 
 
-def make_inputs():
+def make_inputs(scale=SCALE):
     import graphgen as gg
-    r, c = gg.rmat(SCALE, EDGE_FACTOR, seed=GRAPH_SEED)
+    r, c = gg.rmat(scale, EDGE_FACTOR, seed=GRAPH_SEED)
     srcs = gg.sources(r, NUM_SOURCES, seed=SOURCE_SEED)
     return r, c, srcs
 
@@ -147,8 +153,8 @@ def run_reference(args):
     import oracle
     oracle.bfs(r, c, int(srcs[0]))  # warm the page cache / build
     per_step = max(1, min(len(srcs), 2))  # bounded sample per step
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; steps below are timed
+    for k in range(args.warmup):  # untimed
+        oracle.bfs(r, c, int(srcs[k % len(srcs)]))
     times = []
     for k in range(args.steps):
         t0 = time.perf_counter()
@@ -185,9 +191,12 @@ def run_gr(args):
         torch.distributed.barrier()
     from paper_1501_05387_gb300 import gr
 
-    r, c, srcs = make_inputs()
+    r, c, srcs = make_inputs(args.scale)
     n, m = int(r.size - 1), int(c.size)
     g = gr.gr_graph_create(r, c)
+    mode = {"auto": gr.GR_MODE_AUTO, "graph": gr.GR_MODE_GRAPH,
+            "launch": gr.GR_MODE_LAUNCH}[args.mode]
+    bfs_opts = gr.gr_opts(mode=mode)
     dev = torch.device("cuda", local)
     depth = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
     parent = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
@@ -198,7 +207,7 @@ def run_gr(args):
         for i, s in enumerate(srcs):
             if events is not None:
                 events[i][0].record(stream)
-            gr.gr_bfs(g, int(s), depth[i], parent[i])
+            gr.gr_bfs(g, int(s), depth[i], parent[i], bfs_opts)
             if events is not None:
                 events[i][1].record(stream)
 
@@ -209,7 +218,7 @@ def run_gr(args):
     depth_host = [d.cpu().numpy() for d in depth]
     levels = []
     for s in srcs:  # levels per traversal (for the launch count)
-        gr.gr_bfs(g, int(s), depth[0], None)
+        gr.gr_bfs(g, int(s), depth[0], None, bfs_opts)
         levels.append(gr.gr_bfs_stats(g)[0])
     launches_per_step = sum(1 + 4 * lv for lv in levels)
 
@@ -258,20 +267,22 @@ def run_gr(args):
                 "traffic": None}
 
     # end to end: the same traversals through the C ABI with host outputs
-    hd = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
-    hp = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
-    for i, s in enumerate(srcs):
-        gr.gr_bfs(g, int(s), hd[i], hp[i])
-    torch.cuda.synchronize()
-    e2e_times = []
-    for k in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e_times = [float("nan")]
+    if not args.no_e2e:
+        hd = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
+        hp = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
         for i, s in enumerate(srcs):
-            gr.gr_bfs(g, int(s), hd[i], hp[i])
+            gr.gr_bfs(g, int(s), hd[i], hp[i], bfs_opts)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        e2e_times = []
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i, s in enumerate(srcs):
+                gr.gr_bfs(g, int(s), hd[i], hp[i], bfs_opts)
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_times)
     if world > 1:
         t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
@@ -291,8 +302,9 @@ def run_gr(args):
                 "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD,
-                           "graph": f"R-MAT s{SCALE} ef{EDGE_FACTOR} (a,b,c)=(0.57,0.19,0.19) seed {GRAPH_SEED}",
+                "config": {"workload": WORKLOAD if args.scale == SCALE else f"rmat{args.scale}_bfs",
+                           "graph": f"R-MAT s{args.scale} ef{EDGE_FACTOR} (a,b,c)=(0.57,0.19,0.19) seed {GRAPH_SEED}",
+                           "mode": args.mode,
                            "n": n, "m": m, "sources": [int(s) for s in srcs],
                            "outputs": "depth+parent int32",
                            "l2": "256 MB flush before each step (outside the events)",

@@ -119,6 +119,48 @@ gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
  * completed gr_bfs on this graph (host scalars; synchronises). */
 gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels);
 
+/* Single-source shortest paths from src over non-negative integer weights
+ * (Alg. 1; Sec. 4.5 "Priority Queue"; Sec. 5.2). Requires weights.
+ * dist[n] (uint32) receives the shortest distance, 0xFFFFFFFF where
+ * unreachable (sums that do not fit below 0xFFFFFFFF count as unreachable);
+ * pred[n] (int32, may be NULL) receives, for each reached v != src, the
+ * smallest u with an edge (u, v) and dist[u] + w(u, v) = dist[v];
+ * pred[src] = src; -1 where unreachable (with zero-weight edges pred may
+ * contain cycles among equal-distance vertices). opts->delta sets the
+ * near/far bucket width (0: tuned, UINT32_MAX: a single bucket); the
+ * distances do not depend on it. */
+gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
+                  const gr_opts *opts, void *stream);
+
+/* Statistics of the last completed gr_sssp on this graph (host scalars;
+ * synchronises): device-loop iterations, near/far phases (splits) and
+ * edges expanded. Returns GR_ETIMEOUT if that run hit its iteration cap
+ * (opts->max_iters) or a device-side wait limit. */
+gr_status gr_sssp_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
+                        int64_t *relaxations);
+
+/* Connected components (Sec. 5.4): label[n] (int32) receives, for every
+ * vertex, the smallest vertex id of its component (weakly connected
+ * components for a directed CSR). *num_components (host, may be NULL)
+ * receives the number of components; asking for it synchronises. Hooking
+ * links the larger root under the smaller over the edge frontier, pointer
+ * jumping then points every vertex at its root. opts is unused. */
+gr_status gr_cc(gr_graph *g, int32_t *label, int32_t *num_components,
+                const gr_opts *opts, void *stream);
+
+/* PageRank (Sec. 5.5), pull form, FP32 ranks with FP64 reductions:
+ * r'[v] = (1 - damping)/n + damping * (sum over edges (u, v) of
+ * r[u]/deg(u) + D/n), D = sum of r[u] over vertices of out-degree 0,
+ * starting from r = 1/n. Stops after max_iter iterations or once
+ * sum |r' - r| < tol. rank[n] (float) receives the ranks; *iters (host, may
+ * be NULL) the iterations run (asking for it synchronises). damping must lie
+ * in (0, 1), max_iter >= 0, tol >= 0. A directed CSR is transposed once on
+ * the device for the in-neighbour gather. opts->mode GR_MODE_LAUNCH runs
+ * host-driven batches instead of the device-side loop. */
+gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
+                      float *rank, int32_t *iters, const gr_opts *opts,
+                      void *stream);
+
 /* This thread's last error message ("" if none). The pointer stays valid
  * until this thread's next gr_* call. */
 const char *gr_last_error(void);

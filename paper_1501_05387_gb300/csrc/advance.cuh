@@ -1,0 +1,300 @@
+// Generic frontier operators shared by the primitives.
+//
+// The paper's advance step (Sec. 4.1) expands a vertex frontier into the
+// neighbours of its vertices; its load-balanced form (Sec. 4.4) first scans
+// the frontier's degrees ("scanned edge offset queue") and then hands every
+// block an equal share of work, finding each edge's owner by a sorted
+// search. Per-edge work is a functor inlined into the kernel, the paper's
+// kernel fusion of compute into advance/filter (Sec. 4.3).
+//
+// Here the equal shares are merge-path chunks: the frontier's vertex ends
+// and its edge ranks form one merged sequence, and each chunk takes a fixed
+// number of its items, so a chunk never holds more vertices or more edges
+// than its size whatever the degree mix (zero-degree vertices included).
+#pragma once
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+// ------------------------------------------------------------------ scan
+// Decoupled look-back status word of a scan tile:
+// [63:34] epoch tag, [33:32] flag (1 aggregate, 2 inclusive prefix),
+// [31:0] value. The epoch changes on every scan, so the status array never
+// needs clearing.
+constexpr unsigned long long kScanFlagAgg = 1ull, kScanFlagPrefix = 2ull;
+
+struct ScanState {
+  unsigned long long *status;  // one word per tile
+  int32_t *tile_ctr;           // dynamic tile counter, zero before the scan
+  int32_t *error;              // set to kDevTimeout if a look-back gives up
+  uint32_t epoch;
+};
+
+__device__ __forceinline__ void scan_publish(unsigned long long *st, int32_t tile,
+                                             uint32_t epoch, unsigned long long flag,
+                                             uint32_t val) {
+  unsigned long long w =
+      ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | (flag << 32) | val;
+  atomicExch(st + tile, w);
+}
+
+__device__ __forceinline__ uint32_t scan_look_back(const ScanState &s, int32_t tile) {
+  uint32_t excl = 0;
+  int32_t j = tile - 1;
+  int64_t spins = 0;
+  const unsigned long long tag = s.epoch & 0x3FFFFFFFu;
+  while (j >= 0) {
+    unsigned long long w = *(volatile unsigned long long *)(s.status + j);
+    unsigned long long flag = (w >> 32) & 3ull;
+    if ((w >> 34) != tag || flag == 0) {
+      if (++spins > kSpinLimit) {
+        atomicExch(s.error, kDevTimeout);
+        return excl;
+      }
+      continue;
+    }
+    excl += (uint32_t)w;
+    if (flag == kScanFlagPrefix) break;
+    --j;
+  }
+  return excl;
+}
+
+// Exclusive scan of deg(Q[i]) into S[0..q], S[q] = total, by every block of
+// the grid (tiles taken in order from a counter; blocks wait only on earlier
+// tiles, which are held by running blocks). Returns true, on thread 0 of the
+// block that scanned the last tile, with *total set.
+template <int THREADS, int ITEMS>
+__device__ bool frontier_degree_scan(const int32_t *R, const int32_t *Q, int32_t q,
+                                     int32_t *S, const ScanState &st, long long *total) {
+  constexpr int TILE = THREADS * ITEMS;
+  const int32_t ntiles = (q + TILE - 1) / TILE;
+  __shared__ int32_t s_tile;
+  __shared__ uint32_t s_excl;
+  __shared__ uint32_t s_red[33];
+  bool last = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(st.tile_ctr, 1);
+    __syncthreads();
+    const int32_t tile = s_tile;
+    __syncthreads();
+    if (tile >= ntiles) break;
+    const int64_t base = (int64_t)tile * TILE + threadIdx.x * ITEMS;
+    uint32_t deg[ITEMS];
+    uint32_t local = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t i = base + k;
+      uint32_t d = 0;
+      if (i < q) {
+        const int32_t u = Q[i];
+        d = (uint32_t)(R[u + 1] - R[u]);
+      }
+      deg[k] = d;
+      local += d;
+    }
+    uint32_t agg;
+    const uint32_t texcl = block_excl_sum(local, s_red, &agg);
+    if (threadIdx.x == 0) {
+      uint32_t excl = 0;
+      if (tile == 0) {
+        scan_publish(st.status, tile, st.epoch, kScanFlagPrefix, agg);
+      } else {
+        scan_publish(st.status, tile, st.epoch, kScanFlagAgg, agg);
+        excl = scan_look_back(st, tile);
+        scan_publish(st.status, tile, st.epoch, kScanFlagPrefix, excl + agg);
+      }
+      s_excl = excl;
+    }
+    __syncthreads();
+    uint32_t run = s_excl + texcl;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t i = base + k;
+      if (i < q) S[i] = (int32_t)run;
+      run += deg[k];
+    }
+    if (tile == ntiles - 1 && threadIdx.x == 0) {
+      *total = (long long)s_excl + agg;
+      S[q] = (int32_t)*total;
+      last = true;
+    }
+    __syncthreads();
+  }
+  return last;
+}
+
+// ------------------------------------------------------------- advance
+// Number of frontier positions i in [0, q) whose merge-path end marker (at
+// merged position S[i+1] + i) lies before diagonal d.
+__device__ __forceinline__ int32_t merge_count(const int32_t *S, int32_t q, long long d) {
+  int32_t lo = 0, hi = q;
+  while (lo < hi) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    if ((long long)S[mid + 1] + mid < d) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Append `v` to one of two block-local output buffers selected per thread
+// (code 1 -> buffer 0, code 2 -> buffer 1), warp-aggregated.
+__device__ __forceinline__ void warp_append(int code, int32_t v, int32_t *buf0,
+                                            int32_t *cnt0, int32_t *buf1, int32_t *cnt1) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t b0 = __ballot_sync(0xffffffffu, code == 1);
+  const uint32_t b1 = __ballot_sync(0xffffffffu, code == 2);
+  if (b0) {
+    const int leader = __ffs(b0) - 1;
+    int32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(cnt0, __popc(b0));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (code == 1) buf0[pos + __popc(b0 & lt)] = v;
+  }
+  if (b1) {
+    const int leader = __ffs(b1) - 1;
+    int32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(cnt1, __popc(b1));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (code == 2) buf1[pos + __popc(b1 & lt)] = v;
+  }
+}
+
+// Load-balanced advance over frontier Q[0..q) with scanned degrees S[0..q].
+// For every edge e = (u, v) of a frontier vertex, f(u, v, e) runs once and
+// returns 0 (drop), 1 (append v to out0) or 2 (append v to out1, only when
+// NOUT == 2). Column loads are coalesced: consecutive threads take
+// consecutive edge ranks. Outputs are compacted per chunk in shared memory
+// and appended to the global queues with one atomic per chunk and queue.
+// Q == nullptr means the all-vertex frontier (Q[i] = i, S = R, q = n).
+template <int THREADS, int ITEMS, int NOUT, class F>
+__device__ void lb_advance(const int32_t *R, const int32_t *C, const int32_t *Q, int32_t q,
+                           const int32_t *S, F &f, int32_t *out0, int32_t *len0,
+                           int32_t *out1, int32_t *len1) {
+  constexpr int CHUNK = THREADS * ITEMS;
+  const long long total = (long long)q + S[q];
+  const long long nchunks = (total + CHUNK - 1) / CHUNK;
+  __shared__ int32_t s_off[CHUNK + 1];
+  __shared__ int32_t s_u[CHUNK + 1];
+  __shared__ int32_t s_row[CHUNK + 1];
+  __shared__ int32_t s_out0[CHUNK];
+  __shared__ int32_t s_out1[NOUT == 2 ? CHUNK : 1];
+  __shared__ int32_t s_i[2];
+  __shared__ int32_t s_cnt[2], s_base[2];
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * CHUNK;
+    const long long d1 = min(d0 + CHUNK, total);
+    if (threadIdx.x < 2) {
+      s_i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
+      s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int32_t i0 = s_i[0], i1 = s_i[1];
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += THREADS) {
+      const int32_t i = i0 + k;
+      const int32_t u = Q ? Q[i] : i;
+      s_off[k] = S[i];
+      s_u[k] = u;
+      s_row[k] = Q ? R[u] : S[i];
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += THREADS) {
+      const int32_t k = kb + threadIdx.x;
+      int code = 0;
+      int32_t v = 0;
+      if (k < ne) {
+        const int32_t er = (int32_t)(j0 + k);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= er) lo = mid;
+          else hi = mid - 1;
+        }
+        const int32_t e = s_row[lo] + (er - s_off[lo]);
+        v = C[e];
+        code = f(s_u[lo], v, e);
+        if (NOUT == 1 && code == 2) code = 0;
+      }
+      warp_append(code, v, s_out0, &s_cnt[0], s_out1, &s_cnt[1]);
+    }
+    __syncthreads();
+    if (threadIdx.x < NOUT) {
+      const int32_t cnt = s_cnt[threadIdx.x];
+      s_base[threadIdx.x] = cnt ? atomicAdd(threadIdx.x ? len1 : len0, cnt) : 0;
+    }
+    __syncthreads();
+    for (int32_t k = threadIdx.x; k < s_cnt[0]; k += THREADS) out0[s_base[0] + k] = s_out0[k];
+    if (NOUT == 2)
+      for (int32_t k = threadIdx.x; k < s_cnt[1]; k += THREADS) out1[s_base[1] + k] = s_out1[k];
+    __syncthreads();
+  }
+}
+
+}  // namespace gr
+
+namespace gr {
+
+// --------------------------------------------------- neighbourhood reduce
+// Gather-reduce over the neighbourhoods of all vertices (the operator the
+// paper proposes in Sec. 7 for reductions over neighbour lists):
+// acc[v] += sum over edges e = (v, u) of g(u, e), for every v, with the same
+// merge-path chunking as lb_advance over the all-vertex frontier (S = R).
+// Consecutive lanes hold consecutive edge ranks, so the owners within a warp
+// are sorted; a segmented warp sum leaves one total per owner run, added
+// with one atomicAdd. acc must be zero (or hold a partial sum) beforehand.
+template <int THREADS, int ITEMS, class T, class G>
+__device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n, G &g,
+                                   T *acc) {
+  constexpr int CHUNK = THREADS * ITEMS;
+  const long long total = (long long)n + R[n];
+  const long long nchunks = (total + CHUNK - 1) / CHUNK;
+  __shared__ int32_t s_off[CHUNK + 1];
+  __shared__ int32_t s_i[2];
+  const int lane = threadIdx.x & 31;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * CHUNK;
+    const long long d1 = min(d0 + CHUNK, total);
+    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(R, n, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const int32_t i0 = s_i[0], i1 = s_i[1];
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= n - 1) ? (min(i1, n - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += THREADS) s_off[k] = R[i0 + k];
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += THREADS) {
+      const int32_t k = kb + threadIdx.x;
+      int32_t owner = -1;
+      T val = T(0);
+      if (k < ne) {
+        const int32_t e = (int32_t)(j0 + k);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        owner = i0 + lo;
+        val = g(C[e], e);
+      }
+      // segmented suffix sum over runs of equal owners
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T vo = __shfl_down_sync(0xffffffffu, val, o);
+        const int32_t oo = __shfl_down_sync(0xffffffffu, owner, o);
+        if (lane + o < 32 && oo == owner) val += vo;
+      }
+      const int32_t prev = __shfl_up_sync(0xffffffffu, owner, 1);
+      const bool head = owner >= 0 && (lane == 0 || prev != owner);
+      if (head) atomicAdd(acc + owner, val);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gr

@@ -35,7 +35,7 @@
 #include <algorithm>
 #include <cstring>
 
-#include "gr_internal.cuh"
+#include "advance.cuh"
 
 namespace gr {
 
@@ -91,7 +91,6 @@ constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kPushThreads = 256;
 constexpr int kPushItems = 8;
-constexpr int kPushChunk = kPushThreads * kPushItems;  // merge items per chunk
 constexpr int kPullThreads = 256;
 constexpr int kPullFlushRounds = 8;
 
@@ -165,202 +164,57 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
   }
 }
 
-// status word of a scan tile: [63:34] epoch, [33:32] flag, [31:0] value
-constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull;
-
-__device__ __forceinline__ void publish(unsigned long long *st, int32_t tile, uint32_t epoch,
-                                        unsigned long long flag, uint32_t val) {
-  unsigned long long w = ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | (flag << 32) | val;
-  atomicExch(st + tile, w);
-}
-
-// exclusive prefix of tile `tile` from its predecessors' status words
-__device__ uint32_t look_back(unsigned long long *st, int32_t tile, uint32_t epoch, BfsCtl *c) {
-  uint32_t excl = 0;
-  int32_t j = tile - 1;
-  int64_t spins = 0;
-  const unsigned long long tag = epoch & 0x3FFFFFFFu;
-  while (j >= 0) {
-    unsigned long long w = *(volatile unsigned long long *)(st + j);
-    unsigned long long flag = (w >> 32) & 3ull;
-    if ((w >> 34) != tag || flag == 0) {
-      if (++spins > kSpinLimit) {
-        c->error = kDevTimeout;
-        return excl;
-      }
-      continue;
-    }
-    excl += (uint32_t)w;
-    if (flag == kFlagPrefix) break;
-    --j;
-  }
-  return excl;
-}
-
 __global__ void __launch_bounds__(kScanThreads) k_bfs_scan(BfsArgs a) {
   BfsCtl *c = a.ctl;
   if (c->done || c->error || c->dir != kPush) return;
-  const int32_t q = c->q_len;
   const int32_t p = c->parity;
-  const int32_t *Q = queue_of(a, p);
   if (a.do_bitmap) {
     uint32_t *N = bits_of(a, p ^ 1);
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < a.nwords;
          w += (int64_t)gridDim.x * blockDim.x)
       N[w] = 0u;
   }
-  const uint32_t epoch = c->epoch;
-  const int32_t ntiles = (q + kScanTile - 1) / kScanTile;
-  __shared__ int32_t s_tile;
-  __shared__ uint32_t s_excl;
-  __shared__ uint32_t s_red[33];
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_ctr, 1);
-    __syncthreads();
-    const int32_t tile = s_tile;
-    __syncthreads();
-    if (tile >= ntiles) break;
-    const int64_t base = (int64_t)tile * kScanTile + threadIdx.x * kScanItems;
-    uint32_t deg[kScanItems];
-    uint32_t local = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      int64_t i = base + k;
-      uint32_t d = 0;
-      if (i < q) {
-        int32_t u = Q[i];
-        d = (uint32_t)(a.R[u + 1] - a.R[u]);
-      }
-      deg[k] = d;
-      local += d;
-    }
-    uint32_t agg;
-    uint32_t texcl = block_excl_sum(local, s_red, &agg);
-    if (threadIdx.x == 0) {
-      uint32_t excl = 0;
-      if (tile == 0) {
-        publish(a.status, tile, epoch, kFlagPrefix, agg);
-      } else {
-        publish(a.status, tile, epoch, kFlagAgg, agg);
-        excl = look_back(a.status, tile, epoch, c);
-        publish(a.status, tile, epoch, kFlagPrefix, excl + agg);
-      }
-      s_excl = excl;
-    }
-    __syncthreads();
-    uint32_t run = s_excl + texcl;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      int64_t i = base + k;
-      if (i < q) a.scan[i] = (int32_t)run;
-      run += deg[k];
-    }
-    if (tile == ntiles - 1 && threadIdx.x == 0) {
-      const long long total = (long long)s_excl + agg;
-      a.scan[q] = (int32_t)total;
-      if (c->mf_pending) c->mu -= total;
-      c->mf_pending = 0;
-      c->mf = total;
-      if (c->policy == GR_DIR_AUTO && (float)total > (float)c->mu / c->alpha) c->dir = kPull;
-    }
-    __syncthreads();
+  ScanState st{a.status, &c->tile_ctr, &c->error, c->epoch};
+  long long total;
+  if (frontier_degree_scan<kScanThreads, kScanItems>(a.R, queue_of(a, p), c->q_len, a.scan,
+                                                     st, &total)) {
+    // last tile: the frontier's edge count is known; apply push -> pull
+    if (c->mf_pending) c->mu -= total;
+    c->mf_pending = 0;
+    c->mf = total;
+    if (c->policy == GR_DIR_AUTO && (float)total > (float)c->mu / c->alpha) c->dir = kPull;
   }
 }
 
-// number of frontier positions i in [0, q) whose merge-path end marker
-// (at merged position S[i+1] + i) lies before diagonal d
-__device__ __forceinline__ int32_t merge_count(const int32_t *S, int32_t q, long long d) {
-  int32_t lo = 0, hi = q;
-  while (lo < hi) {
-    int32_t mid = lo + ((hi - lo) >> 1);
-    if ((long long)S[mid + 1] + mid < d) lo = mid + 1;
-    else hi = mid;
+// Push functor: plain-load cull on the visited bitmap, then one atomicOr
+// claim; the unique winner writes depth/parent and the next-frontier bit.
+struct BfsPushF {
+  uint32_t *visited;
+  uint32_t *next_bits;
+  int32_t *depth;
+  int32_t *parent;
+  int32_t next_level;
+  int32_t do_bitmap;
+  __device__ __forceinline__ int operator()(int32_t u, int32_t v, int32_t) const {
+    const uint32_t mask = 1u << (v & 31);
+    uint32_t *vw = visited + (v >> 5);
+    if (*vw & mask) return 0;
+    if (atomicOr(vw, mask) & mask) return 0;
+    depth[v] = next_level;
+    if (parent) parent[v] = u;
+    if (do_bitmap) atomicOr(next_bits + (v >> 5), mask);
+    return 1;
   }
-  return lo;
-}
+};
 
 __global__ void __launch_bounds__(kPushThreads) k_bfs_push(BfsArgs a) {
   BfsCtl *c = a.ctl;
   if (c->done || c->error || c->dir != kPush) return;
-  const int32_t q = c->q_len;
   const int32_t p = c->parity;
-  const int32_t L = c->level;
-  const int32_t *Q = queue_of(a, p);
-  int32_t *Qn = queue_of(a, p ^ 1);
-  uint32_t *N = bits_of(a, p ^ 1);
-  int32_t *depth = c->depth;
-  int32_t *parent = c->parent;
-  const int32_t *S = a.scan;
-  const long long total = (long long)q + S[q];
-  const long long nchunks = (total + kPushChunk - 1) / kPushChunk;
-
-  __shared__ int32_t s_off[kPushChunk + 1];
-  __shared__ int32_t s_u[kPushChunk + 1];
-  __shared__ int32_t s_row[kPushChunk + 1];
-  __shared__ int32_t s_out[kPushChunk];
-  __shared__ int32_t s_i[2];
-  __shared__ int32_t s_cnt, s_base;
-  const int lane = threadIdx.x & 31;
-
-  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-    const long long d0 = chunk * kPushChunk;
-    const long long d1 = min(d0 + kPushChunk, total);
-    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
-    const int32_t i0 = s_i[0], i1 = s_i[1];
-    const long long j0 = d0 - i0, j1 = d1 - i1;
-    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
-    for (int32_t k = threadIdx.x; k < nv; k += kPushThreads) {
-      const int32_t i = i0 + k;
-      const int32_t u = Q[i];
-      s_off[k] = S[i];
-      s_u[k] = u;
-      s_row[k] = a.R[u];
-    }
-    __syncthreads();
-    const int32_t ne = (int32_t)(j1 - j0);
-    for (int32_t kb = 0; kb < ne; kb += kPushThreads) {
-      const int32_t k = kb + threadIdx.x;
-      bool won = false;
-      int32_t v = 0;
-      if (k < ne) {
-        const int32_t er = (int32_t)(j0 + k);
-        int32_t lo = 0, hi = nv - 1;
-        while (lo < hi) {
-          int32_t mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= er) lo = mid;
-          else hi = mid - 1;
-        }
-        const int32_t u = s_u[lo];
-        v = a.C[s_row[lo] + (er - s_off[lo])];
-        const uint32_t mask = 1u << (v & 31);
-        uint32_t *vw = a.visited + (v >> 5);
-        if (!(*vw & mask)) {
-          const uint32_t old = atomicOr(vw, mask);
-          won = !(old & mask);
-        }
-        if (won) {
-          depth[v] = L + 1;
-          if (parent) parent[v] = u;
-          if (a.do_bitmap) atomicOr(N + (v >> 5), mask);
-        }
-      }
-      const uint32_t bal = __ballot_sync(0xffffffffu, won);
-      if (bal) {
-        const int leader = __ffs(bal) - 1;
-        int32_t pos = 0;
-        if (lane == leader) pos = atomicAdd(&s_cnt, __popc(bal));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (won) s_out[pos + __popc(bal & ((1u << lane) - 1u))] = v;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&c->next_len, s_cnt) : 0;
-    __syncthreads();
-    for (int32_t k = threadIdx.x; k < s_cnt; k += kPushThreads) Qn[s_base + k] = s_out[k];
-    __syncthreads();
-  }
+  BfsPushF f{a.visited, bits_of(a, p ^ 1), c->depth, c->parent, c->level + 1, a.do_bitmap};
+  int32_t unused = 0;
+  lb_advance<kPushThreads, kPushItems, 1>(a.R, a.C, queue_of(a, p), c->q_len, a.scan, f,
+                                          queue_of(a, p ^ 1), &c->next_len, nullptr, &unused);
 }
 
 __global__ void __launch_bounds__(kPullThreads) k_bfs_pull(BfsArgs a) {

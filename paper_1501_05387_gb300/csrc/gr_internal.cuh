@@ -91,6 +91,8 @@ struct gr_graph {
   bool symmetric = false;
   bool rows_sorted = false;
   bool has_weights = false;
+  uint32_t sssp_delta = 1;    // tuned near/far bucket width
+  double mean_weight = 0.0;
 
   std::mutex mu;  // serialises host-side enqueueing on this graph
   cudaEvent_t last_done = nullptr;
@@ -125,6 +127,9 @@ const gr_opts &default_opts();
 
 // Per-primitive scratch release, defined next to each primitive.
 void free_bfs(BfsWorkspace *);
+void free_sssp(SsspWorkspace *);
+void free_cc(CcWorkspace *);
+void free_pr(PrWorkspace *);
 
 // ------------------------------------------------------ device helpers
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

@@ -2,6 +2,7 @@
 // row offsets R and column indices C, SOA per-vertex data), per-graph
 // derived data, error reporting and call ordering.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 
 #include "gr_internal.cuh"
@@ -184,6 +185,15 @@ __global__ void k_symmetric(const int32_t *R, const int32_t *C, int32_t n,
   }
 }
 
+__global__ void k_weight_sum(const uint32_t *W, int64_t m, unsigned long long *sum) {
+  unsigned long long local = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    local += W[e];
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(sum, local);
+}
+
 }  // namespace
 
 gr_status validate_host_csr(int32_t n, int64_t m, const int32_t *R,
@@ -213,6 +223,12 @@ namespace gr {
 static void destroy_workspaces(gr_graph *g) {
   free_bfs(g->bfs);
   g->bfs = nullptr;
+  free_sssp(g->sssp);
+  g->sssp = nullptr;
+  free_cc(g->cc);
+  g->cc = nullptr;
+  free_pr(g->pr);
+  g->pr = nullptr;
 }
 }  // namespace gr
 
@@ -289,6 +305,20 @@ gr_status gr_graph_create(int32_t n, int64_t m, const int32_t *row_off,
     GR_CUDA(cudaMemcpyAsync(hf, f, sizeof(hf), cudaMemcpyDeviceToHost, s));
     GR_CUDA(cudaStreamSynchronize(s));
     g->symmetric = hf[4] == 0;
+  }
+  if (w && m) {
+    GR_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(unsigned long long), s));
+    k_weight_sum<<<grid, 256, 0, s>>>(g->w.as<uint32_t>(), m,
+                                      (unsigned long long *)flags.p);
+    GR_CUDA(cudaGetLastError());
+    unsigned long long wsum = 0;
+    GR_CUDA(cudaMemcpyAsync(&wsum, flags.p, sizeof(wsum), cudaMemcpyDeviceToHost, s));
+    GR_CUDA(cudaStreamSynchronize(s));
+    g->mean_weight = (double)wsum / (double)m;
+    // near/far bucket width: a few mean edge weights keeps the near
+    // frontier wide enough to fill the GPU
+    double d = 2.0 * g->mean_weight;
+    g->sssp_delta = (uint32_t)std::max(1.0, std::min(d, 4.0e9));
   }
   *out = g.release();
   return GR_OK;

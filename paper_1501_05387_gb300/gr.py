@@ -60,6 +60,11 @@ _sig("gr_graph_destroy", [_vp])
 _sig("gr_graph_info", [_vp, _P(_i32), _P(_i64), _P(_i32), _P(_i32), _P(_i32), _P(_i32)])
 _sig("gr_bfs", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_bfs_stats", [_vp, _P(_i32), _P(_i32)])
+_sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
+_sig("gr_sssp_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
+_sig("gr_cc", [_vp, _vp, _P(_i32), _P(gr_opts), _vp])
+_sig("gr_pagerank", [_vp, ctypes.c_float, _i32, ctypes.c_double, _vp, _P(_i32),
+                     _P(gr_opts), _vp])
 
 
 def _check(status: int, where: str):
@@ -186,6 +191,41 @@ def gr_bfs_stats(g: Graph):
     lv, pl = _i32(), _i32()
     _check(_lib.gr_bfs_stats(g.handle, ctypes.byref(lv), ctypes.byref(pl)), "gr_bfs_stats")
     return lv.value, pl.value
+
+
+def gr_sssp(g: Graph, src: int, dist, pred=None, opts=None, stream=None):
+    """SSSP from src into dist[n] (uint32; torch.int32 tensors are accepted
+    and hold the same bits) and pred[n] (int32) if given."""
+    _check(_lib.gr_sssp(g.handle, int(src), _ptr(dist, np.uint32), _ptr(pred, np.int32),
+                        _opts(opts), _stream(stream)), "gr_sssp")
+
+
+def gr_sssp_stats(g: Graph):
+    it, ph = _i32(), _i32()
+    rl = _i64()
+    _check(_lib.gr_sssp_stats(g.handle, ctypes.byref(it), ctypes.byref(ph), ctypes.byref(rl)),
+           "gr_sssp_stats")
+    return it.value, ph.value, rl.value
+
+
+def gr_cc(g: Graph, label, opts=None, stream=None, count=True):
+    """CC labels (int32, smallest vertex id per component) into label[n];
+    returns the number of components (synchronises) when count is true."""
+    k = _i32()
+    _check(_lib.gr_cc(g.handle, _ptr(label, np.int32), ctypes.byref(k) if count else None,
+                      _opts(opts), _stream(stream)), "gr_cc")
+    return k.value if count else None
+
+
+def gr_pagerank(g: Graph, rank, damping=0.85, max_iter=50, tol=1e-7, opts=None,
+                stream=None, count=True):
+    """PageRank (float32) into rank[n]; returns the iterations run
+    (synchronises) when count is true."""
+    it = _i32()
+    _check(_lib.gr_pagerank(g.handle, float(damping), int(max_iter), float(tol),
+                            _ptr(rank, np.float32), ctypes.byref(it) if count else None,
+                            _opts(opts), _stream(stream)), "gr_pagerank")
+    return it.value if count else None
 
 
 def gr_last_error() -> str:

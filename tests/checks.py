@@ -58,10 +58,11 @@ def validate_bfs(row_off, col, src, depth, parent, symmetric=True, keys=None, su
     du = depth[su]
     dv = depth[col]
     both = (du >= 0) & (dv >= 0)
-    assert np.all(np.abs(du[both] - dv[both]) <= 1), "edge spans > 1 level"
-    # in a directed graph a reached u forces its out-neighbour v reached
-    assert np.all(~(du >= 0) | (dv >= 0)), "edge from reached to unreached"
+    # an arc (u, v) from a reached u reaches v at most one level later
+    assert np.all(dv[both] <= du[both] + 1), "arc spans > 1 level forward"
+    assert np.all(~(du >= 0) | (dv >= 0)), "arc from reached to unreached"
     if symmetric:
+        assert np.all(np.abs(du[both] - dv[both]) <= 1), "edge spans > 1 level"
         assert np.all((du >= 0) == (dv >= 0)), "reachability differs across an edge"
 
 

@@ -1,0 +1,152 @@
+"""SSSP parity: distances bit-exact against Dijkstra, predecessors equal to
+the oracle's canonical choice (smallest shortest-path in-neighbour), for any
+near/far bucket width."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from checks import manhattan, validate_sssp_pred
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+
+
+def run_sssp(gr, g, src, o=None, with_pred=True):
+    import torch
+    dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    pred = torch.empty(g.n, dtype=torch.int32, device="cuda") if with_pred else None
+    gr.gr_sssp(g, src, dist, pred, o)
+    torch.cuda.synchronize()
+    gr.gr_sssp_stats(g)  # raises on a device-side cap or timeout
+    d = dist.cpu().numpy().view(np.uint32)
+    return d, (pred.cpu().numpy() if with_pred else None)
+
+
+def check(gr, r, c, w, g, src, o=None):
+    ref_d, ref_p = oracle.sssp(r, c, w, src)
+    d, p = run_sssp(gr, g, src, o)
+    bad = np.nonzero(d != ref_d)[0]
+    assert bad.size == 0, f"dist mismatch at {bad[:10]}: {d[bad[:10]]} vs {ref_d[bad[:10]]}"
+    assert np.array_equal(p, ref_p)
+
+
+def opts(gr, delta=0, mode="auto"):
+    m = {"auto": gr.GR_MODE_AUTO, "launch": gr.GR_MODE_LAUNCH, "graph": gr.GR_MODE_GRAPH}[mode]
+    return gr.gr_opts(delta=delta, mode=m)
+
+
+@pytest.fixture(scope="module")
+def s14w(cuda_lib):
+    r, c = gg.rmat(14, 16, seed=1)
+    w = gg.weights(r, c, seed=3)
+    g = cuda_lib.gr_graph_create(r, c, w)
+    yield r, c, w, g
+    g.close()
+
+
+@pytest.mark.parametrize("delta", [0, 1, 8, 64, 0xFFFFFFFF])
+@pytest.mark.parametrize("mode", ["graph", "launch"])
+def test_rmat_s14_delta_invariance(cuda_lib, s14w, delta, mode):
+    r, c, w, g = s14w
+    for src in [gg.max_degree_vertex(r)] + list(gg.sources(r, 3, seed=7)):
+        check(cuda_lib, r, c, w, g, int(src), opts(cuda_lib, delta, mode))
+
+
+def test_unit_weights_equal_bfs_depth_on_grid(cuda_lib):
+    side = 50
+    r, c = gg.grid(side, p_del=0.0)
+    w = np.ones(c.size, np.uint32)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        d, p = run_sssp(cuda_lib, g, 77)
+        assert np.array_equal(d.astype(np.int64), manhattan(side, 77))
+        validate_sssp_pred(r, c, w, 77, d, p)
+
+
+@pytest.mark.parametrize("side,p_del", [(40, 0.05), (23, 0.3)])
+def test_grid_weighted(cuda_lib, side, p_del):
+    r, c = gg.grid(side, p_del=p_del, seed=4)
+    w = gg.weights(r, c, seed=5, wmin=1, wmax=16)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for src in [0, side * side // 2]:
+            for delta in [0, 1, 16, 0xFFFFFFFF]:
+                check(cuda_lib, r, c, w, g, src, opts(cuda_lib, delta))
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 257])
+def test_ragged_paths(cuda_lib, n):
+    r, c = gg.from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    w = gg.weights(r, c, seed=n, wmin=1, wmax=64)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for src in sorted({0, n // 2, n - 1}):
+            check(cuda_lib, r, c, w, g, src, opts(cuda_lib, 4))
+
+
+def test_zero_and_large_weights(cuda_lib):
+    # zero weights are allowed (non-negative); a huge weight makes a target
+    # unreachable when the sum does not fit below 0xFFFFFFFF
+    r, c = gg.from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 4)])
+    src = np.repeat(np.arange(5), np.diff(r))
+    for big, d4 in [(0xFFFFFFF0, 0xFFFFFFF5), (0xFFFFFFF9, 0xFFFFFFFE), (0xFFFFFFFA, INF)]:
+        # 5 + big: the largest representable distance is 0xFFFFFFFE
+        key = {(0, 1): 0, (1, 2): 5, (2, 3): 0, (3, 4): big}
+        w = np.array([key[(min(a, b), max(a, b))] for a, b in zip(src, c)], np.uint32)
+        with cuda_lib.gr_graph_create(r, c, w) as g:
+            d, p = run_sssp(cuda_lib, g, 0)
+            assert list(d) == [0, 0, 5, 5, d4]
+            assert list(p) == [0, 0, 1, 2, 3 if d4 != INF else -1]
+
+
+def test_disconnected_and_isolated(cuda_lib):
+    r, c = gg.from_edges(8, [(0, 1), (1, 2), (4, 5)])
+    w = gg.weights(r, c, seed=1)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for s in range(8):
+            check(cuda_lib, r, c, w, g, s)
+
+
+def test_directed_weighted(cuda_lib):
+    # 0->1 (9), 0->2 (2), 2->1 (3), 1->3 (1), 3->0 (1)
+    r = np.array([0, 2, 3, 4, 5], np.int32)
+    c = np.array([1, 2, 3, 1, 0], np.int32)
+    w = np.array([9, 2, 1, 3, 1], np.uint32)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for s in range(4):
+            check(cuda_lib, r, c, w, g, s)
+
+
+def test_requires_weights(cuda_lib):
+    import torch
+    r, c = gg.from_edges(3, [(0, 1)])
+    with cuda_lib.gr_graph_create(r, c) as g:
+        d = torch.empty(3, dtype=torch.int32, device="cuda")
+        with pytest.raises(cuda_lib.GrError) as ei:
+            cuda_lib.gr_sssp(g, 0, d)
+        assert ei.value.status == cuda_lib.GR_EINVAL
+
+
+def test_host_outputs(cuda_lib, s14w):
+    r, c, w, g = s14w
+    s = int(gg.sources(r, 1, seed=3)[0])
+    d = np.empty(g.n, np.uint32)
+    p = np.empty(g.n, np.int32)
+    cuda_lib.gr_sssp(g, s, d, p)
+    import torch
+    torch.cuda.synchronize()
+    ref_d, ref_p = oracle.sssp(r, c, w, s)
+    assert np.array_equal(d, ref_d) and np.array_equal(p, ref_p)
+
+
+@pytest.mark.slow
+def test_rmat_s22_sampled_sources(cuda_lib):
+    """R-MAT scale 22, seed 2, weights U[1,64] from seed 3: distances of 3 of
+    the 16 benchmark sources bit-exact against Dijkstra."""
+    r, c = gg.rmat(22, 16, seed=2)
+    w = gg.weights(r, c, seed=3)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for s in gg.sources(r, 16, seed=2)[:3]:
+            ref_d, ref_p = oracle.sssp(r, c, w, int(s))
+            d, p = run_sssp(cuda_lib, g, int(s))
+            assert np.array_equal(d, ref_d)
+            assert np.array_equal(p, ref_p)
