@@ -292,7 +292,9 @@ __global__ void k_sssp_pred(const int32_t *R, const int32_t *C, const uint32_t *
     if (du == 0xFFFFFFFFu) continue;
     for (int32_t e = R[u] + lane; e < R[u + 1]; e += 32) {
       const int32_t v = C[e];
-      if (v != src && (unsigned long long)du + W[e] == dist[v]) atomicMin(pred + v, u);
+      const uint32_t dv = dist[v];
+      if (v != src && dv != 0xFFFFFFFFu && (unsigned long long)du + W[e] == dv)
+        atomicMin(pred + v, u);
     }
   }
 }
