@@ -161,6 +161,29 @@ gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
                       float *rank, int32_t *iters, const gr_opts *opts,
                       void *stream);
 
+/* BFS that allocates nothing, for callers that cannot call cudaMalloc:
+ * code running while a CUDA stream is being captured into a graph (an
+ * allocation there breaks the capture), hosts whose device memory is owned
+ * by their own allocator or pool, and real-time loops that forbid
+ * allocation after start-up. The paper has no counterpart; it is a variant
+ * of the push-only persistent BFS kernel (GR_MODE_PERSISTENT of gr_bfs).
+ *
+ * row_off[n+1] and col[m] are device pointers to a CSR as described above,
+ * read but not validated; depth[n] and parent[n] (parent may be NULL) are
+ * device pointers receiving the same results as gr_bfs. n must not exceed
+ * 1048576 (1 << 20): the scratch is one fixed device array of about 8.5 MB
+ * (control block, two frontier queues, visited bitmap) that every GPU which
+ * loads this library holds until the process exits; larger n returns
+ * GR_EINVAL. The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls on a device share the array and
+ * each call reinitialises what it reads, so calls that overlap on the GPU
+ * (other streams, other threads) race and must be ordered by the caller.
+ * Work is enqueued on `stream`; nothing is synchronised. */
+gr_status gr_bfs_noalloc(int32_t n, int64_t m, const int32_t *row_off,
+                         const int32_t *col, int32_t src, int32_t *depth,
+                         int32_t *parent, void *stream);
+
 /* This thread's last error message ("" if none). The pointer stays valid
  * until this thread's next gr_* call. */
 const char *gr_last_error(void);

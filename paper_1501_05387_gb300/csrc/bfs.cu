@@ -644,3 +644,93 @@ gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- no-allocation variant
+// BFS for callers that must not allocate device memory. Its scratch (the
+// control block, two frontier queues and the visited bitmap) lives in one
+// file-scope device array sized for kNoAllocMaxVertices vertices; every GPU
+// that loads this library holds that array until the process exits.
+namespace gr {
+namespace {
+
+constexpr int32_t kNoAllocMaxVertices = 1 << 20;
+constexpr size_t kNoAllocCtlBytes = 256;  // BfsCtl, padded to 256 bytes
+constexpr size_t kNoAllocQueueBytes = sizeof(int32_t) * ((size_t)kNoAllocMaxVertices + 1);
+constexpr size_t kNoAllocQueueBytesAligned = (kNoAllocQueueBytes + 255) & ~size_t(255);
+constexpr size_t kNoAllocVisitedBytes = sizeof(uint32_t) * (kNoAllocMaxVertices / 32);
+constexpr size_t kNoAllocScratchBytes =
+    kNoAllocCtlBytes + 2 * kNoAllocQueueBytesAligned + kNoAllocVisitedBytes;
+static_assert(sizeof(BfsCtl) <= kNoAllocCtlBytes, "control block does not fit its slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// device address of g_noalloc_scratch, looked up once per device
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+int g_noalloc_sms[kMaxDevices] = {};
+int g_noalloc_blocks_per_sm[kMaxDevices] = {};
+
+gr_status noalloc_setup(int dev, void **addr, int *sms, int *per_sm) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    GR_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    int nsm = 0, occ = 0;
+    GR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs_persistent,
+                                                          kPersThreads, 0));
+    g_noalloc_sms[dev] = nsm;
+    g_noalloc_blocks_per_sm[dev] = std::max(1, std::min(occ, 4));
+    g_noalloc_addr[dev] = p;
+  }
+  *addr = g_noalloc_addr[dev];
+  *sms = g_noalloc_sms[dev];
+  *per_sm = g_noalloc_blocks_per_sm[dev];
+  return GR_OK;
+}
+
+}  // namespace
+}  // namespace gr
+
+extern "C" gr_status gr_bfs_noalloc(int32_t n, int64_t m, const int32_t *row_off,
+                                    const int32_t *col, int32_t src, int32_t *depth,
+                                    int32_t *parent, void *stream) {
+  using namespace gr;
+  clear_error();
+  if (n < 1 || n > kNoAllocMaxVertices)
+    return fail(GR_EINVAL, "n must be in [1, " + std::to_string(kNoAllocMaxVertices) +
+                               "]: gr_bfs_noalloc has a fixed scratch for at most that "
+                               "many vertices (use gr_graph_create + gr_bfs above it)");
+  if (m < 0 || m > INT32_MAX) return fail(GR_EINVAL, "m must be in [0, INT32_MAX]");
+  if (!row_off || (m > 0 && !col)) return fail(GR_EINVAL, "row_off/col must not be NULL");
+  if (!depth) return fail(GR_EINVAL, "depth must not be NULL");
+  if (src < 0 || src >= n) return fail(GR_EINVAL, "source out of range");
+  int dev = 0;
+  GR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(GR_EINVAL, "device ordinal too large");
+  void *base = nullptr;
+  int sms = 0, per_sm = 0;
+  GR_TRY(noalloc_setup(dev, &base, &sms, &per_sm));
+  unsigned char *p = (unsigned char *)base;
+  BfsArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.R = row_off;
+  a.C = col;
+  a.n = n;
+  a.nwords = (n + 31) / 32;
+  a.m = m;
+  a.ctl = (BfsCtl *)p;
+  a.q[0] = (int32_t *)(p + kNoAllocCtlBytes);
+  a.q[1] = (int32_t *)(p + kNoAllocCtlBytes + kNoAllocQueueBytesAligned);
+  a.visited = (uint32_t *)(p + kNoAllocCtlBytes + 2 * kNoAllocQueueBytesAligned);
+  a.do_bitmap = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the init kernel clears the control block and the visited bitmap
+  k_bfs_init<<<sms * 4, 256, 0, s>>>(a, src, depth, parent, GR_DIR_PUSH, 14.f, 24.f, n + 1, 0);
+  GR_CUDA(cudaGetLastError());
+  void *args[] = {&a};
+  GR_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs_persistent, per_sm * sms, kPersThreads,
+                                      args, 0, s));
+  return GR_OK;
+}

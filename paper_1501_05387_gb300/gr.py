@@ -62,6 +62,7 @@ _sig("gr_bfs", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_bfs_stats", [_vp, _P(_i32), _P(_i32)])
 _sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_sssp_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
+_sig("gr_bfs_noalloc", [_i32, _i64, _vp, _vp, _i32, _vp, _vp, _vp])
 _sig("gr_cc", [_vp, _vp, _P(_i32), _P(gr_opts), _vp])
 _sig("gr_pagerank", [_vp, ctypes.c_float, _i32, ctypes.c_double, _vp, _P(_i32),
                      _P(gr_opts), _vp])
@@ -206,6 +207,14 @@ def gr_sssp_stats(g: Graph):
     _check(_lib.gr_sssp_stats(g.handle, ctypes.byref(it), ctypes.byref(ph), ctypes.byref(rl)),
            "gr_sssp_stats")
     return it.value, ph.value, rl.value
+
+
+def gr_bfs_noalloc(row_off, col, src: int, depth, parent=None, stream=None):
+    """BFS without any device allocation (see include/gr.h): row_off, col,
+    depth and parent are CUDA tensors owned by the caller."""
+    _check(_lib.gr_bfs_noalloc(int(row_off.shape[0]) - 1, int(col.shape[0]), _ptr(row_off),
+                               _ptr(col), int(src), _ptr(depth), _ptr(parent),
+                               _stream(stream)), "gr_bfs_noalloc")
 
 
 def gr_cc(g: Graph, label, opts=None, stream=None, count=True):
