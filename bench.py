@@ -217,9 +217,11 @@ def run_gr(args):
     torch.cuda.synchronize()
     depth_host = [d.cpu().numpy() for d in depth]
     levels = []
+    traces = []
     for s in srcs:  # levels per traversal (for the launch count)
         gr.gr_bfs(g, int(s), depth[0], None, bfs_opts)
         levels.append(gr.gr_bfs_stats(g)[0])
+        traces.append(gr.gr_bfs_trace(g))
     launches_per_step = sum(1 + 4 * lv for lv in levels)
 
     clocks = ClockSampler(local)
@@ -314,7 +316,10 @@ def run_gr(args):
                 "bfs_ms": {"mean": float(per_bfs.mean()), "p50": float(np.median(per_bfs)),
                            "p99": float(np.percentile(per_bfs, 99)),
                            "min": float(per_bfs.min()), "max": float(per_bfs.max())},
-                "levels": levels, "wall_s_timed_loop": wall}
+                "levels": levels, "wall_s_timed_loop": wall,
+                "trace_first_source": [
+                    {"dir": "pull" if d else "push", "frontier": f, "edges": e,
+                     "end_us": round(t, 2)} for d, f, e, t in traces[0]]}
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:

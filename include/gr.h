@@ -161,6 +161,25 @@ gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
                       float *rank, int32_t *iters, const gr_opts *opts,
                       void *stream);
 
+/* Batched BFS from k in [1, 64] sources at once (one bit lane per source;
+ * every level reads each column index once for all lanes). srcs[k] is a
+ * host array of vertices (repeats allowed). depth[k*n] (int32) receives
+ * source-major results: depth[i*n + v] is the hop count from srcs[i] to v,
+ * -1 where unreached, equal to gr_bfs's depth for that source. Synchronises
+ * once per level (the level loop is host-driven). */
+gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k,
+                       int32_t *depth, const gr_opts *opts, void *stream);
+
+/* Betweenness centrality (Brandes; Sec. 5.3): bc[n] (double) receives
+ * bc[v] = sum over s in srcs, t != s of sigma_st(v) / sigma_st, v not in
+ * {s, t}, where sigma_st counts shortest (unweighted) s-t paths: no halving
+ * for undirected graphs, no normalisation. srcs[k] is a host array (k >= 0,
+ * repeats counted). Sources run in batches of 64 bit lanes with FP64 path
+ * counts and dependencies. Returns GR_EINVAL if a path count overflows FP64
+ * (e.g. large grids). Synchronises once per BFS level. */
+gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc,
+                const gr_opts *opts, void *stream);
+
 /* BFS that allocates nothing, for callers that cannot call cudaMalloc:
  * code running while a CUDA stream is being captured into a graph (an
  * allocation there breaks the capture), hosts whose device memory is owned
@@ -183,6 +202,15 @@ gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
 gr_status gr_bfs_noalloc(int32_t n, int64_t m, const int32_t *row_off,
                          const int32_t *col, int32_t src, int32_t *depth,
                          int32_t *parent, void *stream);
+
+/* Per-level trace of the last completed gr_bfs (graph and launch modes;
+ * host outputs, any may be NULL; synchronises). For level i < min(cap,
+ * *levels): dir[i] 0 = push, 1 = pull; frontier[i] the frontier size the
+ * level expanded; edges[i] that frontier's edge count; end_us[i] device
+ * time (globaltimer) from the end of initialisation to the end of level i,
+ * in microseconds. At most 64 levels are recorded. */
+gr_status gr_bfs_trace(gr_graph *g, int32_t cap, int32_t *dir, int32_t *frontier,
+                       int64_t *edges, double *end_us, int32_t *levels);
 
 /* This thread's last error message ("" if none). The pointer stays valid
  * until this thread's next gr_* call. */

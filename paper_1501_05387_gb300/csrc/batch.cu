@@ -1,0 +1,514 @@
+// Multi-source traversals with 64 bitmask lanes: batched BFS and Brandes
+// betweenness centrality (Sec. 5.3).
+//
+// Up to 64 sources advance together, one bit lane each (the multi-source BFS
+// idea of Then et al., VLDB 2014). Per vertex v a 64-bit mask lm[L][v] holds
+// the lanes whose frontier at level L contains v; visit[v] the lanes that
+// reached v at an earlier level. One level is a pull over all vertices
+// (the all-vertex frontier of the load-balanced advance, merge-path chunks,
+// lanes over edges): for an edge (v, u), bits = lm[L][u] & ~visited(v) are
+// the lanes in which u is a predecessor of v, and v joins lm[L+1] in those
+// lanes. Every column index is read once per level; the 64 traversals share
+// that read.
+//
+// BC (Brandes, as the paper's Sec. 5.3 describes: a forward BFS pass
+// counting shortest paths sigma, then a backward pass over the BFS levels
+// accumulating dependencies) keeps per vertex 64 FP64 lanes, vertex-major
+// (512 bytes per vertex), so the warp that serves an edge reads the 64
+// lanes of one vertex in two coalesced 256-byte loads:
+//   forward   sigma[v][s] = sum of sigma[u][s] over predecessors u in lane s
+//   backward  with q[w][s] = 1/sigma[w][s] + sum over children x of q[x][s]
+//             (i.e. (1 + delta[w][s]) / sigma[w][s]),
+//             delta[v][s] = sigma[v][s] * sum over children w of q[w][s],
+//             bc[v] += delta[v][s] for every lane s that reached v at level
+//             >= 1 (v is then not lane s's source).
+// This is the dependency recursion delta[v] += sigma[v]/sigma[w]*(1+delta[w])
+// regrouped so that each edge needs one gathered value per lane.
+//
+// The level loop is host-driven (one small read-back per level) because BC
+// keeps one mask array per level and allocates them as levels appear.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "advance.cuh"
+
+namespace gr {
+
+constexpr int kMbThreads = 256, kMbItems = 4;
+constexpr int kMbChunk = kMbThreads * kMbItems;
+
+struct BatchWorkspace {
+  DevMem visit, sigma, q, counter, srcs;
+  std::vector<DevMem *> lm;  // lm[L]: lane masks of level L
+  ~BatchWorkspace() {
+    for (DevMem *p : lm) delete p;
+  }
+};
+
+void free_batch(BatchWorkspace *ws) { delete ws; }
+
+namespace {
+
+struct MbArgs {
+  const int32_t *R;
+  const int32_t *C;
+  int32_t n;
+  unsigned long long all;  // mask of the lanes in use
+  unsigned long long *visit;
+  const unsigned long long *cur;  // lm[L]
+  unsigned long long *nxt;        // lm[L+1], zero on entry
+  double *sigma;                  // [n][64] or null (BFS only)
+  int32_t *depth;                 // [k][n] or null (BC)
+  int32_t k;
+  int32_t level;
+  unsigned long long *count;      // vertices that joined lm[L+1]
+};
+
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long x, int src) {
+  return __shfl_sync(0xffffffffu, x, src);
+}
+
+__device__ __forceinline__ unsigned long long shfl_down_u64(unsigned long long x, int o) {
+  return __shfl_down_sync(0xffffffffu, x, o);
+}
+
+__global__ void k_mb_init(unsigned long long *visit, unsigned long long *lm0, double *sigma,
+                          double *q, int32_t n) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    visit[v] = 0ull;
+    lm0[v] = 0ull;
+  }
+  if (sigma) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * 64;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      sigma[i] = 0.0;
+      q[i] = 0.0;
+    }
+  }
+}
+
+__global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long *lm0,
+                             double *sigma) {
+  const int s = threadIdx.x;
+  if (s < k) {
+    const int32_t v = srcs[s];
+    atomicOr(lm0 + v, 1ull << s);
+    if (sigma) sigma[(int64_t)v * 64 + s] = 1.0;
+  }
+}
+
+// One forward level: lm[L+1][v] = OR over edges (v,u) of lm[L][u] & ~seen(v),
+// seen(v) = visit[v] | lm[L][v]; with sigma, also the path counts of the
+// newly reached lanes. The vertex loader of each chunk folds lm[L] into
+// visit (idempotent, so chunks sharing a vertex may both do it) and, for
+// batched BFS, writes depth L for the lanes of lm[L].
+template <bool SIGMA>
+__global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
+  __shared__ int32_t s_off[kMbChunk + 1];
+  __shared__ unsigned long long s_U[kMbChunk + 1];
+  __shared__ int32_t s_i[2];
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.n + a.R[a.n];
+  const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
+  unsigned long long new_vertices = 0;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * kMbChunk;
+    const long long d1 = min(d0 + kMbChunk, total);
+    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(a.R, a.n, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const int32_t i0 = s_i[0], i1 = s_i[1];
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
+    for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
+      const int32_t v = i0 + kk;
+      const unsigned long long c = a.cur[v];
+      const unsigned long long seen = a.visit[v] | c;
+      if (c) {
+        a.visit[v] = seen;
+        if (a.depth) {
+          for (int s = 0; s < a.k; ++s)
+            if ((c >> s) & 1ull) a.depth[(int64_t)s * a.n + v] = a.level;
+        }
+      }
+      s_off[kk] = a.R[v];
+      s_U[kk] = a.all & ~seen;
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
+      const int32_t kk = kb + threadIdx.x;
+      int32_t owner = -1, u = 0;
+      unsigned long long bits = 0ull;
+      if (kk < ne) {
+        const int32_t e = (int32_t)(j0 + kk);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        owner = i0 + lo;
+        const unsigned long long U = s_U[lo];
+        if (U) {
+          u = a.C[e];
+          bits = a.cur[u] & U;
+        }
+      }
+      if (!SIGMA) {
+        // segmented OR over runs of equal owners, one atomicOr per run
+        unsigned long long acc = bits;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long x = shfl_down_u64(acc, o);
+          const int32_t oo = __shfl_down_sync(0xffffffffu, owner, o);
+          if (lane + o < 32 && oo == owner) acc |= x;
+        }
+        const int32_t prev = __shfl_up_sync(0xffffffffu, owner, 1);
+        if (owner >= 0 && (lane == 0 || prev != owner) && acc) {
+          const unsigned long long old = atomicOr(a.nxt + owner, acc);
+          if (!old) ++new_vertices;
+        }
+      } else {
+        // the warp serves the edges with bits one at a time: lane l handles
+        // BFS lanes l and l + 32 of the predecessor's 64 sigma values
+        uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
+        int32_t cur_owner = -1;
+        unsigned long long orbits = 0ull;
+        double acc0 = 0.0, acc1 = 0.0;
+        while (act) {
+          const int j = __ffs(act) - 1;
+          act &= act - 1u;
+          const int32_t ov = __shfl_sync(0xffffffffu, owner, j);
+          const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+          const unsigned long long bj = shfl_u64(bits, j);
+          if (ov != cur_owner) {
+            if (cur_owner >= 0) {
+              double *sg = a.sigma + (int64_t)cur_owner * 64;
+              if ((orbits >> lane) & 1ull) atomicAdd(sg + lane, acc0);
+              if ((orbits >> (lane + 32)) & 1ull) atomicAdd(sg + lane + 32, acc1);
+              if (lane == 0) {
+                const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
+                if (!old) ++new_vertices;
+              }
+            }
+            cur_owner = ov;
+            orbits = 0ull;
+            acc0 = acc1 = 0.0;
+          }
+          orbits |= bj;
+          const double *su = a.sigma + (int64_t)uj * 64;
+          if ((bj >> lane) & 1ull) acc0 += su[lane];
+          if ((bj >> (lane + 32)) & 1ull) acc1 += su[lane + 32];
+        }
+        if (cur_owner >= 0) {
+          double *sg = a.sigma + (int64_t)cur_owner * 64;
+          if ((orbits >> lane) & 1ull) atomicAdd(sg + lane, acc0);
+          if ((orbits >> (lane + 32)) & 1ull) atomicAdd(sg + lane + 32, acc1);
+          if (lane == 0) {
+            const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
+            if (!old) ++new_vertices;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // new_vertices counts runs whose atomicOr found an empty mask: exactly the
+  // vertices that joined lm[L+1]
+  for (int o = 16; o > 0; o >>= 1) new_vertices += __shfl_xor_sync(0xffffffffu, new_vertices, o);
+  if (lane == 0 && new_vertices) atomicAdd(a.count, new_vertices);
+}
+
+struct BcBackArgs {
+  const int32_t *R;
+  const int32_t *C;
+  int32_t n;
+  const unsigned long long *lv;   // lm[L]
+  const unsigned long long *lw;   // lm[L+1]
+  double *q;                      // [n][64]
+};
+
+// Backward level L: q[v][s] += q[w][s] over edges (v, w) with v in lane s's
+// level L and w in its level L+1 (w's q is final: level L+1 was finished).
+__global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a) {
+  __shared__ int32_t s_off[kMbChunk + 1];
+  __shared__ unsigned long long s_A[kMbChunk + 1];
+  __shared__ int32_t s_i[2];
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.n + a.R[a.n];
+  const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * kMbChunk;
+    const long long d1 = min(d0 + kMbChunk, total);
+    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(a.R, a.n, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const int32_t i0 = s_i[0], i1 = s_i[1];
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
+    for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
+      s_off[kk] = a.R[i0 + kk];
+      s_A[kk] = a.lv[i0 + kk];
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
+      const int32_t kk = kb + threadIdx.x;
+      int32_t owner = -1, w = 0;
+      unsigned long long bits = 0ull;
+      if (kk < ne) {
+        const int32_t e = (int32_t)(j0 + kk);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        owner = i0 + lo;
+        const unsigned long long A = s_A[lo];
+        if (A) {
+          w = a.C[e];
+          bits = A & a.lw[w];
+        }
+      }
+      uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
+      int32_t cur_owner = -1;
+      unsigned long long orbits = 0ull;
+      double acc0 = 0.0, acc1 = 0.0;
+      while (act) {
+        const int j = __ffs(act) - 1;
+        act &= act - 1u;
+        const int32_t ov = __shfl_sync(0xffffffffu, owner, j);
+        const int32_t wj = __shfl_sync(0xffffffffu, w, j);
+        const unsigned long long bj = shfl_u64(bits, j);
+        if (ov != cur_owner) {
+          if (cur_owner >= 0) {
+            double *qv = a.q + (int64_t)cur_owner * 64;
+            if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
+            if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
+          }
+          cur_owner = ov;
+          orbits = 0ull;
+          acc0 = acc1 = 0.0;
+        }
+        orbits |= bj;
+        const double *qw = a.q + (int64_t)wj * 64;
+        if ((bj >> lane) & 1ull) acc0 += qw[lane];
+        if ((bj >> (lane + 32)) & 1ull) acc1 += qw[lane + 32];
+      }
+      if (cur_owner >= 0) {
+        double *qv = a.q + (int64_t)cur_owner * 64;
+        if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
+        if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Finish level L: delta[v][s] = sigma[v][s] * q[v][s] (q holds the child
+// sum), bc[v] += delta over the lanes of lm[L][v], then q[v][s] becomes
+// 1/sigma + child sum for level L-1. One warp per vertex, lanes over s.
+__global__ void k_bc_finalize(const unsigned long long *lv, const double *sigma, double *q,
+                              double *bc, int32_t n, int32_t *overflow) {
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int64_t v = gw; v < n; v += nw) {
+    const unsigned long long A = lv[v];
+    if (!A) continue;
+    double part = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = lane + 32 * h;
+      if ((A >> s) & 1ull) {
+        const double sg = sigma[v * 64 + s];
+        const double child = q[v * 64 + s];
+        if (!isfinite(sg) || sg <= 0.0) *overflow = 1;
+        part += sg * child;
+        q[v * 64 + s] = 1.0 / sg + child;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) bc[v] += part;
+  }
+}
+
+__global__ void k_fill_f64(double *x, int64_t n, double val) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = val;
+}
+
+}  // namespace
+
+static gr_status ensure_batch_ws(gr_graph *g, bool need_bc) {
+  if (!g->batch) {
+    std::unique_ptr<BatchWorkspace> ws(new BatchWorkspace());
+    GR_TRY(ws->visit.alloc(sizeof(unsigned long long) * (size_t)g->n, "lane visit masks"));
+    GR_TRY(ws->counter.alloc(sizeof(unsigned long long) * 4, "batch counters"));
+    GR_TRY(ws->srcs.alloc(sizeof(int32_t) * 64, "batch sources"));
+    g->batch = ws.release();
+  }
+  BatchWorkspace *ws = g->batch;
+  if (need_bc && !ws->sigma.p) {
+    GR_TRY(ws->sigma.alloc(sizeof(double) * 64 * (size_t)g->n, "BC path counts"));
+    GR_TRY(ws->q.alloc(sizeof(double) * 64 * (size_t)g->n, "BC dependencies"));
+  }
+  return GR_OK;
+}
+
+// level masks, allocated as levels appear (zeroed before use)
+static gr_status level_mask(gr_graph *g, size_t L, cudaStream_t s, unsigned long long **out) {
+  BatchWorkspace *ws = g->batch;
+  while (ws->lm.size() <= L) {
+    std::unique_ptr<DevMem> m(new DevMem());
+    GR_TRY(m->alloc(sizeof(unsigned long long) * (size_t)g->n, "level lane masks"));
+    ws->lm.push_back(m.release());
+  }
+  GR_CUDA(cudaMemsetAsync(ws->lm[L]->p, 0, sizeof(unsigned long long) * (size_t)g->n, s));
+  *out = ws->lm[L]->as<unsigned long long>();
+  return GR_OK;
+}
+
+// Forward levels of one batch of k <= 64 sources. Returns the number of
+// levels holding vertices (the sources' level included).
+static gr_status run_forward(gr_graph *g, const int32_t *h_srcs, int32_t k, int32_t *depth,
+                             bool with_sigma, cudaStream_t s, int32_t max_levels,
+                             int32_t *levels_out) {
+  BatchWorkspace *ws = g->batch;
+  const int grid = g->num_sms * 8;
+  unsigned long long *lm0;
+  GR_TRY(level_mask(g, 0, s, &lm0));
+  k_mb_init<<<grid, 256, 0, s>>>(ws->visit.as<unsigned long long>(), lm0,
+                                 with_sigma ? ws->sigma.as<double>() : nullptr,
+                                 with_sigma ? ws->q.as<double>() : nullptr, g->n);
+  GR_CUDA(cudaMemcpyAsync(ws->srcs.p, h_srcs, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+  k_mb_sources<<<1, 64, 0, s>>>(ws->srcs.as<int32_t>(), k, lm0,
+                                with_sigma ? ws->sigma.as<double>() : nullptr);
+  GR_CUDA(cudaGetLastError());
+  MbArgs a;
+  a.R = g->row_off.as<int32_t>();
+  a.C = g->col.as<int32_t>();
+  a.n = g->n;
+  a.all = k == 64 ? ~0ull : ((1ull << k) - 1ull);
+  a.visit = ws->visit.as<unsigned long long>();
+  a.sigma = with_sigma ? ws->sigma.as<double>() : nullptr;
+  a.depth = depth;
+  a.k = k;
+  a.count = ws->counter.as<unsigned long long>();
+  int32_t L = 0;
+  for (;;) {
+    unsigned long long *nxt;
+    GR_TRY(level_mask(g, (size_t)L + 1, s, &nxt));
+    a.cur = ws->lm[L]->as<unsigned long long>();
+    a.nxt = nxt;
+    a.level = L;
+    GR_CUDA(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
+    if (with_sigma)
+      k_mb_forward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
+    else
+      k_mb_forward<false><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
+    GR_CUDA(cudaGetLastError());
+    unsigned long long cnt = 0;
+    GR_CUDA(cudaMemcpyAsync(&cnt, a.count, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    GR_CUDA(cudaStreamSynchronize(s));
+    ++L;
+    if (cnt == 0) break;  // level L is empty; levels 0..L-1 hold vertices
+    if (L >= max_levels) return fail(GR_ETIMEOUT, "level limit reached");
+  }
+  *levels_out = L;
+  return GR_OK;
+}
+
+}  // namespace gr
+
+using namespace gr;
+
+extern "C" {
+
+gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k, int32_t *depth,
+                       const gr_opts *opts, void *stream) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (k < 1 || k > 64) return fail(GR_EINVAL, "k must be in [1, 64]");
+  if (!srcs || !depth) return fail(GR_EINVAL, "srcs/depth must not be NULL");
+  for (int32_t i = 0; i < k; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->n) return fail(GR_EINVAL, "source out of range");
+  const gr_opts &o = opts ? *opts : default_opts();
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  GR_TRY(begin_call(g, s));
+  GR_TRY(ensure_batch_ws(g, false));
+  void *d_depth;
+  bool cp;
+  const size_t bytes = sizeof(int32_t) * (size_t)k * (size_t)g->n;
+  GR_TRY(resolve_output(g, 0, depth, bytes, &d_depth, &cp));
+  GR_CUDA(cudaMemsetAsync(d_depth, 0xFF, bytes, s));  // -1 = unreached
+  int32_t levels = 0;
+  const int32_t max_levels = o.max_iters > 0 ? o.max_iters : g->n + 1;
+  GR_TRY(run_forward(g, srcs, k, (int32_t *)d_depth, false, s, max_levels, &levels));
+  if (cp) GR_CUDA(cudaMemcpyAsync(depth, d_depth, bytes, cudaMemcpyDeviceToHost, s));
+  GR_TRY(end_call(g, s));
+  return GR_OK;
+}
+
+gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const gr_opts *opts,
+                void *stream) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (k < 0) return fail(GR_EINVAL, "k must be >= 0");
+  if ((k > 0 && !srcs) || !bc) return fail(GR_EINVAL, "srcs/bc must not be NULL");
+  for (int32_t i = 0; i < k; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->n) return fail(GR_EINVAL, "source out of range");
+  const gr_opts &o = opts ? *opts : default_opts();
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  GR_TRY(begin_call(g, s));
+  GR_TRY(ensure_batch_ws(g, true));
+  void *d_bc;
+  bool cp;
+  GR_TRY(resolve_output(g, 0, bc, sizeof(double) * (size_t)g->n, &d_bc, &cp));
+  const int grid = g->num_sms * 8;
+  k_fill_f64<<<grid, 256, 0, s>>>((double *)d_bc, g->n, 0.0);
+  BatchWorkspace *ws = g->batch;
+  int32_t *overflow = (int32_t *)(ws->counter.as<unsigned long long>() + 1);
+  GR_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int32_t), s));
+  const int32_t max_levels = o.max_iters > 0 ? o.max_iters : g->n + 1;
+  for (int32_t b = 0; b < k; b += 64) {
+    const int32_t kb = std::min<int32_t>(64, k - b);
+    int32_t levels = 0;
+    GR_TRY(run_forward(g, srcs + b, kb, nullptr, true, s, max_levels, &levels));
+    // backward over levels levels-2 .. 1 (level levels-1 has no children;
+    // level 0 holds the sources, which take no credit)
+    BcBackArgs ba;
+    ba.R = g->row_off.as<int32_t>();
+    ba.C = g->col.as<int32_t>();
+    ba.n = g->n;
+    ba.q = ws->q.as<double>();
+    for (int32_t L = levels - 1; L >= 1; --L) {
+      if (L + 1 < levels) {
+        ba.lv = ws->lm[L]->as<unsigned long long>();
+        ba.lw = ws->lm[L + 1]->as<unsigned long long>();
+        k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba);
+      }
+      k_bc_finalize<<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
+                                         ws->sigma.as<double>(), ws->q.as<double>(),
+                                         (double *)d_bc, g->n, overflow);
+      GR_CUDA(cudaGetLastError());
+    }
+  }
+  if (cp) GR_CUDA(cudaMemcpyAsync(bc, d_bc, sizeof(double) * (size_t)g->n,
+                                  cudaMemcpyDeviceToHost, s));
+  int32_t h_over = 0;
+  GR_CUDA(cudaMemcpyAsync(&h_over, overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GR_CUDA(cudaStreamSynchronize(s));
+  GR_TRY(end_call(g, s));
+  if (h_over)
+    return fail(GR_EINVAL, "shortest-path counts overflow FP64 on this graph (BC undefined)");
+  return GR_OK;
+}
+
+}  // extern "C"

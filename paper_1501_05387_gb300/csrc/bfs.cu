@@ -1,35 +1,37 @@
 // Breadth-first search over the frontier operators (Sec. 5.1).
 //
-// One BFS level is a fixed sequence of kernels that read every decision from
-// a device-resident control block, so the level loop needs no host round
-// trip:
+// One BFS level is ONE kernel, k_bfs_level, whose blocks take every decision
+// from a device-resident control block, so the level loop needs no host
+// round trip:
 //
-//   k_bfs_scan   exclusive scan of the frontier's degrees (the "scanned edge
-//                offset queue" of Sec. 4.4), single pass with decoupled
-//                look-back; its last tile applies the push->pull rule
-//                (Sec. 4.5) because only then are the frontier's edges known.
-//   k_bfs_push   advance + filter fused (Sec. 4.3 kernel fusion): merge-path
-//                partitioning of frontier vertices and their edges into
-//                equal chunks (Sec. 4.4 load-balanced partitioning, merging
-//                vertex ends with edge ranks), coalesced column loads, a
-//                plain-load visited-bitmap cull, one atomicOr claim per
-//                surviving candidate so that each vertex enters the next
-//                frontier once (the non-idempotent advance of Sec. 4.5), and
-//                a warp-aggregated compaction into the next queue.
-//   k_bfs_pull   bottom-up advance (Sec. 4.5): every unvisited vertex scans
-//                its neighbours for one in the frontier bitmap and stops at
-//                the first. A warp owns 32 consecutive vertices, i.e. one
-//                bitmap word, so the visited and next-frontier bitmaps are
-//                written with a ballot and a plain store: no atomics.
-//   k_bfs_level_end  one thread: swaps queues, applies the pull->push rule,
-//                detects the empty frontier and, inside a CUDA graph, sets
-//                the while-loop condition.
+//   push level  advance + filter fused (Sec. 4.3 kernel fusion): merge-path
+//               chunks over the frontier's vertex ends and edge ranks (the
+//               load-balanced partitioning of Sec. 4.4), coalesced column
+//               loads, a plain-load visited-bitmap cull and one atomicOr claim
+//               per surviving candidate, so each vertex enters the next
+//               frontier once (the non-idempotent advance of Sec. 4.5).
+//   pull level  bottom-up advance (Sec. 4.5): every unvisited vertex looks
+//               for a neighbour in the frontier bitmap and stops at the first.
+//               A warp owns 32 consecutive vertices, one bitmap word, so the
+//               visited and next-frontier bitmaps are written with a ballot and
+//               a plain store: no atomics. Lanes check their first neighbours
+//               with independent loads; vertices left over with longer lists
+//               are then scanned by the whole warp, 32 neighbours at a time.
 //
-// The level loop runs either as a CUDA graph with a device-side while node
-// (GR_MODE_GRAPH) or as host-enqueued batches of levels whose kernels exit at
-// once after the traversal finished (GR_MODE_LAUNCH). A cooperative
-// persistent kernel (GR_MODE_PERSISTENT) serves graphs with thousands of
-// small levels.
+// Both emit the next frontier together with its exclusive degree scan (the
+// "scanned edge offset queue" of Sec. 4.4): a block compacts its new
+// vertices in shared memory, scans their degrees and reserves queue and
+// edge ranges with a single 64-bit atomicAdd on a packed (vertices, edges)
+// counter, so queue order and scan order agree and no separate scan pass is
+// needed. The last block to finish a level applies the push/pull rule
+// (Sec. 4.5), swaps the buffers and, inside a CUDA graph, sets the while
+// loop's condition.
+//
+// Drivers: a CUDA graph holding a device-side while loop over k_bfs_level
+// (GR_MODE_GRAPH), host-enqueued batches of levels that exit at once after
+// the traversal finished (GR_MODE_LAUNCH), and a cooperative persistent
+// kernel with a bounded-spin grid barrier for long chains of small push
+// frontiers (GR_MODE_PERSISTENT).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -46,28 +48,41 @@ struct BfsCtl {
   int32_t *parent;
   int32_t src;
   int32_t level;        // depth of the current frontier
-  int32_t parity;       // which queue / bitmap holds the current frontier
+  int32_t parity;       // which queue / scan array holds the current frontier
   int32_t dir;          // direction of the current level
   int32_t q_len;        // current frontier size
   int32_t q_prev;       // previous frontier size
-  int32_t next_len;     // next frontier size (atomic counter)
-  int32_t tile_ctr;     // scan tile counter (atomic)
   int32_t done;
   int32_t error;
   int32_t pull_levels;
   int32_t policy;       // GR_DIR_*
-  int32_t mf_pending;   // 1: frontier edge count not yet known (push level)
   int32_t max_levels;
-  uint32_t epoch;       // tags scan tile status words; never reset
+  int32_t blocks_done;  // level-kernel blocks finished (the last one ends the level)
   int32_t barrier_gen;  // persistent-kernel grid barrier generation
   int32_t barrier_cnt;  // persistent-kernel grid barrier arrivals
-  int32_t pad;
+  int32_t from_bitmap;  // 1: the current frontier exists only as a bitmap
+  int32_t pad_;
+  unsigned long long next_packed;  // [31:0] next frontier size, [63:32] its edges
   long long mf;         // edges leaving the current frontier
-  long long next_mf;    // edges leaving the next frontier (pull producer)
   long long mu;         // edges of still-unexplored vertices
   float alpha;
   float beta;
+  // per-level trace (first kTraceLevels levels): direction, frontier size
+  // and edges of the frontier each level expanded, and globaltimer at the
+  // end of the level (the init kernel stamps t_start)
+  unsigned long long t_start;
+  int32_t tr_dir[64];
+  int32_t tr_q[64];
+  long long tr_mf[64];
+  unsigned long long tr_t[64];
 };
+constexpr int kTraceLevels = 64;
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct BfsArgs {
   const int32_t *R;
@@ -77,27 +92,24 @@ struct BfsArgs {
   long long m;
   const uint32_t *iso;
   int32_t *q[2];
-  int32_t *scan;
+  int32_t *S[2];        // exclusive degree scan of q[p], S[p][q_len] = edges
   uint32_t *visited;
-  uint32_t *fb[2];
-  unsigned long long *status;
+  uint32_t *fb[3];      // frontier bitmaps, rotating by level (cur, next, spare)
   BfsCtl *ctl;
   int32_t do_bitmap;
 };
 
-// launch shapes
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kPushThreads = 256;
-constexpr int kPushItems = 8;
-constexpr int kPullThreads = 256;
-constexpr int kPullFlushRounds = 8;
+// launch shape of the level kernel
+constexpr int kLvThreads = 256;
+constexpr int kLvItems = 4;                        // merge items per thread (push)
+constexpr int kLvChunk = kLvThreads * kLvItems;    // merge items per chunk
+constexpr int kLvWarps = kLvThreads / 32;
+constexpr int kPullLane = 3;  // neighbours after the first a lane checks alone (pull)
+constexpr int kLvBlocksPerSm = 6;
 
 struct BfsWorkspace {
-  DevMem q[2], scan, visited, fb[2], status, ctl;
+  DevMem q[2], S[2], visited, fb[3], ctl;
   PinnedMem h_ctl;
-  int32_t ntiles = 0;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // by do_bitmap
   cudaGraph_t graph[2] = {nullptr, nullptr};
   ~BfsWorkspace() {
@@ -113,16 +125,20 @@ void free_bfs(BfsWorkspace *ws) { delete ws; }
 // ------------------------------------------------------------- kernels
 namespace {
 
-// select by parity without indexing the parameter arrays (a dynamic index
+// select by index without indexing the parameter arrays (a dynamic index
 // would copy the kernel parameters to local memory)
 __device__ __forceinline__ int32_t *queue_of(const BfsArgs &a, int p) { return p ? a.q[1] : a.q[0]; }
-__device__ __forceinline__ uint32_t *bits_of(const BfsArgs &a, int p) { return p ? a.fb[1] : a.fb[0]; }
+__device__ __forceinline__ int32_t *scan_of(const BfsArgs &a, int p) { return p ? a.S[1] : a.S[0]; }
+__device__ __forceinline__ uint32_t *bits_of(const BfsArgs &a, int level) {
+  const int k = level % 3;
+  return k == 0 ? a.fb[0] : (k == 1 ? a.fb[1] : a.fb[2]);
+}
 
 __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *parent,
                            int32_t policy, float alpha, float beta,
                            int32_t max_levels, int32_t preset_iso) {
-  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = tid; v < a.n; v += stride) {
     depth[v] = v == src ? 0 : -1;
     if (parent) parent[v] = v == src ? src : -1;
@@ -133,11 +149,19 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     uint32_t vis = preset_iso ? a.iso[w] : 0u;
     if (w == sw) vis |= sb;
     a.visited[w] = vis;
-    if (a.do_bitmap) a.fb[0][w] = (w == sw) ? sb : 0u;
+    if (a.do_bitmap) {
+      a.fb[0][w] = (w == sw) ? sb : 0u;  // frontier of level 0
+      a.fb[1][w] = 0u;                   // filled by level 0
+    }
   }
   if (tid == 0) {
     BfsCtl *c = a.ctl;
+    const int32_t dsrc = a.R[src + 1] - a.R[src];
     a.q[0][0] = src;
+    if (a.S[0]) {
+      a.S[0][0] = 0;
+      a.S[0][1] = dsrc;
+    }
     c->depth = depth;
     c->parent = parent;
     c->src = src;
@@ -146,174 +170,336 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     c->dir = kPush;
     c->q_len = 1;
     c->q_prev = 0;
-    c->next_len = 0;
-    c->tile_ctr = 0;
     c->done = 0;
     c->error = kDevOk;
     c->pull_levels = 0;
     c->policy = policy;
-    c->mf_pending = 1;
     c->max_levels = max_levels;
+    c->blocks_done = 0;
     c->barrier_gen = 0;
     c->barrier_cnt = 0;
-    c->mf = 0;
-    c->next_mf = 0;
-    c->mu = a.m;
+    c->next_packed = 0ull;
+    c->mf = dsrc;
+    c->mu = a.m - dsrc;
     c->alpha = alpha;
     c->beta = beta;
+    c->from_bitmap = 0;
+    c->t_start = globaltimer();
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_bfs_scan(BfsArgs a) {
-  BfsCtl *c = a.ctl;
-  if (c->done || c->error || c->dir != kPush) return;
-  const int32_t p = c->parity;
-  if (a.do_bitmap) {
-    uint32_t *N = bits_of(a, p ^ 1);
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < a.nwords;
-         w += (int64_t)gridDim.x * blockDim.x)
-      N[w] = 0u;
-  }
-  ScanState st{a.status, &c->tile_ctr, &c->error, c->epoch};
-  long long total;
-  if (frontier_degree_scan<kScanThreads, kScanItems>(a.R, queue_of(a, p), c->q_len, a.scan,
-                                                     st, &total)) {
-    // last tile: the frontier's edge count is known; apply push -> pull
-    if (c->mf_pending) c->mu -= total;
-    c->mf_pending = 0;
-    c->mf = total;
-    if (c->policy == GR_DIR_AUTO && (float)total > (float)c->mu / c->alpha) c->dir = kPull;
-  }
-}
-
-// Push functor: plain-load cull on the visited bitmap, then one atomicOr
-// claim; the unique winner writes depth/parent and the next-frontier bit.
-struct BfsPushF {
-  uint32_t *visited;
-  uint32_t *next_bits;
-  int32_t *depth;
-  int32_t *parent;
-  int32_t next_level;
-  int32_t do_bitmap;
-  __device__ __forceinline__ int operator()(int32_t u, int32_t v, int32_t) const {
-    const uint32_t mask = 1u << (v & 31);
-    uint32_t *vw = visited + (v >> 5);
-    if (*vw & mask) return 0;
-    if (atomicOr(vw, mask) & mask) return 0;
-    depth[v] = next_level;
-    if (parent) parent[v] = u;
-    if (do_bitmap) atomicOr(next_bits + (v >> 5), mask);
-    return 1;
-  }
+// Shared memory of the level kernel: the push part's merge-path tables and
+// the emit buffer (new vertices and their degrees), which the pull part
+// reuses.
+struct LevelSmem {
+  int32_t off[kLvChunk + 1];
+  int32_t u[kLvChunk + 1];
+  int32_t row[kLvChunk + 1];
+  int32_t out[kLvChunk];
+  int32_t deg[kLvChunk];
+  uint32_t red[33];
+  unsigned long long red64[33];
+  int32_t i[2];
+  int32_t cnt;
+  int32_t vbase, ebase;
+  int32_t last;
 };
 
-__global__ void __launch_bounds__(kPushThreads) k_bfs_push(BfsArgs a) {
-  BfsCtl *c = a.ctl;
-  if (c->done || c->error || c->dir != kPush) return;
-  const int32_t p = c->parity;
-  BfsPushF f{a.visited, bits_of(a, p ^ 1), c->depth, c->parent, c->level + 1, a.do_bitmap};
-  int32_t unused = 0;
-  lb_advance<kPushThreads, kPushItems, 1>(a.R, a.C, queue_of(a, p), c->q_len, a.scan, f,
-                                          queue_of(a, p ^ 1), &c->next_len, nullptr, &unused);
+// Append (v, deg) to the block's emit buffer, warp-aggregated.
+__device__ __forceinline__ void emit(LevelSmem &sm, bool take, int32_t v, int32_t d) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t b = __ballot_sync(0xffffffffu, take);
+  if (!b) return;
+  const int leader = __ffs(b) - 1;
+  int32_t pos = 0;
+  if (lane == leader) pos = atomicAdd(&sm.cnt, __popc(b));
+  pos = __shfl_sync(0xffffffffu, pos, leader);
+  if (take) {
+    const int32_t k = pos + __popc(b & ((1u << lane) - 1u));
+    sm.out[k] = v;
+    sm.deg[k] = d;
+  }
 }
 
-__global__ void __launch_bounds__(kPullThreads) k_bfs_pull(BfsArgs a) {
-  BfsCtl *c = a.ctl;
-  if (c->done || c->error || c->dir != kPull) return;
-  const int32_t p = c->parity;
-  const int32_t L = c->level;
-  const uint32_t *F = bits_of(a, p);
-  uint32_t *N = bits_of(a, p ^ 1);
+// Write the emit buffer to the next queue with its exclusive degree scan,
+// reserving both ranges with one packed atomicAdd. Block-uniform call.
+__device__ void flush(LevelSmem &sm, BfsCtl *c, int32_t *Qn, int32_t *Sn) {
+  __syncthreads();
+  const int32_t cnt = sm.cnt;
+  if (cnt) {  // block-uniform
+    constexpr int PER = kLvChunk / kLvThreads;
+    const int32_t k0 = threadIdx.x * PER;
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+      if (k0 + j < cnt) local += (uint32_t)sm.deg[k0 + j];
+    uint32_t total;
+    uint32_t run = block_excl_sum(local, sm.red, &total);
+    if (threadIdx.x == 0) {
+      const unsigned long long old = atomicAdd(
+          &c->next_packed, ((unsigned long long)total << 32) | (unsigned long long)cnt);
+      sm.vbase = (int32_t)(old & 0xFFFFFFFFull);
+      sm.ebase = (int32_t)(old >> 32);
+    }
+    __syncthreads();
+    const int32_t vb = sm.vbase, eb = sm.ebase;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int32_t k = k0 + j;
+      if (k < cnt) {
+        Qn[vb + k] = sm.out[k];
+        Sn[vb + k] = eb + (int32_t)run;
+        run += (uint32_t)sm.deg[k];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sm.cnt = 0;
+  __syncthreads();
+}
+
+__device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p, int32_t L,
+                           int32_t q) {
+  const int32_t *Q = queue_of(a, p);
+  const int32_t *S = scan_of(a, p);
   int32_t *Qn = queue_of(a, p ^ 1);
+  int32_t *Sn = scan_of(a, p ^ 1);
+  uint32_t *N = bits_of(a, L + 1);
   int32_t *depth = c->depth;
   int32_t *parent = c->parent;
+  const long long total = (long long)q + S[q];
+  const long long nchunks = (total + kLvChunk - 1) / kLvChunk;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * kLvChunk;
+    const long long d1 = min(d0 + kLvChunk, total);
+    if (threadIdx.x < 2) sm.i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const int32_t i0 = sm.i[0], i1 = sm.i[1];
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += kLvThreads) {
+      const int32_t u = Q[i0 + k];
+      sm.off[k] = S[i0 + k];
+      sm.u[k] = u;
+      sm.row[k] = a.R[u];
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += kLvThreads) {
+      const int32_t k = kb + threadIdx.x;
+      bool won = false;
+      int32_t v = 0, dv = 0;
+      if (k < ne) {
+        const int32_t er = (int32_t)(j0 + k);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (sm.off[mid] <= er) lo = mid;
+          else hi = mid - 1;
+        }
+        v = a.C[sm.row[lo] + (er - sm.off[lo])];
+        const uint32_t mask = 1u << (v & 31);
+        uint32_t *vw = a.visited + (v >> 5);
+        if (!(*vw & mask)) won = !(atomicOr(vw, mask) & mask);
+        if (won) {
+          depth[v] = L + 1;
+          if (parent) parent[v] = sm.u[lo];
+          if (a.do_bitmap) atomicOr(N + (v >> 5), mask);
+          dv = a.R[v + 1] - a.R[v];
+        }
+      }
+      emit(sm, won, v, dv);
+    }
+    flush(sm, c, Qn, Sn);
+  }
+}
 
-  constexpr int kWarps = kPullThreads / 32;
-  constexpr int kCap = kPullThreads * kPullFlushRounds;
-  __shared__ int32_t s_out[kCap];
-  __shared__ int32_t s_cnt, s_base;
-  __shared__ long long s_red[33];
+// Pull level: no queue is written; the block counts the vertices it found
+// and their edges and adds both to the packed counter once at the end. A
+// warp owns kPullWords consecutive bitmap words per step (32 * kPullWords
+// vertices, kPullWords per lane) so several load chains are in flight.
+constexpr int kPullWords = 2;
+
+__device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L) {
+  const uint32_t *F = bits_of(a, L);
+  uint32_t *N = bits_of(a, L + 1);
+  int32_t *depth = c->depth;
+  int32_t *parent = c->parent;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_cnt = 0;
-  __syncthreads();
-  const long long words_per_round = (long long)gridDim.x * kWarps;
-  const int32_t rounds = (int32_t)((a.nwords + words_per_round - 1) / words_per_round);
-  long long local_mf = 0;
-  for (int32_t r = 0; r < rounds; ++r) {
-    const long long w = ((long long)r * gridDim.x + blockIdx.x) * kWarps + wid;
-    if (w < a.nwords) {
-      const uint32_t vis = a.visited[w];
-      const int32_t v = (int32_t)(w * 32 + lane);
-      bool found = false;
-      int32_t uf = -1, deg = 0;
-      if (v < a.n && !((vis >> lane) & 1u)) {
-        const int32_t r0 = a.R[v], r1 = a.R[v + 1];
-        for (int32_t e = r0; e < r1; ++e) {
+  const long long gw = (long long)blockIdx.x * kLvWarps + wid;
+  const long long nw = (long long)gridDim.x * kLvWarps;
+  const long long groups = (a.nwords + kPullWords - 1) / kPullWords;
+  uint32_t found_cnt = 0;
+  unsigned long long found_deg = 0;
+  for (long long gi = gw; gi < groups; gi += nw) {  // warp-uniform loop
+    const long long w0 = gi * kPullWords;
+    uint32_t vis[kPullWords];
+    int32_t v[kPullWords], r0[kPullWords], r1[kPullWords], uf[kPullWords];
+    bool act[kPullWords], fnd[kPullWords];
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j) {
+      const long long w = w0 + j;
+      vis[j] = w < a.nwords ? a.visited[w] : 0xFFFFFFFFu;
+      v[j] = (int32_t)(w * 32 + lane);
+      act[j] = w < a.nwords && v[j] < a.n && !((vis[j] >> lane) & 1u);
+      fnd[j] = false;
+      uf[j] = -1;
+      r0[j] = r1[j] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j)
+      if (act[j]) {
+        r0[j] = a.R[v[j]];
+        r1[j] = a.R[v[j] + 1];
+      }
+    // first neighbour of every vertex, independent loads
+    int32_t u1[kPullWords];
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j) u1[j] = (act[j] && r0[j] < r1[j]) ? a.C[r0[j]] : -1;
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j)
+      if (u1[j] >= 0 && test_bit(F, u1[j])) {
+        fnd[j] = true;
+        uf[j] = u1[j];
+      }
+    // the rest of each list: lanes alone up to kPullLane more neighbours,
+    // then the whole warp on whatever is left, 32 neighbours at a time
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j) {
+      if (act[j] && !fnd[j]) {
+        const int32_t stop = min(r1[j], r0[j] + 1 + kPullLane);
+        for (int32_t e = r0[j] + 1; e < stop; ++e) {
           const int32_t u = a.C[e];
           if (test_bit(F, u)) {
-            found = true;
-            uf = u;
+            fnd[j] = true;
+            uf[j] = u;
             break;
           }
         }
-        if (found) deg = r1 - r0;
       }
-      const uint32_t fm = __ballot_sync(0xffffffffu, found);
-      if (lane == 0) {
+      uint32_t longm =
+          __ballot_sync(0xffffffffu, act[j] && !fnd[j] && r1[j] - r0[j] > 1 + kPullLane);
+      while (longm) {
+        const int leader = __ffs(longm) - 1;
+        longm &= longm - 1u;
+        const int32_t b0 = __shfl_sync(0xffffffffu, r0[j], leader) + 1 + kPullLane;
+        const int32_t b1 = __shfl_sync(0xffffffffu, r1[j], leader);
+        for (int32_t base = b0; base < b1; base += 32) {
+          const int32_t e = base + lane;
+          const int32_t u = e < b1 ? a.C[e] : 0;
+          const bool hit = e < b1 && test_bit(F, u);
+          const uint32_t hb = __ballot_sync(0xffffffffu, hit);
+          if (hb) {
+            const int32_t hu = __shfl_sync(0xffffffffu, u, __ffs(hb) - 1);
+            if (lane == leader) {
+              fnd[j] = true;
+              uf[j] = hu;
+            }
+            break;
+          }
+        }
+      }
+      const uint32_t fm = __ballot_sync(0xffffffffu, fnd[j]);
+      const long long w = w0 + j;
+      if (w < a.nwords && lane == 0) {
         N[w] = fm;
-        if (fm) a.visited[w] = vis | fm;
+        if (fm) a.visited[w] = vis[j] | fm;
       }
-      if (found) {
-        depth[v] = L + 1;
-        if (parent) parent[v] = uf;
-        local_mf += deg;
+      if (fnd[j]) {
+        depth[v[j]] = L + 1;
+        if (parent) parent[v[j]] = uf[j];
+        ++found_cnt;
+        found_deg += (unsigned long long)(r1[j] - r0[j]);
       }
-      if (fm) {
-        int32_t pos = 0;
-        if (lane == 0) pos = atomicAdd(&s_cnt, __popc(fm));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (found) s_out[pos + __popc(fm & ((1u << lane) - 1u))] = v;
-      }
-    }
-    if ((r + 1) % kPullFlushRounds == 0 || r == rounds - 1) {
-      __syncthreads();
-      if (threadIdx.x == 0) s_base = s_cnt ? atomicAdd(&c->next_len, s_cnt) : 0;
-      __syncthreads();
-      for (int32_t k = threadIdx.x; k < s_cnt; k += kPullThreads) Qn[s_base + k] = s_out[k];
-      __syncthreads();
-      if (threadIdx.x == 0) s_cnt = 0;
-      __syncthreads();
     }
   }
-  const long long mf = block_sum(local_mf, s_red);
-  if (threadIdx.x == 0 && mf) atomicAdd((unsigned long long *)&c->next_mf, (unsigned long long)mf);
+  // one packed atomicAdd per block: [31:0] vertices, [63:32] their edges
+  const unsigned long long packed =
+      block_sum((found_deg << 32) | (unsigned long long)found_cnt, (unsigned long long *)sm.red64);
+  if (threadIdx.x == 0 && packed) atomicAdd(&c->next_packed, packed);
 }
 
-__device__ __forceinline__ void level_end_body(const BfsArgs &a) {
-  BfsCtl *c = a.ctl;
-  if (c->done) return;
-  if (c->error) {
-    c->done = 1;
-    return;
+// Push level whose frontier exists only as a bitmap (the level after a
+// pull): warps walk the frontier bitmap's words, expand each set vertex
+// lane-parallel, and append winners with a warp-level degree scan and one
+// packed atomicAdd per warp step. Used for the small frontiers after the
+// pull phase, where per-warp appends do not contend.
+__device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t L) {
+  const uint32_t *F = bits_of(a, L);
+  uint32_t *N = bits_of(a, L + 1);
+  int32_t *Qn = queue_of(a, p ^ 1);
+  int32_t *Sn = scan_of(a, p ^ 1);
+  int32_t *depth = c->depth;
+  int32_t *parent = c->parent;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kLvWarps + wid;
+  const long long nw = (long long)gridDim.x * kLvWarps;
+  for (long long w = gw; w < a.nwords; w += nw) {
+    uint32_t fw = F[w];
+    while (fw) {
+      const int j = __ffs(fw) - 1;
+      fw &= fw - 1u;
+      const int32_t u = (int32_t)(w * 32 + j);
+      const int32_t r0 = a.R[u], r1 = a.R[u + 1];
+      for (int32_t base = r0; base < r1; base += 32) {
+        const int32_t e = base + lane;
+        bool won = false;
+        int32_t v = 0, dv = 0;
+        if (e < r1) {
+          v = a.C[e];
+          const uint32_t mask = 1u << (v & 31);
+          uint32_t *vw = a.visited + (v >> 5);
+          if (!(*vw & mask)) won = !(atomicOr(vw, mask) & mask);
+          if (won) {
+            depth[v] = L + 1;
+            if (parent) parent[v] = u;
+            if (a.do_bitmap) atomicOr(N + (v >> 5), mask);
+            dv = a.R[v + 1] - a.R[v];
+          }
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, won);
+        if (b) {
+          const uint32_t incl = warp_incl_sum((uint32_t)dv);
+          const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+          unsigned long long old = 0;
+          if (lane == 0)
+            old = atomicAdd(&c->next_packed,
+                            ((unsigned long long)tot << 32) | (unsigned long long)__popc(b));
+          old = __shfl_sync(0xffffffffu, old, 0);
+          if (won) {
+            const int32_t k = (int32_t)(old & 0xFFFFFFFFull) + __popc(b & ((1u << lane) - 1u));
+            Qn[k] = v;
+            Sn[k] = (int32_t)(old >> 32) + (int32_t)(incl - dv);
+          }
+        }
+      }
+    }
   }
-  const int32_t qn = c->next_len;
+}
+
+// Run by the last block of a level: install the next frontier and decide
+// the next level's direction (Sec. 4.5; Beamer et al.'s rule).
+__device__ void level_end(const BfsArgs &a, BfsCtl *c) {
+  const unsigned long long packed = c->next_packed;
+  const int32_t qn = (int32_t)(packed & 0xFFFFFFFFull);
+  const long long mf = (long long)(packed >> 32);
   const bool was_pull = c->dir == kPull;
-  if (was_pull) {
-    c->mf = c->next_mf;
-    c->mu -= c->next_mf;
-    c->pull_levels += 1;
-    c->mf_pending = 0;
-  } else {
-    c->mf_pending = 1;
+  if (was_pull) c->pull_levels += 1;
+  if (c->level < kTraceLevels) {
+    c->tr_dir[c->level] = c->dir;
+    c->tr_q[c->level] = c->q_len;
+    c->tr_mf[c->level] = c->mf;
+    c->tr_t[c->level] = globaltimer();
   }
+  c->from_bitmap = was_pull;  // a pull leaves only the bitmap of its output
   c->level += 1;
   c->parity ^= 1;
   c->q_prev = c->q_len;
   c->q_len = qn;
-  c->next_len = 0;
-  c->next_mf = 0;
-  c->tile_ctr = 0;
-  c->epoch += 1;
+  c->next_packed = 0ull;
+  c->mf = mf;
+  c->mu -= mf;
+  if (!was_pull) scan_of(a, c->parity)[qn] = (int32_t)mf;
   if (qn == 0) {
     c->done = 1;
     return;
@@ -330,14 +516,41 @@ __device__ __forceinline__ void level_end_body(const BfsArgs &a) {
   } else if (was_pull) {
     c->dir = ((float)qn < (float)a.n / c->beta && qn < c->q_prev) ? kPush : kPull;
   } else {
-    c->dir = kPush;  // the next scan may still switch to pull
+    c->dir = ((float)mf > (float)c->mu / c->alpha) ? kPull : kPush;
   }
 }
 
-__global__ void k_bfs_level_end(BfsArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
-  if (threadIdx.x != 0) return;
-  level_end_body(a);
-  if (use_cond) cudaGraphSetConditional(h, a.ctl->done ? 0u : 1u);
+__global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
+    k_bfs_level(BfsArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
+  BfsCtl *c = a.ctl;
+  if (c->done) return;  // host-driven batches past the end: every block leaves
+  __shared__ LevelSmem sm;
+  if (threadIdx.x == 0) sm.cnt = 0;
+  const int32_t p = c->parity, L = c->level, q = c->q_len, dir = c->dir;
+  // clear the bitmap the next level will fill (nobody reads or writes it now)
+  if (a.do_bitmap) {
+    uint32_t *spare = bits_of(a, L + 2);
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < a.nwords;
+         w += (int64_t)gridDim.x * blockDim.x)
+      spare[w] = 0u;
+  }
+  __syncthreads();
+  if (dir == kPull) pull_level(a, c, sm, L);
+  else if (c->from_bitmap) push_from_bitmap(a, c, p, L);
+  else push_level(a, c, sm, p, L, q);
+  // the last block to finish ends the level
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sm.last = atomicAdd(&c->blocks_done, 1) == (int32_t)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (sm.last && threadIdx.x == 0) {
+    __threadfence();
+    c->blocks_done = 0;
+    level_end(a, c);
+    if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
+  }
 }
 
 // ------------------------------------------------- persistent (push only)
@@ -373,6 +586,22 @@ __device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t
   gen += 1;
   __syncthreads();
   return ok;
+}
+
+// level end of the persistent kernel (push only, no degree scan)
+__device__ void persistent_level_end(BfsCtl *c) {
+  const int32_t qn = (int32_t)(c->next_packed & 0xFFFFFFFFull);
+  c->level += 1;
+  c->parity ^= 1;
+  c->q_prev = c->q_len;
+  c->q_len = qn;
+  c->next_packed = 0ull;
+  if (qn == 0) {
+    c->done = 1;
+  } else if (c->level >= c->max_levels) {
+    c->error = kDevOverflow;
+    c->done = 1;
+  }
 }
 
 __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
@@ -414,14 +643,16 @@ __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
         const uint32_t bal = __ballot_sync(0xffffffffu, won);
         if (bal) {
           int32_t pos = 0;
-          if (lane == 0) pos = atomicAdd(&c->next_len, __popc(bal));
+          if (lane == 0)
+            pos = (int32_t)(atomicAdd(&c->next_packed, (unsigned long long)__popc(bal)) &
+                            0xFFFFFFFFull);
           pos = __shfl_sync(0xffffffffu, pos, 0);
           if (won) Qn[pos + __popc(bal & ((1u << lane) - 1u))] = v;
         }
       }
     }
     if (!grid_barrier(c, nblocks, gen)) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) level_end_body(a);
+    if (blockIdx.x == 0 && threadIdx.x == 0) persistent_level_end(c);
     if (!grid_barrier(c, nblocks, gen)) break;
   }
 }
@@ -433,21 +664,16 @@ static gr_status ensure_bfs_ws(gr_graph *g, cudaStream_t s) {
   if (g->bfs) return GR_OK;
   std::unique_ptr<BfsWorkspace> ws(new BfsWorkspace());
   const size_t n = (size_t)g->n;
-  GR_TRY(ws->q[0].alloc(sizeof(int32_t) * (n + 1), "BFS queue"));
-  GR_TRY(ws->q[1].alloc(sizeof(int32_t) * (n + 1), "BFS queue"));
-  GR_TRY(ws->scan.alloc(sizeof(int32_t) * (n + 2), "BFS degree scan"));
+  for (int i = 0; i < 2; ++i) {
+    GR_TRY(ws->q[i].alloc(sizeof(int32_t) * (n + 1), "BFS queue"));
+    GR_TRY(ws->S[i].alloc(sizeof(int32_t) * (n + 2), "BFS degree scan"));
+  }
   GR_TRY(ws->visited.alloc(sizeof(uint32_t) * g->nwords, "visited bitmap"));
-  GR_TRY(ws->fb[0].alloc(sizeof(uint32_t) * g->nwords, "frontier bitmap"));
-  GR_TRY(ws->fb[1].alloc(sizeof(uint32_t) * g->nwords, "frontier bitmap"));
-  ws->ntiles = (int32_t)((n + kScanTile) / kScanTile) + 1;
-  GR_TRY(ws->status.alloc(sizeof(unsigned long long) * ws->ntiles, "scan status"));
+  for (int i = 0; i < 3; ++i)
+    GR_TRY(ws->fb[i].alloc(sizeof(uint32_t) * g->nwords, "frontier bitmap"));
   GR_TRY(ws->ctl.alloc(sizeof(BfsCtl), "BFS control"));
   GR_TRY(ws->h_ctl.alloc(sizeof(BfsCtl), "BFS control mirror"));
-  GR_CUDA(cudaMemsetAsync(ws->status.p, 0, ws->status.bytes, s));
-  BfsCtl init;
-  std::memset(&init, 0, sizeof(init));
-  init.epoch = 1;
-  GR_CUDA(cudaMemcpyAsync(ws->ctl.p, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  GR_CUDA(cudaMemsetAsync(ws->ctl.p, 0, sizeof(BfsCtl), s));
   GR_CUDA(cudaStreamSynchronize(s));
   g->bfs = ws.release();
   return GR_OK;
@@ -462,36 +688,22 @@ static BfsArgs make_args(gr_graph *g, int32_t do_bitmap) {
   a.nwords = g->nwords;
   a.m = g->m;
   a.iso = g->isolated_bits.as<uint32_t>();
-  a.q[0] = ws->q[0].as<int32_t>();
-  a.q[1] = ws->q[1].as<int32_t>();
-  a.scan = ws->scan.as<int32_t>();
+  for (int i = 0; i < 2; ++i) {
+    a.q[i] = ws->q[i].as<int32_t>();
+    a.S[i] = ws->S[i].as<int32_t>();
+  }
   a.visited = ws->visited.as<uint32_t>();
-  a.fb[0] = ws->fb[0].as<uint32_t>();
-  a.fb[1] = ws->fb[1].as<uint32_t>();
-  a.status = ws->status.as<unsigned long long>();
+  for (int i = 0; i < 3; ++i) a.fb[i] = ws->fb[i].as<uint32_t>();
   a.ctl = ws->ctl.as<BfsCtl>();
   a.do_bitmap = do_bitmap;
   return a;
 }
 
-struct Grids {
-  int scan, push, pull;
-};
+static int level_grid(const gr_graph *g) { return g->num_sms * kLvBlocksPerSm; }
 
-static Grids grids_for(const gr_graph *g) {
-  Grids gr_;
-  gr_.scan = g->num_sms * 2;
-  gr_.push = g->num_sms * 4;
-  gr_.pull = g->num_sms * 8;
-  return gr_;
-}
-
-static gr_status enqueue_level(const BfsArgs &a, const Grids &gd, cudaStream_t s,
+static gr_status enqueue_level(gr_graph *g, const BfsArgs &a, cudaStream_t s,
                                cudaGraphConditionalHandle h, int use_cond) {
-  k_bfs_scan<<<gd.scan, kScanThreads, 0, s>>>(a);
-  k_bfs_push<<<gd.push, kPushThreads, 0, s>>>(a);
-  if (a.do_bitmap) k_bfs_pull<<<gd.pull, kPullThreads, 0, s>>>(a);
-  k_bfs_level_end<<<1, 32, 0, s>>>(a, h, use_cond);
+  k_bfs_level<<<level_grid(g), kLvThreads, 0, s>>>(a, h, use_cond);
   GR_CUDA(cudaGetLastError());
   return GR_OK;
 }
@@ -515,8 +727,7 @@ static gr_status build_level_graph(gr_graph *g, int32_t do_bitmap) {
   GR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   GR_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  BfsArgs a = make_args(g, do_bitmap);
-  gr_status st = enqueue_level(a, grids_for(g), cs, h, 1);
+  gr_status st = enqueue_level(g, make_args(g, do_bitmap), cs, h, 1);
   cudaGraph_t captured;
   cudaError_t e = cudaStreamEndCapture(cs, &captured);
   cudaStreamDestroy(cs);
@@ -585,10 +796,9 @@ gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   GR_TRY(resolve_output(g, 1, parent, sizeof(int32_t) * (size_t)g->n, &d_parent, &cp_parent));
 
   BfsArgs a = make_args(g, do_bitmap);
-  const int init_grid = g->num_sms * 8;
-  k_bfs_init<<<init_grid, 256, 0, s>>>(a, src, (int32_t *)d_depth, (int32_t *)d_parent,
-                                       policy, alpha, beta, max_levels,
-                                       (g->symmetric && do_bitmap) ? 1 : 0);
+  k_bfs_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, (int32_t *)d_depth, (int32_t *)d_parent,
+                                            policy, alpha, beta, max_levels,
+                                            (g->symmetric && do_bitmap) ? 1 : 0);
   GR_CUDA(cudaGetLastError());
 
   if (mode == GR_MODE_GRAPH) {
@@ -604,12 +814,11 @@ gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                                         args, 0, s));
   } else {
     // host-driven: enqueue batches of levels, then check the done flag
-    const Grids gd = grids_for(g);
     BfsCtl *h = g->bfs->h_ctl.as<BfsCtl>();
     int32_t levels_enqueued = 0;
     int32_t batch = 4;
     for (;;) {
-      for (int i = 0; i < batch; ++i) GR_TRY(enqueue_level(a, gd, s, 0, 0));
+      for (int i = 0; i < batch; ++i) GR_TRY(enqueue_level(g, a, s, 0, 0));
       levels_enqueued += batch;
       GR_CUDA(cudaMemcpyAsync(h, g->bfs->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost, s));
       GR_CUDA(cudaStreamSynchronize(s));
@@ -643,8 +852,30 @@ gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels) {
   return GR_OK;
 }
 
-}  // extern "C"
 
+gr_status gr_bfs_trace(gr_graph *g, int32_t cap, int32_t *dir, int32_t *frontier,
+                       int64_t *edges, double *end_us, int32_t *levels) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (!g->bfs) return fail(GR_EINVAL, "no BFS has run on this graph");
+  if (cap < 0) return fail(GR_EINVAL, "cap must be >= 0");
+  std::lock_guard<std::mutex> lock(g->mu);
+  GR_CUDA(cudaSetDevice(g->device));
+  if (g->has_last) GR_CUDA(cudaEventSynchronize(g->last_done));
+  BfsCtl h;
+  GR_CUDA(cudaMemcpy(&h, g->bfs->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost));
+  const int32_t nl = std::min<int32_t>(h.level, kTraceLevels);
+  for (int32_t i = 0; i < std::min(cap, nl); ++i) {
+    if (dir) dir[i] = h.tr_dir[i];
+    if (frontier) frontier[i] = h.tr_q[i];
+    if (edges) edges[i] = h.tr_mf[i];
+    if (end_us) end_us[i] = (double)(h.tr_t[i] - h.t_start) * 1e-3;
+  }
+  if (levels) *levels = nl;
+  return GR_OK;
+}
+
+}  // extern "C"
 // ------------------------------------------------- no-allocation variant
 // BFS for callers that must not allocate device memory. Its scratch (the
 // control block, two frontier queues and the visited bitmap) lives in one
@@ -654,7 +885,7 @@ namespace gr {
 namespace {
 
 constexpr int32_t kNoAllocMaxVertices = 1 << 20;
-constexpr size_t kNoAllocCtlBytes = 256;  // BfsCtl, padded to 256 bytes
+constexpr size_t kNoAllocCtlBytes = 2048;  // BfsCtl, padded to 2 KB
 constexpr size_t kNoAllocQueueBytes = sizeof(int32_t) * ((size_t)kNoAllocMaxVertices + 1);
 constexpr size_t kNoAllocQueueBytesAligned = (kNoAllocQueueBytes + 255) & ~size_t(255);
 constexpr size_t kNoAllocVisitedBytes = sizeof(uint32_t) * (kNoAllocMaxVertices / 32);

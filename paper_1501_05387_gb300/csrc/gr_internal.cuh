@@ -130,6 +130,7 @@ void free_bfs(BfsWorkspace *);
 void free_sssp(SsspWorkspace *);
 void free_cc(CcWorkspace *);
 void free_pr(PrWorkspace *);
+void free_batch(BatchWorkspace *);
 
 // ------------------------------------------------------ device helpers
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

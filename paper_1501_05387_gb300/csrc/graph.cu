@@ -229,6 +229,8 @@ static void destroy_workspaces(gr_graph *g) {
   g->cc = nullptr;
   free_pr(g->pr);
   g->pr = nullptr;
+  free_batch(g->batch);
+  g->batch = nullptr;
 }
 }  // namespace gr
 

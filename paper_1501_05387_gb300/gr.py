@@ -60,8 +60,11 @@ _sig("gr_graph_destroy", [_vp])
 _sig("gr_graph_info", [_vp, _P(_i32), _P(_i64), _P(_i32), _P(_i32), _P(_i32), _P(_i32)])
 _sig("gr_bfs", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_bfs_stats", [_vp, _P(_i32), _P(_i32)])
+_sig("gr_bfs_trace", [_vp, _i32, _vp, _vp, _vp, _vp, _P(_i32)])
 _sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_sssp_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
+_sig("gr_bfs_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
+_sig("gr_bc", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_bfs_noalloc", [_i32, _i64, _vp, _vp, _i32, _vp, _vp, _vp])
 _sig("gr_cc", [_vp, _vp, _P(_i32), _P(gr_opts), _vp])
 _sig("gr_pagerank", [_vp, ctypes.c_float, _i32, ctypes.c_double, _vp, _P(_i32),
@@ -194,6 +197,19 @@ def gr_bfs_stats(g: Graph):
     return lv.value, pl.value
 
 
+def gr_bfs_trace(g: Graph, cap: int = 64):
+    """Per-level trace of the last BFS: list of (dir, frontier, edges, end_us)."""
+    d = np.zeros(cap, np.int32)
+    f = np.zeros(cap, np.int32)
+    e = np.zeros(cap, np.int64)
+    t = np.zeros(cap, np.float64)
+    nl = _i32()
+    _check(_lib.gr_bfs_trace(g.handle, cap, d.ctypes.data, f.ctypes.data, e.ctypes.data,
+                             t.ctypes.data, ctypes.byref(nl)), "gr_bfs_trace")
+    k = min(cap, nl.value)
+    return [(int(d[i]), int(f[i]), int(e[i]), float(t[i])) for i in range(k)]
+
+
 def gr_sssp(g: Graph, src: int, dist, pred=None, opts=None, stream=None):
     """SSSP from src into dist[n] (uint32; torch.int32 tensors are accepted
     and hold the same bits) and pred[n] (int32) if given."""
@@ -207,6 +223,22 @@ def gr_sssp_stats(g: Graph):
     _check(_lib.gr_sssp_stats(g.handle, ctypes.byref(it), ctypes.byref(ph), ctypes.byref(rl)),
            "gr_sssp_stats")
     return it.value, ph.value, rl.value
+
+
+def gr_bfs_batch(g: Graph, srcs, depth, opts=None, stream=None):
+    """Batched BFS from up to 64 sources into depth[k*n] (int32,
+    source-major)."""
+    srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    _check(_lib.gr_bfs_batch(g.handle, srcs.ctypes.data, int(srcs.size), _ptr(depth, np.int32),
+                             _opts(opts), _stream(stream)), "gr_bfs_batch")
+
+
+def gr_bc(g: Graph, srcs, bc, opts=None, stream=None):
+    """Brandes BC summed over srcs (no halving, no normalisation) into
+    bc[n] (float64)."""
+    srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    _check(_lib.gr_bc(g.handle, srcs.ctypes.data if srcs.size else None, int(srcs.size),
+                      _ptr(bc, np.float64), _opts(opts), _stream(stream)), "gr_bc")
 
 
 def gr_bfs_noalloc(row_off, col, src: int, depth, parent=None, stream=None):

@@ -208,3 +208,24 @@ def test_rmat_s22_sixteen_sources(cuda_lib):
             d, p = run_bfs(cuda_lib, g, int(s))
             assert np.array_equal(d, ref)
             validate_bfs(r, c, int(s), d, p, keys=keys, su=su)
+
+
+@pytest.mark.parametrize("direction", DIRS)
+def test_trace_frontier_sizes_match_oracle_levels(cuda_lib, s14, direction):
+    # every frontier is exact (each vertex enters once), so the traced
+    # frontier sizes equal the oracle's vertex count per depth
+    r, c, g = s14
+    src = gg.max_degree_vertex(r)
+    run_bfs(cuda_lib, g, src, opts(cuda_lib, direction, "graph"))
+    tr = cuda_lib.gr_bfs_trace(g)
+    ref, _ = oracle.bfs(r, c, src)
+    hist = np.bincount(ref[ref >= 0])
+    assert [f for _, f, _, _ in tr] == list(hist)
+    deg = np.diff(r)
+    for lvl, (d, f, e, t) in enumerate(tr):
+        assert e == int(deg[ref == lvl].sum())
+        assert d == (0 if direction == "push" or lvl == 0 else d)
+    if direction == "pull":
+        assert all(d == 1 for d, _, _, _ in tr[1:])
+    times = [t for _, _, _, t in tr]
+    assert all(b >= a for a, b in zip(times, times[1:]))
