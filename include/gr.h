@@ -68,14 +68,14 @@ enum {
   GR_MODE_GRAPH = 2,      /* one CUDA graph whose device-side while loop
                              runs one level per iteration */
   GR_MODE_PERSISTENT = 3  /* one cooperative kernel runs every level with a
-                             bounded-spin grid barrier (push only) */
+                             bounded-spin grid barrier between levels */
 };
 
 /* Options; pass NULL for tuned defaults. Zero in a field means "tuned". */
 typedef struct gr_opts {
   int32_t direction;  /* GR_DIR_* */
   int32_t mode;       /* GR_MODE_* */
-  int32_t block;      /* threads per block of the advance kernels (0: tuned) */
+  int32_t block;      /* persistent BFS: blocks per SM (0: tuned) */
   int32_t chunk;      /* merge-path items per block chunk (0: tuned) */
   float alpha;        /* push->pull when frontier edges > unexplored/alpha */
   float beta;         /* pull->push when frontier vertices < n/beta */
@@ -211,6 +211,78 @@ gr_status gr_bfs_noalloc(int32_t n, int64_t m, const int32_t *row_off,
  * in microseconds. At most 64 levels are recorded. */
 gr_status gr_bfs_trace(gr_graph *g, int32_t cap, int32_t *dir, int32_t *frontier,
                        int64_t *edges, double *end_us, int32_t *levels);
+
+/* Autotuning (the paper leaves these knobs to the user, Sec. 4.4, and notes
+ * that the best strategy follows from the degree distribution, Sec. 6). A
+ * graph starts with settings derived from its degree statistics;
+ * gr_autotune times candidate settings on the k >= 1 sample sources srcs
+ * (host array) with CUDA events and keeps the fastest, per graph:
+ * GR_TUNE_BFS tunes the level-loop driver, the persistent grid size and the
+ * push/pull thresholds; GR_TUNE_SSSP the near/far bucket width. Options
+ * passed as 0 use the tuned values. Results never depend on tuning.
+ * Synchronises. */
+enum { GR_TUNE_BFS = 1, GR_TUNE_SSSP = 2 };
+gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
+                      void *stream);
+
+/* The graph's current tuned settings (host outputs; times may be NULL and
+ * are 0 until measured): mode, alpha, beta, block (blocks per SM of the
+ * persistent kernel, 0 = all resident) and delta; mean time per BFS / SSSP
+ * over the tuning sample. */
+gr_status gr_tuned_opts(const gr_graph *g, gr_opts *out, double *bfs_ms, double *sssp_ms);
+
+/* ------------------------------------------------------------------------
+ * Query server (not in the paper): BFS / SSSP / CC queries on resident
+ * graphs with continuous batching. Worker slots each own a CUDA stream and
+ * per-graph workspaces, so queries on different slots overlap on the GPU.
+ * A queued request starts when its result buffer (4n bytes) fits in the
+ * device-memory budget left by the requests in flight and the slots'
+ * workspaces (requests are admitted in arrival order; one that does not fit
+ * holds back the ones behind it). A slot that takes a BFS request on a
+ * batchable graph also takes up to max_batch - 1 further queued BFS
+ * requests for that graph and runs them as lanes of one gr_bfs_batch
+ * traversal. Results equal those of gr_bfs / gr_sssp / gr_cc alone. With
+ * num_slots = 1 and max_batch = 1 the server is the plain path: one query
+ * per launch sequence, in arrival order, on one stream.
+ * ---------------------------------------------------------------------- */
+typedef struct gr_server gr_server;
+
+enum { GR_QUERY_BFS = 0, GR_QUERY_SSSP = 1, GR_QUERY_CC = 2 };
+
+/* budget_bytes > 0; num_slots and max_batch in [1, 64]. */
+gr_status gr_server_create(size_t budget_bytes, int32_t num_slots, int32_t max_batch,
+                           gr_server **out);
+
+/* Register a graph (it must outlive the server) before the first submit.
+ * batchable = 0 keeps its BFS queries single (graphs with many levels). */
+gr_status gr_server_add_graph(gr_server *s, gr_graph *g, int32_t batchable,
+                              int32_t *graph_id);
+
+/* Queue a query: kind GR_QUERY_BFS (depth), GR_QUERY_SSSP (dist, uint32)
+ * or GR_QUERY_CC (labels; src ignored). out (n int32/uint32, device or host
+ * memory, may be NULL to discard) receives the result before the request
+ * counts as done. *ticket identifies the request. Never blocks. */
+gr_status gr_server_submit(gr_server *s, int32_t graph_id, int32_t kind, int32_t src,
+                           void *out, uint64_t *ticket);
+
+/* Wait for one request (timeout_ms < 0: no limit; GR_ETIMEOUT on expiry)
+ * and forget it; *latency_ms (may be NULL) = submission to completion. */
+gr_status gr_server_wait(gr_server *s, uint64_t ticket, int32_t timeout_ms,
+                         double *latency_ms);
+
+/* Wait until every submitted request has finished (GR_ETIMEOUT on expiry). */
+gr_status gr_server_drain(gr_server *s, int32_t timeout_ms);
+
+/* Totals since creation (host scalars, any may be NULL): completed and
+ * failed requests, device launches (a batch counts once), throughput from
+ * the first submission to the last completion, latency percentiles (ms,
+ * submission to completion) and the mean number of requests per launch. */
+gr_status gr_server_stats(gr_server *s, int64_t *completed, int64_t *failed,
+                          int64_t *launches, double *qps, double *p50_ms, double *p99_ms,
+                          double *mean_batch);
+
+/* Stop the workers (queued requests are dropped) and free the server. */
+gr_status gr_server_destroy(gr_server *s);
 
 /* This thread's last error message ("" if none). The pointer stays valid
  * until this thread's next gr_* call. */

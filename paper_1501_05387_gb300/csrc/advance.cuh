@@ -138,6 +138,20 @@ __device__ __forceinline__ int32_t merge_count(const int32_t *S, int32_t q, long
   return lo;
 }
 
+// merge_count with S[q] supplied by the caller (when the array's last entry
+// is not stored)
+__device__ __forceinline__ int32_t merge_count_t(const int32_t *S, int32_t q, int32_t s_q,
+                                                 long long d) {
+  int32_t lo = 0, hi = q;
+  while (lo < hi) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    const int32_t sv = (mid + 1 == q) ? s_q : S[mid + 1];
+    if ((long long)sv + mid < d) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Append `v` to one of two block-local output buffers selected per thread
 // (code 1 -> buffer 0, code 2 -> buffer 1), warp-aggregated.
 __device__ __forceinline__ void warp_append(int code, int32_t v, int32_t *buf0,
@@ -295,6 +309,115 @@ __device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n
     }
     __syncthreads();
   }
+}
+
+}  // namespace gr
+
+namespace gr {
+
+// ------------------------------------------- scanned frontier emission
+// A block-local buffer of newly produced frontier vertices and their
+// degrees. flush_scanned writes it to a queue Qn together with the queue's
+// exclusive degree scan Sn (the scanned edge offsets the next advance
+// needs), reserving both ranges with one atomicAdd on a packed counter
+// ([31:0] vertices, [63:32] edges), so queue order and scan order agree and
+// no separate scan pass is needed.
+template <int CAP>
+struct ScannedBuf {
+  int32_t out[CAP];
+  int32_t deg[CAP];
+  int32_t cnt;
+  int32_t vbase, ebase;
+  uint32_t red[33];
+};
+
+template <int CAP>
+__device__ __forceinline__ void emit_scanned(ScannedBuf<CAP> &b, bool take, int32_t v,
+                                             int32_t d) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t bal = __ballot_sync(0xffffffffu, take);
+  if (!bal) return;
+  const int leader = __ffs(bal) - 1;
+  int32_t pos = 0;
+  if (lane == leader) pos = atomicAdd(&b.cnt, __popc(bal));
+  pos = __shfl_sync(0xffffffffu, pos, leader);
+  if (take) {
+    const int32_t k = pos + __popc(bal & ((1u << lane) - 1u));
+    b.out[k] = v;
+    b.deg[k] = d;
+  }
+}
+
+// Block-uniform call; leaves b.cnt = 0.
+template <int THREADS, int CAP>
+__device__ void flush_scanned(ScannedBuf<CAP> &b, unsigned long long *packed, int32_t *Qn,
+                              int32_t *Sn) {
+  static_assert(CAP % THREADS == 0, "buffer must split evenly over the block");
+  constexpr int PER = CAP / THREADS;
+  __syncthreads();
+  const int32_t cnt = b.cnt;
+  if (cnt) {
+    const int32_t k0 = threadIdx.x * PER;
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+      if (k0 + j < cnt) local += (uint32_t)b.deg[k0 + j];
+    uint32_t total;
+    uint32_t run = block_excl_sum(local, b.red, &total);
+    if (threadIdx.x == 0) {
+      const unsigned long long old =
+          atomicAdd(packed, ((unsigned long long)total << 32) | (unsigned long long)cnt);
+      b.vbase = (int32_t)(old & 0xFFFFFFFFull);
+      b.ebase = (int32_t)(old >> 32);
+    }
+    __syncthreads();
+    const int32_t vb = b.vbase, eb = b.ebase;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int32_t k = k0 + j;
+      if (k < cnt) {
+        Qn[vb + k] = b.out[k];
+        Sn[vb + k] = eb + (int32_t)run;
+        run += (uint32_t)b.deg[k];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) b.cnt = 0;
+  __syncthreads();
+}
+
+// A plain block-local append buffer (no degrees), flushed with one
+// atomicAdd on a length counter.
+template <int CAP>
+struct AppendBuf {
+  int32_t out[CAP];
+  int32_t cnt;
+  int32_t base;
+};
+
+template <int CAP>
+__device__ __forceinline__ void emit_plain(AppendBuf<CAP> &b, bool take, int32_t v) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t bal = __ballot_sync(0xffffffffu, take);
+  if (!bal) return;
+  const int leader = __ffs(bal) - 1;
+  int32_t pos = 0;
+  if (lane == leader) pos = atomicAdd(&b.cnt, __popc(bal));
+  pos = __shfl_sync(0xffffffffu, pos, leader);
+  if (take) b.out[pos + __popc(bal & ((1u << lane) - 1u))] = v;
+}
+
+template <int THREADS, int CAP>
+__device__ void flush_plain(AppendBuf<CAP> &b, int32_t *len, int32_t *Q) {
+  __syncthreads();
+  const int32_t cnt = b.cnt;
+  if (threadIdx.x == 0 && cnt) b.base = atomicAdd(len, cnt);
+  __syncthreads();
+  for (int32_t k = threadIdx.x; k < cnt; k += THREADS) Q[b.base + k] = b.out[k];
+  __syncthreads();
+  if (threadIdx.x == 0) b.cnt = 0;
+  __syncthreads();
 }
 
 }  // namespace gr

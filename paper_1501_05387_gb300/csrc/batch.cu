@@ -344,15 +344,23 @@ __global__ void k_fill_f64(double *x, int64_t n, double val) {
 
 }  // namespace
 
-static gr_status ensure_batch_ws(gr_graph *g, bool need_bc) {
-  if (!g->batch) {
-    std::unique_ptr<BatchWorkspace> ws(new BatchWorkspace());
-    GR_TRY(ws->visit.alloc(sizeof(unsigned long long) * (size_t)g->n, "lane visit masks"));
-    GR_TRY(ws->counter.alloc(sizeof(unsigned long long) * 4, "batch counters"));
-    GR_TRY(ws->srcs.alloc(sizeof(int32_t) * 64, "batch sources"));
-    g->batch = ws.release();
-  }
-  BatchWorkspace *ws = g->batch;
+size_t batch_ws_bytes(const gr_graph *g) {
+  // visit masks + the two level masks batched BFS alternates
+  return 3 * sizeof(unsigned long long) * (size_t)g->n + 512;
+}
+
+gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out) {
+  std::unique_ptr<BatchWorkspace> ws(new BatchWorkspace());
+  GR_TRY(ws->visit.alloc(sizeof(unsigned long long) * (size_t)g->n, "lane visit masks"));
+  GR_TRY(ws->counter.alloc(sizeof(unsigned long long) * 4, "batch counters"));
+  GR_TRY(ws->srcs.alloc(sizeof(int32_t) * 64, "batch sources"));
+  *out = ws.release();
+  return GR_OK;
+}
+
+static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_bc) {
+  if (!*slot) GR_TRY(batch_ws_create(g, slot));
+  BatchWorkspace *ws = *slot;
   if (need_bc && !ws->sigma.p) {
     GR_TRY(ws->sigma.alloc(sizeof(double) * 64 * (size_t)g->n, "BC path counts"));
     GR_TRY(ws->q.alloc(sizeof(double) * 64 * (size_t)g->n, "BC dependencies"));
@@ -361,8 +369,8 @@ static gr_status ensure_batch_ws(gr_graph *g, bool need_bc) {
 }
 
 // level masks, allocated as levels appear (zeroed before use)
-static gr_status level_mask(gr_graph *g, size_t L, cudaStream_t s, unsigned long long **out) {
-  BatchWorkspace *ws = g->batch;
+static gr_status level_mask(gr_graph *g, BatchWorkspace *ws, size_t L, cudaStream_t s,
+                            unsigned long long **out) {
   while (ws->lm.size() <= L) {
     std::unique_ptr<DevMem> m(new DevMem());
     GR_TRY(m->alloc(sizeof(unsigned long long) * (size_t)g->n, "level lane masks"));
@@ -375,13 +383,12 @@ static gr_status level_mask(gr_graph *g, size_t L, cudaStream_t s, unsigned long
 
 // Forward levels of one batch of k <= 64 sources. Returns the number of
 // levels holding vertices (the sources' level included).
-static gr_status run_forward(gr_graph *g, const int32_t *h_srcs, int32_t k, int32_t *depth,
-                             bool with_sigma, cudaStream_t s, int32_t max_levels,
-                             int32_t *levels_out) {
-  BatchWorkspace *ws = g->batch;
+static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
+                             int32_t *depth, bool with_sigma, cudaStream_t s,
+                             int32_t max_levels, int32_t *levels_out) {
   const int grid = g->num_sms * 8;
   unsigned long long *lm0;
-  GR_TRY(level_mask(g, 0, s, &lm0));
+  GR_TRY(level_mask(g, ws, 0, s, &lm0));
   k_mb_init<<<grid, 256, 0, s>>>(ws->visit.as<unsigned long long>(), lm0,
                                  with_sigma ? ws->sigma.as<double>() : nullptr,
                                  with_sigma ? ws->q.as<double>() : nullptr, g->n);
@@ -400,10 +407,13 @@ static gr_status run_forward(gr_graph *g, const int32_t *h_srcs, int32_t k, int3
   a.k = k;
   a.count = ws->counter.as<unsigned long long>();
   int32_t L = 0;
+  // BC keeps every level's masks for the backward pass; BFS needs only the
+  // current and the next level, so it alternates two arrays
+  auto slot = [&](int32_t lvl) { return with_sigma ? (size_t)lvl : (size_t)(lvl & 1); };
   for (;;) {
     unsigned long long *nxt;
-    GR_TRY(level_mask(g, (size_t)L + 1, s, &nxt));
-    a.cur = ws->lm[L]->as<unsigned long long>();
+    GR_TRY(level_mask(g, ws, slot(L + 1), s, &nxt));
+    a.cur = ws->lm[slot(L)]->as<unsigned long long>();
     a.nxt = nxt;
     a.level = L;
     GR_CUDA(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
@@ -421,6 +431,14 @@ static gr_status run_forward(gr_graph *g, const int32_t *h_srcs, int32_t k, int3
   }
   *levels_out = L;
   return GR_OK;
+}
+
+// Batched BFS into a device depth array [k][n] with an explicit workspace.
+gr_status bfs_batch_run(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
+                        int32_t *depth, int32_t max_levels, cudaStream_t s) {
+  GR_CUDA(cudaMemsetAsync(depth, 0xFF, sizeof(int32_t) * (size_t)k * (size_t)g->n, s));
+  int32_t levels = 0;
+  return run_forward(g, ws, h_srcs, k, depth, false, s, max_levels, &levels);
 }
 
 }  // namespace gr
@@ -441,15 +459,13 @@ gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
   std::lock_guard<std::mutex> lock(g->mu);
   cudaStream_t s = (cudaStream_t)stream;
   GR_TRY(begin_call(g, s));
-  GR_TRY(ensure_batch_ws(g, false));
+  GR_TRY(ensure_batch_ws(g, &g->batch, false));
   void *d_depth;
   bool cp;
   const size_t bytes = sizeof(int32_t) * (size_t)k * (size_t)g->n;
   GR_TRY(resolve_output(g, 0, depth, bytes, &d_depth, &cp));
-  GR_CUDA(cudaMemsetAsync(d_depth, 0xFF, bytes, s));  // -1 = unreached
-  int32_t levels = 0;
   const int32_t max_levels = o.max_iters > 0 ? o.max_iters : g->n + 1;
-  GR_TRY(run_forward(g, srcs, k, (int32_t *)d_depth, false, s, max_levels, &levels));
+  GR_TRY(bfs_batch_run(g, g->batch, srcs, k, (int32_t *)d_depth, max_levels, s));
   if (cp) GR_CUDA(cudaMemcpyAsync(depth, d_depth, bytes, cudaMemcpyDeviceToHost, s));
   GR_TRY(end_call(g, s));
   return GR_OK;
@@ -467,7 +483,7 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
   std::lock_guard<std::mutex> lock(g->mu);
   cudaStream_t s = (cudaStream_t)stream;
   GR_TRY(begin_call(g, s));
-  GR_TRY(ensure_batch_ws(g, true));
+  GR_TRY(ensure_batch_ws(g, &g->batch, true));
   void *d_bc;
   bool cp;
   GR_TRY(resolve_output(g, 0, bc, sizeof(double) * (size_t)g->n, &d_bc, &cp));
@@ -480,7 +496,7 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
   for (int32_t b = 0; b < k; b += 64) {
     const int32_t kb = std::min<int32_t>(64, k - b);
     int32_t levels = 0;
-    GR_TRY(run_forward(g, srcs + b, kb, nullptr, true, s, max_levels, &levels));
+    GR_TRY(run_forward(g, ws, srcs + b, kb, nullptr, true, s, max_levels, &levels));
     // backward over levels levels-2 .. 1 (level levels-1 has no children;
     // level 0 holds the sources, which take no credit)
     BcBackArgs ba;

@@ -58,10 +58,14 @@ struct BfsCtl {
   int32_t policy;       // GR_DIR_*
   int32_t max_levels;
   int32_t blocks_done;  // level-kernel blocks finished (the last one ends the level)
-  int32_t barrier_gen;  // persistent-kernel grid barrier generation
-  int32_t barrier_cnt;  // persistent-kernel grid barrier arrivals
+  int32_t barrier_gen_unused;
+  int32_t barrier_cnt_unused;
   int32_t from_bitmap;  // 1: the current frontier exists only as a bitmap
   int32_t pad_;
+  // persistent kernel: next-frontier and bitmap-compaction counters, a ring
+  // of three so that one can be cleared while the others are in use
+  unsigned long long cnt3[3];
+  unsigned long long cq3[3];
   unsigned long long next_packed;  // [31:0] next frontier size, [63:32] its edges
   long long mf;         // edges leaving the current frontier
   long long mu;         // edges of still-unexplored vertices
@@ -75,8 +79,17 @@ struct BfsCtl {
   int32_t tr_q[64];
   long long tr_mf[64];
   unsigned long long tr_t[64];
+  // grid barrier of the persistent kernels: group counters, root counter
+  // and release generation, each on its own 128-byte line
+  struct alignas(128) Line {
+    int32_t v;
+  };
+  Line bar_group[16];
+  Line bar_root;
+  Line bar_gen;
 };
 constexpr int kTraceLevels = 64;
+constexpr int kBarrierGroups = 16;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -176,14 +189,19 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     c->policy = policy;
     c->max_levels = max_levels;
     c->blocks_done = 0;
-    c->barrier_gen = 0;
-    c->barrier_cnt = 0;
+    for (int i = 0; i < kBarrierGroups; ++i) c->bar_group[i].v = 0;
+    c->bar_root.v = 0;
+    c->bar_gen.v = 0;
     c->next_packed = 0ull;
     c->mf = dsrc;
     c->mu = a.m - dsrc;
     c->alpha = alpha;
     c->beta = beta;
     c->from_bitmap = 0;
+    for (int i = 0; i < 3; ++i) {
+      c->cnt3[i] = 0ull;
+      c->cq3[i] = 0ull;
+    }
     c->t_start = globaltimer();
   }
 }
@@ -223,7 +241,7 @@ __device__ __forceinline__ void emit(LevelSmem &sm, bool take, int32_t v, int32_
 
 // Write the emit buffer to the next queue with its exclusive degree scan,
 // reserving both ranges with one packed atomicAdd. Block-uniform call.
-__device__ void flush(LevelSmem &sm, BfsCtl *c, int32_t *Qn, int32_t *Sn) {
+__device__ void flush(LevelSmem &sm, unsigned long long *counter, int32_t *Qn, int32_t *Sn) {
   __syncthreads();
   const int32_t cnt = sm.cnt;
   if (cnt) {  // block-uniform
@@ -237,7 +255,7 @@ __device__ void flush(LevelSmem &sm, BfsCtl *c, int32_t *Qn, int32_t *Sn) {
     uint32_t run = block_excl_sum(local, sm.red, &total);
     if (threadIdx.x == 0) {
       const unsigned long long old = atomicAdd(
-          &c->next_packed, ((unsigned long long)total << 32) | (unsigned long long)cnt);
+          counter, ((unsigned long long)total << 32) | (unsigned long long)cnt);
       sm.vbase = (int32_t)(old & 0xFFFFFFFFull);
       sm.ebase = (int32_t)(old >> 32);
     }
@@ -259,7 +277,7 @@ __device__ void flush(LevelSmem &sm, BfsCtl *c, int32_t *Qn, int32_t *Sn) {
 }
 
 __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p, int32_t L,
-                           int32_t q) {
+                           int32_t q, int32_t q_edges, unsigned long long *counter) {
   const int32_t *Q = queue_of(a, p);
   const int32_t *S = scan_of(a, p);
   int32_t *Qn = queue_of(a, p ^ 1);
@@ -267,12 +285,13 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
   uint32_t *N = bits_of(a, L + 1);
   int32_t *depth = c->depth;
   int32_t *parent = c->parent;
-  const long long total = (long long)q + S[q];
+  const long long total = (long long)q + q_edges;
   const long long nchunks = (total + kLvChunk - 1) / kLvChunk;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kLvChunk;
     const long long d1 = min(d0 + kLvChunk, total);
-    if (threadIdx.x < 2) sm.i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
+    if (threadIdx.x < 2)
+      sm.i[threadIdx.x] = merge_count_t(S, q, q_edges, threadIdx.x ? d1 : d0);
     __syncthreads();
     const int32_t i0 = sm.i[0], i1 = sm.i[1];
     const long long j0 = d0 - i0, j1 = d1 - i1;
@@ -310,7 +329,7 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
       }
       emit(sm, won, v, dv);
     }
-    flush(sm, c, Qn, Sn);
+    flush(sm, counter, Qn, Sn);
   }
 }
 
@@ -320,7 +339,8 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
 // vertices, kPullWords per lane) so several load chains are in flight.
 constexpr int kPullWords = 2;
 
-__device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L) {
+__device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L,
+                           unsigned long long *counter) {
   const uint32_t *F = bits_of(a, L);
   uint32_t *N = bits_of(a, L + 1);
   int32_t *depth = c->depth;
@@ -416,7 +436,7 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
   // one packed atomicAdd per block: [31:0] vertices, [63:32] their edges
   const unsigned long long packed =
       block_sum((found_deg << 32) | (unsigned long long)found_cnt, (unsigned long long *)sm.red64);
-  if (threadIdx.x == 0 && packed) atomicAdd(&c->next_packed, packed);
+  if (threadIdx.x == 0 && packed) atomicAdd(counter, packed);
 }
 
 // Push level whose frontier exists only as a bitmap (the level after a
@@ -424,7 +444,8 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
 // lane-parallel, and append winners with a warp-level degree scan and one
 // packed atomicAdd per warp step. Used for the small frontiers after the
 // pull phase, where per-warp appends do not contend.
-__device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t L) {
+__device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t L,
+                                 unsigned long long *counter) {
   const uint32_t *F = bits_of(a, L);
   uint32_t *N = bits_of(a, L + 1);
   int32_t *Qn = queue_of(a, p ^ 1);
@@ -463,7 +484,7 @@ __device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t
           const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
           unsigned long long old = 0;
           if (lane == 0)
-            old = atomicAdd(&c->next_packed,
+            old = atomicAdd(counter,
                             ((unsigned long long)tot << 32) | (unsigned long long)__popc(b));
           old = __shfl_sync(0xffffffffu, old, 0);
           if (won) {
@@ -475,6 +496,22 @@ __device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t
       }
     }
   }
+}
+
+// Direction of the next level (Sec. 4.5; Beamer et al.'s rule): push ->
+// pull when the new frontier's edges exceed the unexplored edges / alpha
+// (and are not a negligible share of the graph, so that a tiny frontier
+// late in the traversal, when few edges remain unexplored, stays push);
+// pull -> push when the frontier has fallen below n / beta vertices and is
+// shrinking.
+__device__ __forceinline__ int32_t next_direction(int32_t policy, bool was_pull, int32_t qn,
+                                                  int32_t q_prev, long long mf, long long mu,
+                                                  long long m, int32_t n, float alpha,
+                                                  float beta) {
+  if (policy == GR_DIR_PUSH) return kPush;
+  if (policy == GR_DIR_PULL) return kPull;
+  if (was_pull) return ((float)qn < (float)n / beta && qn < q_prev) ? kPush : kPull;
+  return ((float)mf > (float)mu / alpha && mf * 1024 > m) ? kPull : kPush;
 }
 
 // Run by the last block of a level: install the next frontier and decide
@@ -509,15 +546,8 @@ __device__ void level_end(const BfsArgs &a, BfsCtl *c) {
     c->done = 1;
     return;
   }
-  if (c->policy == GR_DIR_PUSH) {
-    c->dir = kPush;
-  } else if (c->policy == GR_DIR_PULL) {
-    c->dir = kPull;
-  } else if (was_pull) {
-    c->dir = ((float)qn < (float)a.n / c->beta && qn < c->q_prev) ? kPush : kPull;
-  } else {
-    c->dir = ((float)mf > (float)c->mu / c->alpha) ? kPull : kPush;
-  }
+  c->dir = next_direction(c->policy, was_pull, qn, c->q_prev, mf, c->mu, a.m, a.n, c->alpha,
+                          c->beta);
 }
 
 __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
@@ -535,9 +565,9 @@ __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
       spare[w] = 0u;
   }
   __syncthreads();
-  if (dir == kPull) pull_level(a, c, sm, L);
-  else if (c->from_bitmap) push_from_bitmap(a, c, p, L);
-  else push_level(a, c, sm, p, L, q);
+  if (dir == kPull) pull_level(a, c, sm, L, &c->next_packed);
+  else if (c->from_bitmap) push_from_bitmap(a, c, p, L, &c->next_packed);
+  else push_level(a, c, sm, p, L, q, (int32_t)c->mf, &c->next_packed);
   // the last block to finish ends the level
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -550,6 +580,113 @@ __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
     c->blocks_done = 0;
     level_end(a, c);
     if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
+  }
+}
+
+// ------------------------------------------- persistent direction-optimising
+// The whole traversal in one cooperative kernel: every block runs every
+// level and the levels are separated by one bounded-spin grid barrier. After
+// the barrier each block reads the level's packed counter and recomputes the
+// same next state (direction, sizes, edge counts) in registers, so no second
+// barrier is needed to publish it. The counters form a ring of three: the
+// one a level fills, the one just read, and the one block 0 clears for the
+// next level (its last readers passed the previous barrier).
+
+__device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t &gen);
+
+// Queue + degree scan of a frontier given as a bitmap (the level after a
+// pull switches back to push): each warp takes one word per round.
+__device__ void bitmap_to_queue(const BfsArgs &a, LevelSmem &sm, const uint32_t *F, int32_t *Q,
+                                int32_t *S, unsigned long long *counter) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long per_round = (long long)gridDim.x * kLvWarps;
+  const long long rounds = (a.nwords + per_round - 1) / per_round;
+  constexpr int kRoundsPerFlush = kLvChunk / kLvThreads;
+  for (long long r = 0; r < rounds; ++r) {
+    const long long w = (r * gridDim.x + blockIdx.x) * kLvWarps + wid;
+    bool take = false;
+    int32_t v = 0, d = 0;
+    if (w < a.nwords) {
+      const uint32_t fw = F[w];
+      v = (int32_t)(w * 32 + lane);
+      take = (fw >> lane) & 1u;
+      if (take) d = a.R[v + 1] - a.R[v];
+    }
+    emit(sm, take, v, d);
+    if ((r + 1) % kRoundsPerFlush == 0 || r == rounds - 1) flush(sm, counter, Q, S);
+  }
+}
+
+constexpr int kDoBlocksPerSm = 5;
+
+__global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a) {
+  BfsCtl *c = a.ctl;
+  __shared__ LevelSmem sm;
+  const int32_t policy = c->policy, max_levels = c->max_levels;
+  const float alpha = c->alpha, beta = c->beta;
+  int32_t level = 0, parity = 0, dir = kPush, q = 1, q_prev = 0, from_bitmap = 0;
+  long long mf = c->mf, mu = c->mu;
+  int32_t gen = 0, pulls = 0;
+  if (threadIdx.x == 0) sm.cnt = 0;
+  __syncthreads();
+  for (;;) {
+    const int32_t L = level;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->cnt3[(L + 1) % 3] = 0ull;
+      c->cq3[(L + 1) % 3] = 0ull;
+    }
+    if (a.do_bitmap) {
+      uint32_t *spare = bits_of(a, L + 2);
+      for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < a.nwords;
+           w += (int64_t)gridDim.x * blockDim.x)
+        spare[w] = 0u;
+    }
+    unsigned long long *counter = &c->cnt3[L % 3];
+    if (dir == kPull) {
+      pull_level(a, c, sm, L, counter);
+    } else {
+      int32_t qq = q, qe = (int32_t)mf;
+      if (from_bitmap) {
+        bitmap_to_queue(a, sm, bits_of(a, L), queue_of(a, parity), scan_of(a, parity),
+                        &c->cq3[L % 3]);
+        if (!grid_barrier(c, gridDim.x, gen)) break;
+        const unsigned long long pk = *(volatile unsigned long long *)&c->cq3[L % 3];
+        qq = (int32_t)(pk & 0xFFFFFFFFull);
+        qe = (int32_t)(pk >> 32);
+      }
+      push_level(a, c, sm, parity, L, qq, qe, counter);
+    }
+    if (!grid_barrier(c, gridDim.x, gen)) break;
+    const unsigned long long pk = *(volatile unsigned long long *)counter;
+    const int32_t qn = (int32_t)(pk & 0xFFFFFFFFull);
+    const long long mfn = (long long)(pk >> 32);
+    const bool was_pull = dir == kPull;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && L < kTraceLevels) {
+      c->tr_dir[L] = dir;
+      c->tr_q[L] = q;
+      c->tr_mf[L] = mf;
+      c->tr_t[L] = globaltimer();
+    }
+    pulls += was_pull;
+    level += 1;
+    parity ^= 1;
+    q_prev = q;
+    q = qn;
+    mf = mfn;
+    mu -= mfn;
+    from_bitmap = was_pull;
+    bool done = qn == 0;
+    const bool overflow = !done && level >= max_levels;
+    if (done || overflow) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->level = level;
+        c->pull_levels = pulls;
+        if (overflow) c->error = kDevOverflow;
+        c->done = 1;
+      }
+      break;
+    }
+    dir = next_direction(policy, was_pull, qn, q_prev, mfn, mu, a.m, a.n, alpha, beta);
   }
 }
 
@@ -566,19 +703,34 @@ __device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t
   if (threadIdx.x == 0) {
     __threadfence();
     const int32_t my_gen = gen;
-    if (atomicAdd(&c->barrier_cnt, 1) == nblocks - 1) {
-      c->barrier_cnt = 0;
+    // arrive at this block's group counter; the group's last arriver
+    // clears it and arrives at the root; the root's last arriver releases
+    const int32_t grp = blockIdx.x % kBarrierGroups;
+    const int32_t members = (nblocks - grp + kBarrierGroups - 1) / kBarrierGroups;
+    const int32_t groups = min(nblocks, kBarrierGroups);
+    bool release = false;
+    if (atomicAdd(&c->bar_group[grp].v, 1) == members - 1) {
+      c->bar_group[grp].v = 0;
       __threadfence();
-      atomicExch(&c->barrier_gen, my_gen + 1);
+      if (atomicAdd(&c->bar_root.v, 1) == groups - 1) {
+        c->bar_root.v = 0;
+        __threadfence();
+        release = true;
+      }
+    }
+    if (release) {
+      atomicExch(&c->bar_gen.v, my_gen + 1);
     } else {
       int64_t spins = 0;
-      while (*(volatile int32_t *)&c->barrier_gen == my_gen) {
+      unsigned ns = 32;
+      while (*(volatile int32_t *)&c->bar_gen.v == my_gen) {
         if (++spins > kSpinLimit) {
           atomicExch(&c->error, kDevTimeout);
           ok = false;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(ns);
+        ns = ns < 256 ? ns * 2 : 256;
       }
     }
     __threadfence();
@@ -660,8 +812,13 @@ __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
 }  // namespace
 
 // ---------------------------------------------------------------- host
-static gr_status ensure_bfs_ws(gr_graph *g, cudaStream_t s) {
-  if (g->bfs) return GR_OK;
+size_t bfs_ws_bytes(const gr_graph *g) {
+  const size_t n = (size_t)g->n;
+  return 2 * sizeof(int32_t) * (n + 1) + 2 * sizeof(int32_t) * (n + 2) +
+         4 * sizeof(uint32_t) * (size_t)g->nwords + sizeof(BfsCtl);
+}
+
+gr_status bfs_ws_create(gr_graph *g, cudaStream_t s, BfsWorkspace **out) {
   std::unique_ptr<BfsWorkspace> ws(new BfsWorkspace());
   const size_t n = (size_t)g->n;
   for (int i = 0; i < 2; ++i) {
@@ -675,12 +832,11 @@ static gr_status ensure_bfs_ws(gr_graph *g, cudaStream_t s) {
   GR_TRY(ws->h_ctl.alloc(sizeof(BfsCtl), "BFS control mirror"));
   GR_CUDA(cudaMemsetAsync(ws->ctl.p, 0, sizeof(BfsCtl), s));
   GR_CUDA(cudaStreamSynchronize(s));
-  g->bfs = ws.release();
+  *out = ws.release();
   return GR_OK;
 }
 
-static BfsArgs make_args(gr_graph *g, int32_t do_bitmap) {
-  BfsWorkspace *ws = g->bfs;
+static BfsArgs make_args(gr_graph *g, BfsWorkspace *ws, int32_t do_bitmap) {
   BfsArgs a;
   a.R = g->row_off.as<int32_t>();
   a.C = g->col.as<int32_t>();
@@ -708,8 +864,7 @@ static gr_status enqueue_level(gr_graph *g, const BfsArgs &a, cudaStream_t s,
   return GR_OK;
 }
 
-static gr_status build_level_graph(gr_graph *g, int32_t do_bitmap) {
-  BfsWorkspace *ws = g->bfs;
+static gr_status build_level_graph(gr_graph *g, BfsWorkspace *ws, int32_t do_bitmap) {
   if (ws->exec[do_bitmap]) return GR_OK;
   cudaGraph_t graph;
   GR_CUDA(cudaGraphCreate(&graph, 0));
@@ -727,7 +882,7 @@ static gr_status build_level_graph(gr_graph *g, int32_t do_bitmap) {
   GR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   GR_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  gr_status st = enqueue_level(g, make_args(g, do_bitmap), cs, h, 1);
+  gr_status st = enqueue_level(g, make_args(g, ws, do_bitmap), cs, h, 1);
   cudaGraph_t captured;
   cudaError_t e = cudaStreamEndCapture(cs, &captured);
   cudaStreamDestroy(cs);
@@ -743,17 +898,81 @@ static gr_status build_level_graph(gr_graph *g, int32_t do_bitmap) {
 static int32_t resolve_policy(const gr_graph *g, const gr_opts &o) {
   if (o.direction == GR_DIR_PUSH) return GR_DIR_PUSH;
   if (o.direction == GR_DIR_PULL) return GR_DIR_PULL;
-  return g->symmetric ? GR_DIR_AUTO : GR_DIR_PUSH;
+  if (!g->symmetric) return GR_DIR_PUSH;
+  return g->tuned_direction == GR_DIR_PUSH ? GR_DIR_PUSH : GR_DIR_AUTO;
 }
 
-// mode AUTO: graphs whose traversals are long chains of small frontiers
-// (low maximum degree, large n) run the persistent kernel; others the
-// device-side while loop.
+// mode AUTO: the tuned mode of the graph (see gr_autotune), else the
+// persistent kernel (one launch, one grid barrier per level)
 static int32_t resolve_mode(const gr_graph *g, const gr_opts &o, int32_t policy) {
+  (void)policy;
   if (o.mode != GR_MODE_AUTO) return o.mode;
-  if (policy == GR_DIR_PUSH && g->max_degree <= 32 && g->n >= (1 << 16))
-    return GR_MODE_PERSISTENT;
-  return GR_MODE_GRAPH;
+  if (g->tuned_mode != GR_MODE_AUTO) return g->tuned_mode;
+  return GR_MODE_PERSISTENT;
+}
+
+gr_status bfs_check(const gr_graph *g, int32_t src, const gr_opts &o) {
+  if (src < 0 || src >= g->n) return fail(GR_EINVAL, "source out of range");
+  if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL)
+    return fail(GR_EINVAL, "unknown direction policy");
+  if (o.mode < GR_MODE_AUTO || o.mode > GR_MODE_PERSISTENT)
+    return fail(GR_EINVAL, "unknown mode");
+  if (o.direction == GR_DIR_PULL && !g->symmetric)
+    return fail(GR_EINVAL, "pull traversal needs a symmetric CSR (in-neighbours = out-neighbours)");
+  if (o.alpha < 0.f || o.beta < 0.f) return fail(GR_EINVAL, "alpha/beta must be >= 0");
+  return GR_OK;
+}
+
+// BFS into device outputs with an explicit workspace (no locking, no
+// staging): the public gr_bfs and the query server both call this.
+gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, int32_t *parent,
+                  const gr_opts &o, cudaStream_t s) {
+  const int32_t policy = resolve_policy(g, o);
+  const int32_t mode = resolve_mode(g, o, policy);
+  const int32_t do_bitmap = policy != GR_DIR_PUSH;
+  const float alpha = o.alpha > 0.f ? o.alpha : g->tuned_alpha;
+  const float beta = o.beta > 0.f ? o.beta : g->tuned_beta;
+  int32_t max_levels = g->n + 1;
+  if (o.max_iters > 0) max_levels = std::min(max_levels, o.max_iters);
+  BfsArgs a = make_args(g, ws, do_bitmap);
+  k_bfs_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, depth, parent, policy, alpha, beta,
+                                            max_levels, (g->symmetric && do_bitmap) ? 1 : 0);
+  GR_CUDA(cudaGetLastError());
+  if (mode == GR_MODE_GRAPH) {
+    GR_TRY(build_level_graph(g, ws, do_bitmap));
+    GR_CUDA(cudaGraphLaunch(ws->exec[do_bitmap], s));
+  } else if (mode == GR_MODE_PERSISTENT) {
+    int per_sm = 0;
+    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_do, kLvThreads, 0));
+    int bps = std::min(per_sm, kDoBlocksPerSm);
+    const int32_t want = o.block > 0 ? o.block : g->tuned_blocks_per_sm;
+    if (want > 0) bps = std::min(bps, want);
+    const int blocks = std::max(1, bps) * g->num_sms;
+    void *args[] = {&a};
+    GR_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs_do, blocks, kLvThreads, args, 0, s));
+  } else {
+    // host-driven: enqueue batches of levels, then check the done flag
+    BfsCtl *h = ws->h_ctl.as<BfsCtl>();
+    int32_t levels_enqueued = 0;
+    int32_t batch = 4;
+    for (;;) {
+      for (int i = 0; i < batch; ++i) GR_TRY(enqueue_level(g, a, s, 0, 0));
+      levels_enqueued += batch;
+      GR_CUDA(cudaMemcpyAsync(h, ws->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost, s));
+      GR_CUDA(cudaStreamSynchronize(s));
+      if (h->done || levels_enqueued > max_levels) break;
+      batch = std::min(batch * 2, 64);
+    }
+  }
+  return GR_OK;
+}
+
+gr_status bfs_read_ctl_error(BfsWorkspace *ws) {
+  BfsCtl h;
+  GR_CUDA(cudaMemcpy(&h, ws->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost));
+  if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
+  if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "level limit reached");
+  return GR_OK;
 }
 
 }  // namespace gr
@@ -766,66 +985,18 @@ gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                  const gr_opts *opts, void *stream) {
   clear_error();
   if (!g) return fail(GR_EINVAL, "graph must not be NULL");
-  if (src < 0 || src >= g->n) return fail(GR_EINVAL, "source out of range");
   if (!depth) return fail(GR_EINVAL, "depth must not be NULL");
-  const gr_opts &o = opts ? *opts : default_opts();
-  if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL)
-    return fail(GR_EINVAL, "unknown direction policy");
-  if (o.mode < GR_MODE_AUTO || o.mode > GR_MODE_PERSISTENT)
-    return fail(GR_EINVAL, "unknown mode");
-  if (o.direction == GR_DIR_PULL && !g->symmetric)
-    return fail(GR_EINVAL, "pull traversal needs a symmetric CSR (in-neighbours = out-neighbours)");
-  if (o.alpha < 0.f || o.beta < 0.f) return fail(GR_EINVAL, "alpha/beta must be >= 0");
+  GR_TRY(bfs_check(g, src, opts ? *opts : default_opts()));
   std::lock_guard<std::mutex> lock(g->mu);
   cudaStream_t s = (cudaStream_t)stream;
   GR_TRY(begin_call(g, s));
-  GR_TRY(ensure_bfs_ws(g, s));
-  const int32_t policy = resolve_policy(g, o);
-  const int32_t mode = resolve_mode(g, o, policy);
-  if (mode == GR_MODE_PERSISTENT && policy != GR_DIR_PUSH)
-    return fail(GR_EINVAL, "the persistent BFS kernel runs push levels only");
-  const int32_t do_bitmap = policy != GR_DIR_PUSH;
-  const float alpha = o.alpha > 0.f ? o.alpha : 14.f;
-  const float beta = o.beta > 0.f ? o.beta : 24.f;
-  int32_t max_levels = g->n + 1;
-  if (o.max_iters > 0) max_levels = std::min(max_levels, o.max_iters);
-
+  if (!g->bfs) GR_TRY(bfs_ws_create(g, s, &g->bfs));
   void *d_depth, *d_parent;
   bool cp_depth, cp_parent;
   GR_TRY(resolve_output(g, 0, depth, sizeof(int32_t) * (size_t)g->n, &d_depth, &cp_depth));
   GR_TRY(resolve_output(g, 1, parent, sizeof(int32_t) * (size_t)g->n, &d_parent, &cp_parent));
-
-  BfsArgs a = make_args(g, do_bitmap);
-  k_bfs_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, (int32_t *)d_depth, (int32_t *)d_parent,
-                                            policy, alpha, beta, max_levels,
-                                            (g->symmetric && do_bitmap) ? 1 : 0);
-  GR_CUDA(cudaGetLastError());
-
-  if (mode == GR_MODE_GRAPH) {
-    GR_TRY(build_level_graph(g, do_bitmap));
-    GR_CUDA(cudaGraphLaunch(g->bfs->exec[do_bitmap], s));
-  } else if (mode == GR_MODE_PERSISTENT) {
-    int per_sm = 0;
-    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent,
-                                                          kPersThreads, 0));
-    int blocks = std::max(1, std::min(per_sm, 4)) * g->num_sms;
-    void *args[] = {&a};
-    GR_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs_persistent, blocks, kPersThreads,
-                                        args, 0, s));
-  } else {
-    // host-driven: enqueue batches of levels, then check the done flag
-    BfsCtl *h = g->bfs->h_ctl.as<BfsCtl>();
-    int32_t levels_enqueued = 0;
-    int32_t batch = 4;
-    for (;;) {
-      for (int i = 0; i < batch; ++i) GR_TRY(enqueue_level(g, a, s, 0, 0));
-      levels_enqueued += batch;
-      GR_CUDA(cudaMemcpyAsync(h, g->bfs->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost, s));
-      GR_CUDA(cudaStreamSynchronize(s));
-      if (h->done || levels_enqueued > max_levels) break;
-      batch = std::min(batch * 2, 64);
-    }
-  }
+  GR_TRY(bfs_run(g, g->bfs, src, (int32_t *)d_depth, (int32_t *)d_parent,
+                 opts ? *opts : default_opts(), s));
   if (cp_depth)
     GR_CUDA(cudaMemcpyAsync(depth, d_depth, sizeof(int32_t) * (size_t)g->n,
                             cudaMemcpyDeviceToHost, s));
@@ -885,7 +1056,7 @@ namespace gr {
 namespace {
 
 constexpr int32_t kNoAllocMaxVertices = 1 << 20;
-constexpr size_t kNoAllocCtlBytes = 2048;  // BfsCtl, padded to 2 KB
+constexpr size_t kNoAllocCtlBytes = 8192;  // BfsCtl, padded to 8 KB
 constexpr size_t kNoAllocQueueBytes = sizeof(int32_t) * ((size_t)kNoAllocMaxVertices + 1);
 constexpr size_t kNoAllocQueueBytesAligned = (kNoAllocQueueBytes + 255) & ~size_t(255);
 constexpr size_t kNoAllocVisitedBytes = sizeof(uint32_t) * (kNoAllocMaxVertices / 32);

@@ -96,6 +96,30 @@ __global__ void k_cc_jump(int32_t *label, int32_t n, int32_t *num_roots) {
 
 }  // namespace
 
+size_t cc_ws_bytes(const gr_graph *) { return sizeof(int32_t) * 4; }
+
+gr_status cc_ws_create(gr_graph *, CcWorkspace **out) {
+  std::unique_ptr<CcWorkspace> ws(new CcWorkspace());
+  GR_TRY(ws->counter.alloc(sizeof(int32_t) * 4, "CC counters"));
+  *out = ws.release();
+  return GR_OK;
+}
+
+// CC into a device label array with an explicit workspace; the component
+// count is left in the workspace counter (cc_count reads it).
+gr_status cc_run(gr_graph *g, CcWorkspace *ws, int32_t *label, cudaStream_t s) {
+  int32_t *cnt = ws->counter.as<int32_t>();
+  const int grid = g->num_sms * 8;
+  GR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), s));
+  k_cc_init<<<grid, 256, 0, s>>>(label, g->n);
+  k_cc_hook<<<g->num_sms * 4, kCcThreads, 0, s>>>(g->row_off.as<int32_t>(),
+                                                  g->col.as<int32_t>(), g->n, label,
+                                                  g->symmetric ? 1 : 0);
+  k_cc_jump<<<grid, 256, 0, s>>>(label, g->n, cnt);
+  GR_CUDA(cudaGetLastError());
+  return GR_OK;
+}
+
 }  // namespace gr
 
 using namespace gr;
@@ -111,30 +135,17 @@ gr_status gr_cc(gr_graph *g, int32_t *label, int32_t *num_components, const gr_o
   std::lock_guard<std::mutex> lock(g->mu);
   cudaStream_t s = (cudaStream_t)stream;
   GR_TRY(begin_call(g, s));
-  if (!g->cc) {
-    std::unique_ptr<CcWorkspace> ws(new CcWorkspace());
-    GR_TRY(ws->counter.alloc(sizeof(int32_t) * 4, "CC counters"));
-    g->cc = ws.release();
-  }
+  if (!g->cc) GR_TRY(cc_ws_create(g, &g->cc));
   void *d_label;
   bool cp_label;
   GR_TRY(resolve_output(g, 0, label, sizeof(int32_t) * (size_t)g->n, &d_label, &cp_label));
-  int32_t *L = (int32_t *)d_label;
-  int32_t *cnt = g->cc->counter.as<int32_t>();
-  const int grid = g->num_sms * 8;
-  GR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), s));
-  k_cc_init<<<grid, 256, 0, s>>>(L, g->n);
-  k_cc_hook<<<g->num_sms * 4, kCcThreads, 0, s>>>(g->row_off.as<int32_t>(),
-                                                  g->col.as<int32_t>(), g->n, L,
-                                                  g->symmetric ? 1 : 0);
-  k_cc_jump<<<grid, 256, 0, s>>>(L, g->n, cnt);
-  GR_CUDA(cudaGetLastError());
+  GR_TRY(cc_run(g, g->cc, (int32_t *)d_label, s));
   if (cp_label)
     GR_CUDA(cudaMemcpyAsync(label, d_label, sizeof(int32_t) * (size_t)g->n,
                             cudaMemcpyDeviceToHost, s));
   if (num_components) {
     int32_t h = 0;
-    GR_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GR_CUDA(cudaMemcpyAsync(&h, g->cc->counter.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     GR_CUDA(cudaStreamSynchronize(s));
     *num_components = h;
   }

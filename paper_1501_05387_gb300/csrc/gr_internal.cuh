@@ -92,6 +92,12 @@ struct gr_graph {
   bool rows_sorted = false;
   bool has_weights = false;
   uint32_t sssp_delta = 1;    // tuned near/far bucket width
+  float tuned_alpha = 14.f;   // push -> pull threshold (see gr_autotune)
+  float tuned_beta = 24.f;    // pull -> push threshold
+  int32_t tuned_mode = GR_MODE_AUTO;
+  int32_t tuned_direction = GR_DIR_AUTO;  // GR_DIR_PUSH: never pull
+  int32_t tuned_blocks_per_sm = 0;  // persistent BFS grid (0: all resident)
+  double tuned_bfs_ms = 0.0, tuned_sssp_ms = 0.0;  // measured by gr_autotune
   double mean_weight = 0.0;
 
   std::mutex mu;  // serialises host-side enqueueing on this graph
@@ -124,6 +130,30 @@ gr_status resolve_output(gr_graph *g, int slot, void *user, size_t bytes,
                          void **dev, bool *needs_copy);
 
 const gr_opts &default_opts();
+
+// Internal primitive entry points with explicit workspaces (device outputs,
+// no locking, no staging); used by the C ABI wrappers and the server.
+gr_status bfs_ws_create(gr_graph *g, cudaStream_t s, BfsWorkspace **out);
+size_t bfs_ws_bytes(const gr_graph *g);
+gr_status bfs_check(const gr_graph *g, int32_t src, const gr_opts &o);
+gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, int32_t *parent,
+                  const gr_opts &o, cudaStream_t s);
+gr_status bfs_read_ctl_error(BfsWorkspace *ws);
+gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out);
+size_t sssp_ws_bytes(const gr_graph *g);
+gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o);
+gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, int32_t *pred,
+                   const gr_opts &o, cudaStream_t s);
+gr_status cc_ws_create(gr_graph *g, CcWorkspace **out);
+size_t cc_ws_bytes(const gr_graph *g);
+gr_status cc_run(gr_graph *g, CcWorkspace *ws, int32_t *label, cudaStream_t s);
+gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out);
+size_t batch_ws_bytes(const gr_graph *g);
+gr_status bfs_batch_run(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
+                        int32_t *depth, int32_t max_levels, cudaStream_t s);
+
+// Degree-statistics prior of the tuned settings (set at graph creation).
+void tune_prior(gr_graph *g);
 
 // Per-primitive scratch release, defined next to each primitive.
 void free_bfs(BfsWorkspace *);

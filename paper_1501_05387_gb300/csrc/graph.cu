@@ -322,6 +322,7 @@ gr_status gr_graph_create(int32_t n, int64_t m, const int32_t *row_off,
     double d = 2.0 * g->mean_weight;
     g->sssp_delta = (uint32_t)std::max(1.0, std::min(d, 4.0e9));
   }
+  tune_prior(g.get());
   *out = g.release();
   return GR_OK;
 }

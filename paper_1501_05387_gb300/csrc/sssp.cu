@@ -4,21 +4,25 @@
 // Alg. 1 initialises labels to infinity and label[root] = 0, then loops
 // advance (UpdateLabel = atomicMin relaxation), filter (RemoveRedundant, an
 // output-queue stamp per vertex) and the priority-queue split until the
-// frontier is empty. Here one iteration of the device-side loop is:
+// frontier is empty. Here one iteration of the device-side loop is ONE
+// kernel, k_sssp_iter, in one of two modes chosen on the device:
 //
-//   k_sssp_scan   degree scan of the near frontier (skipped when empty)
-//   k_sssp_relax  load-balanced advance; per edge new = dist[u] + w(e),
-//                 atomicMin on dist[v]; an improved v goes to the next near
-//                 frontier if new < T (deduplicated by a per-iteration stamp,
-//                 the RemoveRedundant filter) and to the far pile otherwise
-//                 (deduplicated by a per-phase stamp)
-//   k_sssp_split  only when the near frontier is empty: the far pile is
-//                 split by the raised threshold into near and far; entries
-//                 whose distance fell below the old threshold were already
-//                 expanded and are dropped
-//   k_sssp_end    one thread: swaps buffers, raises T (jumping to the
-//                 bucket of the smallest far distance when the next bucket
-//                 would be empty), ends the loop when both piles are empty
+//   relax  load-balanced advance over the near frontier (merge-path chunks
+//          over its vertex ends and edge ranks, Sec. 4.4); per edge
+//          new = dist[u] + w(e), atomicMin on dist[v]; an improved v joins
+//          the next near frontier if new < T (deduplicated by a
+//          per-iteration stamp, the RemoveRedundant filter) and the far pile
+//          otherwise (deduplicated by a per-phase stamp)
+//   split  only when the near frontier is empty: the far pile is split by
+//          the raised threshold into near and far; entries whose distance
+//          fell below the old threshold were already expanded and are
+//          dropped
+//
+// New near vertices are emitted with their degree scan (one packed atomic
+// per block), so no scan pass separates two iterations. The last block of
+// an iteration swaps the buffers, raises T (jumping to the bucket of the
+// smallest far distance when the next bucket would be empty) and ends the
+// loop when both piles are empty.
 //
 // T starts at delta and grows by delta per phase (delta = UINT32_MAX: one
 // bucket, i.e. plain frontier relaxation). Distances do not depend on delta.
@@ -41,22 +45,22 @@ struct SsspCtl {
   int32_t near_parity;   // which near buffer holds the current frontier
   int32_t far_parity;    // which far buffer holds the current pile
   int32_t near_len;
-  int32_t near_next_len;  // atomic
   int32_t far_len;        // atomic (relax appends to the current pile)
   int32_t far_next_len;   // atomic (split output)
-  int32_t tile_ctr;
   int32_t done;
   int32_t error;
   int32_t iter;           // iteration id, also the near-frontier stamp
   int32_t far_epoch;      // far-pile stamp
   int32_t max_iters;
   int32_t phases;         // number of splits
-  uint32_t epoch;         // scan epoch (never reset)
+  int32_t blocks_done;    // blocks finished (the last one ends the iteration)
   uint32_t far_min;       // lower bound of far-pile distances (atomicMin)
   uint32_t far_min_next;  // min distance of entries kept by a split
+  unsigned long long near_next_packed;  // [31:0] next near size, [63:32] its edges
   unsigned long long T;   // near criterion: dist < T
   unsigned long long T_old;
   unsigned long long delta;
+  long long near_edges;   // edges of the current near frontier
   long long relaxations;  // edges expanded (statistics)
 };
 
@@ -66,19 +70,19 @@ struct SsspArgs {
   const uint32_t *W;
   int32_t n;
   int32_t *nearq[2];
+  int32_t *nearS[2];
   int32_t *farq[2];
-  int32_t *scan;
   int32_t *stamp;
   int32_t *far_stamp;
-  unsigned long long *status;
   SsspCtl *ctl;
 };
 
-constexpr int kSsspScanThreads = 512, kSsspScanItems = 4;
-constexpr int kSsspThreads = 256, kSsspItems = 8;
+constexpr int kSsspThreads = 256, kSsspItems = 4;
+constexpr int kSsspChunk = kSsspThreads * kSsspItems;
+constexpr int kSsspBlocksPerSm = 5;
 
 struct SsspWorkspace {
-  DevMem nearq[2], farq[2], scan, stamp, far_stamp, status, ctl;
+  DevMem nearq[2], nearS[2], farq[2], stamp, far_stamp, ctl;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   ~SsspWorkspace() {
@@ -104,7 +108,10 @@ __global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pr
   }
   if (tid == 0) {
     SsspCtl *c = a.ctl;
+    const int32_t dsrc = a.R[src + 1] - a.R[src];
     a.nearq[0][0] = src;
+    a.nearS[0][0] = 0;
+    a.nearS[0][1] = dsrc;
     c->dist = dist;
     c->pred = pred;
     c->src = src;
@@ -112,111 +119,144 @@ __global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pr
     c->near_parity = 0;
     c->far_parity = 0;
     c->near_len = 1;
-    c->near_next_len = 0;
     c->far_len = 0;
     c->far_next_len = 0;
-    c->tile_ctr = 0;
     c->done = 0;
     c->error = kDevOk;
     c->iter = 0;
     c->far_epoch = 0;
     c->max_iters = max_iters;
     c->phases = 0;
+    c->blocks_done = 0;
     c->far_min = 0xFFFFFFFFu;
     c->far_min_next = 0xFFFFFFFFu;
+    c->near_next_packed = 0ull;
     c->delta = delta;
     c->T = delta;
     c->T_old = 0;
+    c->near_edges = dsrc;
     c->relaxations = 0;
   }
 }
 
-__global__ void __launch_bounds__(kSsspScanThreads) k_sssp_scan(SsspArgs a) {
-  SsspCtl *c = a.ctl;
-  if (c->done || c->error || c->mode != kSsspRelax) return;
-  ScanState st{a.status, &c->tile_ctr, &c->error, c->epoch};
-  long long total;
-  if (frontier_degree_scan<kSsspScanThreads, kSsspScanItems>(
-          a.R, pick(a.nearq, c->near_parity), c->near_len, a.scan, st, &total))
-    c->relaxations += total;
-}
-
-struct RelaxF {
-  const uint32_t *W;
-  uint32_t *dist;
-  int32_t *stamp;
-  int32_t *far_stamp;
-  uint32_t *far_min;
-  unsigned long long T;
-  int32_t iter;
-  int32_t far_epoch;
-  __device__ __forceinline__ int operator()(int32_t u, int32_t v, int32_t e) const {
-    const unsigned long long nd = (unsigned long long)dist[u] + W[e];
-    if (nd >= 0xFFFFFFFFull) return 0;  // not representable: no path improvement
-    const uint32_t nd32 = (uint32_t)nd;
-    if (nd32 >= dist[v]) return 0;  // plain-load cull
-    const uint32_t old = atomicMin(dist + v, nd32);
-    if (nd32 >= old) return 0;
-    if (nd < T) return atomicExch(stamp + v, iter) != iter ? 1 : 0;
-    atomicMin(far_min, nd32);
-    return atomicExch(far_stamp + v, far_epoch) != far_epoch ? 2 : 0;
-  }
+struct SsspSmem {
+  int32_t off[kSsspChunk + 1];
+  int32_t u[kSsspChunk + 1];
+  int32_t row[kSsspChunk + 1];
+  ScannedBuf<kSsspChunk> nearb;
+  AppendBuf<kSsspChunk> farb;
+  int32_t i[2];
+  int32_t last;
 };
 
-__global__ void __launch_bounds__(kSsspThreads) k_sssp_relax(SsspArgs a) {
-  SsspCtl *c = a.ctl;
-  if (c->done || c->error || c->mode != kSsspRelax) return;
+__device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   const int32_t np = c->near_parity;
-  RelaxF f{a.W, c->dist, a.stamp, a.far_stamp, &c->far_min, c->T, c->iter, c->far_epoch};
-  lb_advance<kSsspThreads, kSsspItems, 2>(a.R, a.C, pick(a.nearq, np), c->near_len, a.scan, f,
-                                          pick(a.nearq, np ^ 1), &c->near_next_len,
-                                          pick(a.farq, c->far_parity), &c->far_len);
+  const int32_t *Q = pick(a.nearq, np);
+  const int32_t *S = pick(a.nearS, np);
+  int32_t *Qn = pick(a.nearq, np ^ 1);
+  int32_t *Sn = pick(a.nearS, np ^ 1);
+  int32_t *F = pick(a.farq, c->far_parity);
+  const int32_t q = c->near_len;
+  const unsigned long long T = c->T;
+  const int32_t iter = c->iter, epoch = c->far_epoch;
+  uint32_t *dist = c->dist;
+  const long long total = (long long)q + S[q];
+  const long long nchunks = (total + kSsspChunk - 1) / kSsspChunk;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * kSsspChunk;
+    const long long d1 = min(d0 + kSsspChunk, total);
+    if (threadIdx.x < 2) sm.i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const int32_t i0 = sm.i[0], i1 = sm.i[1];
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += kSsspThreads) {
+      const int32_t u = Q[i0 + k];
+      sm.off[k] = S[i0 + k];
+      sm.u[k] = u;
+      sm.row[k] = a.R[u];
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += kSsspThreads) {
+      const int32_t k = kb + threadIdx.x;
+      int code = 0;
+      int32_t v = 0, dv = 0;
+      if (k < ne) {
+        const int32_t er = (int32_t)(j0 + k);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (sm.off[mid] <= er) lo = mid;
+          else hi = mid - 1;
+        }
+        const int32_t e = sm.row[lo] + (er - sm.off[lo]);
+        v = a.C[e];
+        const unsigned long long nd = (unsigned long long)dist[sm.u[lo]] + a.W[e];
+        if (nd < 0xFFFFFFFFull) {  // else not representable: no improvement
+          const uint32_t nd32 = (uint32_t)nd;
+          if (nd32 < dist[v]) {  // plain-load cull
+            const uint32_t old = atomicMin(dist + v, nd32);
+            if (nd32 < old) {
+              if (nd < T) {
+                if (atomicExch(a.stamp + v, iter) != iter) {
+                  code = 1;
+                  dv = a.R[v + 1] - a.R[v];
+                }
+              } else {
+                atomicMin(&c->far_min, nd32);
+                if (atomicExch(a.far_stamp + v, epoch) != epoch) code = 2;
+              }
+            }
+          }
+        }
+      }
+      emit_scanned(sm.nearb, code == 1, v, dv);
+      emit_plain(sm.farb, code == 2, v);
+    }
+    flush_scanned<kSsspThreads>(sm.nearb, &c->near_next_packed, Qn, Sn);
+    flush_plain<kSsspThreads>(sm.farb, &c->far_len, F);
+  }
 }
 
-__global__ void __launch_bounds__(kSsspThreads) k_sssp_split(SsspArgs a) {
-  SsspCtl *c = a.ctl;
-  if (c->done || c->error || c->mode != kSsspSplit) return;
+__device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   const int32_t *F = pick(a.farq, c->far_parity);
   int32_t *Fn = pick(a.farq, c->far_parity ^ 1);
-  int32_t *Nn = pick(a.nearq, c->near_parity ^ 1);
+  const int32_t np = c->near_parity;
+  int32_t *Qn = pick(a.nearq, np ^ 1);
+  int32_t *Sn = pick(a.nearS, np ^ 1);
   const int32_t len = c->far_len;
   const unsigned long long T = c->T, T_old = c->T_old;
   const int32_t iter = c->iter, epoch = c->far_epoch + 1;
   const uint32_t *dist = c->dist;
-  __shared__ int32_t s_out0[kSsspThreads], s_out1[kSsspThreads];
-  __shared__ int32_t s_cnt[2], s_base[2];
   uint32_t local_min = 0xFFFFFFFFu;
-  const int64_t rounds = (len + (int64_t)gridDim.x * kSsspThreads - 1) /
-                         ((int64_t)gridDim.x * kSsspThreads);
-  for (int64_t r = 0; r < rounds; ++r) {
-    const int64_t i = (r * gridDim.x + blockIdx.x) * kSsspThreads + threadIdx.x;
-    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
+  const long long per_round = (long long)gridDim.x * kSsspThreads;
+  const long long rounds = (len + per_round - 1) / per_round;
+  for (long long r = 0; r < rounds; ++r) {
+    const long long i = (r * gridDim.x + blockIdx.x) * kSsspThreads + threadIdx.x;
     int code = 0;
-    int32_t v = 0;
+    int32_t v = 0, dv = 0;
     if (i < len) {
       v = F[i];
       const uint32_t d = dist[v];
       if ((unsigned long long)d < T_old) {
         code = 0;  // stale: improved below the old threshold and expanded
       } else if ((unsigned long long)d < T) {
-        code = atomicExch(a.stamp + v, iter) != iter ? 1 : 0;
+        if (atomicExch(a.stamp + v, iter) != iter) {
+          code = 1;
+          dv = a.R[v + 1] - a.R[v];
+        }
       } else {
         local_min = min(local_min, d);
         code = atomicExch(a.far_stamp + v, epoch) != epoch ? 2 : 0;
       }
     }
-    warp_append(code, v, s_out0, &s_cnt[0], s_out1, &s_cnt[1]);
-    __syncthreads();
-    if (threadIdx.x < 2) {
-      const int32_t cnt = s_cnt[threadIdx.x];
-      s_base[threadIdx.x] =
-          cnt ? atomicAdd(threadIdx.x ? &c->far_next_len : &c->near_next_len, cnt) : 0;
+    emit_scanned(sm.nearb, code == 1, v, dv);
+    emit_plain(sm.farb, code == 2, v);
+    if ((r + 1) % (kSsspChunk / kSsspThreads) == 0 || r == rounds - 1) {
+      flush_scanned<kSsspThreads>(sm.nearb, &c->near_next_packed, Qn, Sn);
+      flush_plain<kSsspThreads>(sm.farb, &c->far_next_len, Fn);
     }
-    __syncthreads();
-    for (int32_t k = threadIdx.x; k < s_cnt[0]; k += kSsspThreads) Nn[s_base[0] + k] = s_out0[k];
-    for (int32_t k = threadIdx.x; k < s_cnt[1]; k += kSsspThreads) Fn[s_base[1] + k] = s_out1[k];
-    __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
   if ((threadIdx.x & 31) == 0 && local_min != 0xFFFFFFFFu) atomicMin(&c->far_min_next, local_min);
@@ -226,36 +266,38 @@ __device__ __forceinline__ unsigned long long bucket_end(uint32_t d, unsigned lo
   return ((unsigned long long)d / delta + 1ull) * delta;
 }
 
-__device__ __forceinline__ void sssp_end_body(SsspCtl *c) {
-  if (c->done) return;
+// Run by the last block of an iteration.
+__device__ void sssp_end(const SsspArgs &a, SsspCtl *c) {
   if (c->error) {
     c->done = 1;
     return;
   }
+  const unsigned long long packed = c->near_next_packed;
+  const int32_t qn = (int32_t)(packed & 0xFFFFFFFFull);
+  const long long en = (long long)(packed >> 32);
   if (c->mode == kSsspRelax) {
-    c->near_len = c->near_next_len;
-    c->near_parity ^= 1;
+    c->relaxations += c->near_edges;
   } else {
-    c->near_len = c->near_next_len;
-    c->near_parity ^= 1;
     c->far_len = c->far_next_len;
     c->far_parity ^= 1;
     c->far_epoch += 1;
     c->far_min = c->far_min_next;
     c->phases += 1;
   }
-  c->near_next_len = 0;
+  c->near_len = qn;
+  c->near_edges = en;
+  c->near_parity ^= 1;
+  pick(a.nearS, c->near_parity)[qn] = (int32_t)en;
+  c->near_next_packed = 0ull;
   c->far_next_len = 0;
   c->far_min_next = 0xFFFFFFFFu;
-  c->tile_ctr = 0;
-  c->epoch += 1;
   c->iter += 1;
   if (c->near_len > 0) {
     c->mode = kSsspRelax;
   } else if (c->far_len > 0) {
     c->mode = kSsspSplit;
     c->T_old = c->T;
-    unsigned long long t = c->T + c->delta;
+    const unsigned long long t = c->T + c->delta;
     const unsigned long long j = bucket_end(c->far_min, c->delta);
     c->T = t > j ? t : j;
   } else {
@@ -268,10 +310,30 @@ __device__ __forceinline__ void sssp_end_body(SsspCtl *c) {
   }
 }
 
-__global__ void k_sssp_end(SsspArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
-  if (threadIdx.x != 0) return;
-  sssp_end_body(a.ctl);
-  if (use_cond) cudaGraphSetConditional(h, a.ctl->done ? 0u : 1u);
+__global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
+    k_sssp_iter(SsspArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
+  SsspCtl *c = a.ctl;
+  if (c->done) return;  // host-driven batches past the end: every block leaves
+  __shared__ SsspSmem sm;
+  if (threadIdx.x == 0) {
+    sm.nearb.cnt = 0;
+    sm.farb.cnt = 0;
+  }
+  __syncthreads();
+  if (c->mode == kSsspRelax) relax_mode(a, c, sm);
+  else split_mode(a, c, sm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sm.last = atomicAdd(&c->blocks_done, 1) == (int32_t)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (sm.last && threadIdx.x == 0) {
+    __threadfence();
+    c->blocks_done = 0;
+    sssp_end(a, c);
+    if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
+  }
 }
 
 // pred[v] = smallest u with an edge (u, v) and dist[u] + w = dist[v]
@@ -307,32 +369,30 @@ __global__ void k_sssp_pred_fin(int32_t *pred, int32_t n, int32_t src) {
 
 }  // namespace
 
-static gr_status ensure_sssp_ws(gr_graph *g, cudaStream_t s) {
-  if (g->sssp) return GR_OK;
+size_t sssp_ws_bytes(const gr_graph *g) {
+  const size_t n = (size_t)g->n;
+  return 4 * sizeof(int32_t) * (n + 1) + 2 * sizeof(int32_t) * (n + 2) +
+         2 * sizeof(int32_t) * n + sizeof(SsspCtl);
+}
+
+gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out) {
   std::unique_ptr<SsspWorkspace> ws(new SsspWorkspace());
   const size_t n = (size_t)g->n;
   for (int i = 0; i < 2; ++i) {
     GR_TRY(ws->nearq[i].alloc(sizeof(int32_t) * (n + 1), "SSSP near queue"));
+    GR_TRY(ws->nearS[i].alloc(sizeof(int32_t) * (n + 2), "SSSP near degree scan"));
     GR_TRY(ws->farq[i].alloc(sizeof(int32_t) * (n + 1), "SSSP far pile"));
   }
-  GR_TRY(ws->scan.alloc(sizeof(int32_t) * (n + 2), "SSSP degree scan"));
   GR_TRY(ws->stamp.alloc(sizeof(int32_t) * n, "SSSP near stamps"));
   GR_TRY(ws->far_stamp.alloc(sizeof(int32_t) * n, "SSSP far stamps"));
-  const size_t ntiles = n / (kSsspScanThreads * kSsspScanItems) + 2;
-  GR_TRY(ws->status.alloc(sizeof(unsigned long long) * ntiles, "scan status"));
   GR_TRY(ws->ctl.alloc(sizeof(SsspCtl), "SSSP control"));
-  GR_CUDA(cudaMemsetAsync(ws->status.p, 0, ws->status.bytes, s));
-  SsspCtl init;
-  std::memset(&init, 0, sizeof(init));
-  init.epoch = 1;
-  GR_CUDA(cudaMemcpyAsync(ws->ctl.p, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  GR_CUDA(cudaMemsetAsync(ws->ctl.p, 0, sizeof(SsspCtl), s));
   GR_CUDA(cudaStreamSynchronize(s));
-  g->sssp = ws.release();
+  *out = ws.release();
   return GR_OK;
 }
 
-static SsspArgs sssp_args(gr_graph *g) {
-  SsspWorkspace *ws = g->sssp;
+static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws) {
   SsspArgs a;
   a.R = g->row_off.as<int32_t>();
   a.C = g->col.as<int32_t>();
@@ -340,28 +400,23 @@ static SsspArgs sssp_args(gr_graph *g) {
   a.n = g->n;
   for (int i = 0; i < 2; ++i) {
     a.nearq[i] = ws->nearq[i].as<int32_t>();
+    a.nearS[i] = ws->nearS[i].as<int32_t>();
     a.farq[i] = ws->farq[i].as<int32_t>();
   }
-  a.scan = ws->scan.as<int32_t>();
   a.stamp = ws->stamp.as<int32_t>();
   a.far_stamp = ws->far_stamp.as<int32_t>();
-  a.status = ws->status.as<unsigned long long>();
   a.ctl = ws->ctl.as<SsspCtl>();
   return a;
 }
 
 static gr_status sssp_enqueue_iter(gr_graph *g, const SsspArgs &a, cudaStream_t s,
                                    cudaGraphConditionalHandle h, int use_cond) {
-  k_sssp_scan<<<g->num_sms * 2, kSsspScanThreads, 0, s>>>(a);
-  k_sssp_relax<<<g->num_sms * 4, kSsspThreads, 0, s>>>(a);
-  k_sssp_split<<<g->num_sms * 4, kSsspThreads, 0, s>>>(a);
-  k_sssp_end<<<1, 32, 0, s>>>(a, h, use_cond);
+  k_sssp_iter<<<g->num_sms * kSsspBlocksPerSm, kSsspThreads, 0, s>>>(a, h, use_cond);
   GR_CUDA(cudaGetLastError());
   return GR_OK;
 }
 
-static gr_status build_sssp_graph(gr_graph *g) {
-  SsspWorkspace *ws = g->sssp;
+static gr_status build_sssp_graph(gr_graph *g, SsspWorkspace *ws) {
   if (ws->exec) return GR_OK;
   cudaGraph_t graph;
   GR_CUDA(cudaGraphCreate(&graph, 0));
@@ -379,7 +434,7 @@ static gr_status build_sssp_graph(gr_graph *g) {
   GR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   GR_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  gr_status st = sssp_enqueue_iter(g, sssp_args(g), cs, h, 1);
+  gr_status st = sssp_enqueue_iter(g, sssp_args(g, ws), cs, h, 1);
   cudaGraph_t captured;
   cudaError_t e = cudaStreamEndCapture(cs, &captured);
   cudaStreamDestroy(cs);
@@ -390,40 +445,25 @@ static gr_status build_sssp_graph(gr_graph *g) {
   return GR_OK;
 }
 
-// default bucket width: a multiple of the mean weight (computed once)
-static uint32_t tuned_delta(gr_graph *g) { return g->sssp_delta; }
-
-}  // namespace gr
-
-using namespace gr;
-
-extern "C" {
-
-gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
-                  const gr_opts *opts, void *stream) {
-  clear_error();
-  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o) {
   if (!g->has_weights) return fail(GR_EINVAL, "SSSP needs edge weights (w was NULL at creation)");
   if (src < 0 || src >= g->n) return fail(GR_EINVAL, "source out of range");
-  if (!dist) return fail(GR_EINVAL, "dist must not be NULL");
-  const gr_opts &o = opts ? *opts : default_opts();
   if (o.mode < GR_MODE_AUTO || o.mode > GR_MODE_PERSISTENT)
     return fail(GR_EINVAL, "unknown mode");
-  std::lock_guard<std::mutex> lock(g->mu);
-  cudaStream_t s = (cudaStream_t)stream;
-  GR_TRY(begin_call(g, s));
-  GR_TRY(ensure_sssp_ws(g, s));
+  return GR_OK;
+}
+
+// SSSP into device outputs with an explicit workspace (no locking, no
+// staging): the public gr_sssp and the query server both call this.
+gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, int32_t *pred,
+                   const gr_opts &o, cudaStream_t s) {
   const unsigned long long delta =
-      o.delta == UINT32_MAX ? (1ull << 40) : (o.delta ? o.delta : tuned_delta(g));
-  int32_t max_iters = o.max_iters > 0 ? o.max_iters : (int32_t)std::min<long long>(
-                                                          INT32_MAX, 8ll * g->n + 1024);
-  void *d_dist, *d_pred;
-  bool cp_dist, cp_pred;
-  GR_TRY(resolve_output(g, 0, dist, sizeof(uint32_t) * (size_t)g->n, &d_dist, &cp_dist));
-  GR_TRY(resolve_output(g, 1, pred, sizeof(int32_t) * (size_t)g->n, &d_pred, &cp_pred));
-  SsspArgs a = sssp_args(g);
-  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, (uint32_t *)d_dist, (int32_t *)d_pred,
-                                             delta, max_iters);
+      o.delta == UINT32_MAX ? (1ull << 40) : (o.delta ? o.delta : g->sssp_delta);
+  const int32_t max_iters = o.max_iters > 0
+                                ? o.max_iters
+                                : (int32_t)std::min<long long>(INT32_MAX, 8ll * g->n + 1024);
+  SsspArgs a = sssp_args(g, ws);
+  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, dist, pred, delta, max_iters);
   GR_CUDA(cudaGetLastError());
   if (o.mode == GR_MODE_LAUNCH || o.mode == GR_MODE_PERSISTENT) {
     SsspCtl h;
@@ -437,17 +477,41 @@ gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
       batch = std::min(batch * 2, 256);
     }
   } else {
-    GR_TRY(build_sssp_graph(g));
-    GR_CUDA(cudaGraphLaunch(g->sssp->exec, s));
+    GR_TRY(build_sssp_graph(g, ws));
+    GR_CUDA(cudaGraphLaunch(ws->exec, s));
   }
-  if (d_pred) {
+  if (pred) {
     const int grid = g->num_sms * 8;
-    k_sssp_pred_init<<<grid, 256, 0, s>>>((int32_t *)d_pred, g->n);
-    k_sssp_pred<<<grid, 256, 0, s>>>(a.R, a.C, a.W, (uint32_t *)d_dist, (int32_t *)d_pred,
-                                     g->n, src);
-    k_sssp_pred_fin<<<grid, 256, 0, s>>>((int32_t *)d_pred, g->n, src);
+    k_sssp_pred_init<<<grid, 256, 0, s>>>(pred, g->n);
+    k_sssp_pred<<<grid, 256, 0, s>>>(a.R, a.C, a.W, dist, pred, g->n, src);
+    k_sssp_pred_fin<<<grid, 256, 0, s>>>(pred, g->n, src);
     GR_CUDA(cudaGetLastError());
   }
+  return GR_OK;
+}
+
+}  // namespace gr
+
+using namespace gr;
+
+extern "C" {
+
+gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
+                  const gr_opts *opts, void *stream) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (!dist) return fail(GR_EINVAL, "dist must not be NULL");
+  const gr_opts &o = opts ? *opts : default_opts();
+  GR_TRY(sssp_check(g, src, o));
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  GR_TRY(begin_call(g, s));
+  if (!g->sssp) GR_TRY(sssp_ws_create(g, s, &g->sssp));
+  void *d_dist, *d_pred;
+  bool cp_dist, cp_pred;
+  GR_TRY(resolve_output(g, 0, dist, sizeof(uint32_t) * (size_t)g->n, &d_dist, &cp_dist));
+  GR_TRY(resolve_output(g, 1, pred, sizeof(int32_t) * (size_t)g->n, &d_pred, &cp_pred));
+  GR_TRY(sssp_run(g, g->sssp, src, (uint32_t *)d_dist, (int32_t *)d_pred, o, s));
   if (cp_dist)
     GR_CUDA(cudaMemcpyAsync(dist, d_dist, sizeof(uint32_t) * (size_t)g->n,
                             cudaMemcpyDeviceToHost, s));

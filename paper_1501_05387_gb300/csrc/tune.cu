@@ -1,0 +1,176 @@
+// Autotuner: per-graph choice of the traversal knobs the paper leaves to
+// the user (Sec. 4.4: the hybrid's threshold "can be changed easily ... for
+// their own datasets"; Sec. 6: "we can predict which strategies will be most
+// beneficial based only on the degree distribution").
+//
+// Two stages:
+//   * a prior from degree statistics, set when the graph is created
+//     (tune_prior): mesh-like graphs (small maximum degree) get push-only
+//     traversal and a small persistent grid (cheap barriers for thousands of
+//     levels); skewed graphs get direction-optimising traversal on the full
+//     GPU;
+//   * gr_autotune measures candidate settings on sample sources with CUDA
+//     events and keeps the fastest: BFS level-loop driver, persistent grid
+//     size, push->pull / pull->push thresholds (alpha, beta), and the SSSP
+//     near/far bucket width. The results are stored in the graph and used
+//     whenever the caller's options leave a field at 0.
+// Tuning never changes results: every candidate computes the same depths
+// and distances.
+#include <algorithm>
+#include <cfloat>
+#include <vector>
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+void tune_prior(gr_graph *g) {
+  g->tuned_alpha = 14.f;
+  g->tuned_beta = 24.f;
+  if (g->max_degree <= 32) {
+    g->tuned_direction = GR_DIR_PUSH;  // never pull: frontiers stay thin
+    g->tuned_blocks_per_sm = 1;
+  } else {
+    g->tuned_direction = GR_DIR_AUTO;
+    g->tuned_blocks_per_sm = 0;  // all resident blocks
+  }
+  g->tuned_mode = GR_MODE_AUTO;
+}
+
+namespace {
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timer() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+}  // namespace
+
+}  // namespace gr
+
+using namespace gr;
+
+extern "C" {
+
+gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
+                      void *stream) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (k < 1 || !srcs) return fail(GR_EINVAL, "need at least one sample source");
+  for (int32_t i = 0; i < k; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->n) return fail(GR_EINVAL, "source out of range");
+  if (what & ~(GR_TUNE_BFS | GR_TUNE_SSSP)) return fail(GR_EINVAL, "unknown tuning flags");
+  if ((what & GR_TUNE_SSSP) && !g->has_weights)
+    return fail(GR_EINVAL, "SSSP tuning needs edge weights");
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  GR_TRY(begin_call(g, s));
+  DevMem out, out2;
+  GR_TRY(out.alloc(sizeof(int32_t) * (size_t)g->n, "tuning output"));
+  Timer t;
+  if (what & GR_TUNE_BFS) {
+    if (!g->bfs) GR_TRY(bfs_ws_create(g, s, &g->bfs));
+    struct Cand {
+      int32_t mode, bps, dir;
+      float alpha, beta;
+    };
+    std::vector<Cand> cands;
+    const int32_t bpss[] = {1, 2, 0};
+    auto add = [&](int32_t dir, float al, float be) {
+      for (int32_t bps : bpss) cands.push_back({GR_MODE_PERSISTENT, bps, dir, al, be});
+      cands.push_back({GR_MODE_GRAPH, 0, dir, al, be});
+    };
+    add(GR_DIR_PUSH, 14.f, 24.f);  // thresholds unused without pull
+    if (g->symmetric)
+      for (float al : {4.f, 14.f, 40.f})
+        for (float be : {8.f, 24.f, 64.f}) add(GR_DIR_AUTO, al, be);
+    float best = FLT_MAX;
+    Cand pick = cands[0];
+    const int32_t saved_bps = g->tuned_blocks_per_sm;
+    for (const Cand &c : cands) {
+      gr_opts o = default_opts();
+      o.mode = c.mode;
+      o.alpha = c.alpha;
+      o.beta = c.beta;
+      o.direction = c.dir;
+      g->tuned_blocks_per_sm = c.bps;
+      // one untimed run, then the sample
+      GR_TRY(bfs_run(g, g->bfs, srcs[0], out.as<int32_t>(), nullptr, o, s));
+      GR_CUDA(cudaEventRecord(t.a, s));
+      for (int32_t i = 0; i < k; ++i)
+        GR_TRY(bfs_run(g, g->bfs, srcs[i], out.as<int32_t>(), nullptr, o, s));
+      GR_CUDA(cudaEventRecord(t.b, s));
+      GR_CUDA(cudaEventSynchronize(t.b));
+      GR_TRY(bfs_read_ctl_error(g->bfs));
+      float ms = 0.f;
+      GR_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+      if (ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    g->tuned_blocks_per_sm = pick.bps;
+    if (pick.mode == GR_MODE_GRAPH) g->tuned_blocks_per_sm = saved_bps;
+    g->tuned_mode = pick.mode;
+    g->tuned_direction = pick.dir;
+    g->tuned_alpha = pick.alpha;
+    g->tuned_beta = pick.beta;
+    g->tuned_bfs_ms = best / k;
+  }
+  if (what & GR_TUNE_SSSP) {
+    if (!g->sssp) GR_TRY(sssp_ws_create(g, s, &g->sssp));
+    std::vector<uint32_t> deltas;
+    const double mw = std::max(1.0, g->mean_weight);
+    for (double f : {0.5, 1.0, 2.0, 4.0, 8.0, 32.0})
+      deltas.push_back((uint32_t)std::max(1.0, std::min(4.0e9, f * mw)));
+    deltas.push_back(UINT32_MAX);
+    float best = FLT_MAX;
+    uint32_t pick = g->sssp_delta;
+    for (uint32_t d : deltas) {
+      gr_opts o = default_opts();
+      o.delta = d;
+      GR_TRY(sssp_run(g, g->sssp, srcs[0], out.as<uint32_t>(), nullptr, o, s));
+      GR_CUDA(cudaEventRecord(t.a, s));
+      for (int32_t i = 0; i < k; ++i)
+        GR_TRY(sssp_run(g, g->sssp, srcs[i], out.as<uint32_t>(), nullptr, o, s));
+      GR_CUDA(cudaEventRecord(t.b, s));
+      GR_CUDA(cudaEventSynchronize(t.b));
+      float ms = 0.f;
+      GR_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+      if (ms < best) {
+        best = ms;
+        pick = d;
+      }
+    }
+    // UINT32_MAX selects "one bucket"; store it as the widest delta
+    g->sssp_delta = pick;
+    g->tuned_sssp_ms = best / k;
+  }
+  GR_CUDA(cudaStreamSynchronize(s));
+  GR_TRY(end_call(g, s));
+  return GR_OK;
+}
+
+gr_status gr_tuned_opts(const gr_graph *g, gr_opts *out, double *bfs_ms, double *sssp_ms) {
+  clear_error();
+  if (!g || !out) return fail(GR_EINVAL, "graph and out must not be NULL");
+  *out = default_opts();
+  out->mode = g->tuned_mode;
+  out->direction = g->tuned_direction;
+  out->alpha = g->tuned_alpha;
+  out->beta = g->tuned_beta;
+  out->block = g->tuned_blocks_per_sm;
+  out->delta = g->sssp_delta;
+  if (bfs_ms) *bfs_ms = g->tuned_bfs_ms;
+  if (sssp_ms) *sssp_ms = g->tuned_sssp_ms;
+  return GR_OK;
+}
+
+}  // extern "C"

@@ -27,6 +27,8 @@ STATUS_NAMES = {0: "GR_OK", 1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA",
                 4: "GR_ETIMEOUT", 5: "GR_EBUSY"}
 GR_DIR_AUTO, GR_DIR_PUSH, GR_DIR_PULL = 0, 1, 2
 GR_MODE_AUTO, GR_MODE_LAUNCH, GR_MODE_GRAPH, GR_MODE_PERSISTENT = 0, 1, 2, 3
+GR_QUERY_BFS, GR_QUERY_SSSP, GR_QUERY_CC = 0, 1, 2
+GR_TUNE_BFS, GR_TUNE_SSSP = 1, 2
 
 
 class gr_opts(ctypes.Structure):
@@ -65,6 +67,16 @@ _sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_sssp_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("gr_bfs_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_bc", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
+_sig("gr_autotune", [_vp, _vp, _i32, _i32, _vp])
+_sig("gr_tuned_opts", [_vp, _P(gr_opts), _P(ctypes.c_double), _P(ctypes.c_double)])
+_sig("gr_server_create", [ctypes.c_size_t, _i32, _i32, _P(_vp)])
+_sig("gr_server_add_graph", [_vp, _vp, _i32, _P(_i32)])
+_sig("gr_server_submit", [_vp, _i32, _i32, _i32, _vp, _P(ctypes.c_uint64)])
+_sig("gr_server_wait", [_vp, ctypes.c_uint64, _i32, _P(ctypes.c_double)])
+_sig("gr_server_drain", [_vp, _i32])
+_sig("gr_server_stats", [_vp, _P(_i64), _P(_i64), _P(_i64), _P(ctypes.c_double),
+                         _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)])
+_sig("gr_server_destroy", [_vp])
 _sig("gr_bfs_noalloc", [_i32, _i64, _vp, _vp, _i32, _vp, _vp, _vp])
 _sig("gr_cc", [_vp, _vp, _P(_i32), _P(gr_opts), _vp])
 _sig("gr_pagerank", [_vp, ctypes.c_float, _i32, ctypes.c_double, _vp, _P(_i32),
@@ -267,6 +279,94 @@ def gr_pagerank(g: Graph, rank, damping=0.85, max_iter=50, tol=1e-7, opts=None,
                             _ptr(rank, np.float32), ctypes.byref(it) if count else None,
                             _opts(opts), _stream(stream)), "gr_pagerank")
     return it.value if count else None
+
+
+def gr_autotune(g: Graph, srcs, what: int = 1, stream=None):
+    """Measure candidate settings on sample sources; keep the fastest."""
+    srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    _check(_lib.gr_autotune(g.handle, srcs.ctypes.data, int(srcs.size), int(what),
+                            _stream(stream)), "gr_autotune")
+
+
+def gr_tuned_opts(g: Graph):
+    o = gr_opts()
+    b, s = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.gr_tuned_opts(g.handle, ctypes.byref(o), ctypes.byref(b), ctypes.byref(s)),
+           "gr_tuned_opts")
+    return {"mode": o.mode, "direction": o.direction, "alpha": o.alpha, "beta": o.beta, "blocks_per_sm": o.block,
+            "delta": o.delta, "bfs_ms": b.value, "sssp_ms": s.value}
+
+
+class Server:
+    """Owning wrapper of a gr_server handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.graphs = []  # keep the graphs alive as long as the server
+
+    def close(self):
+        if self.handle:
+            _lib.gr_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def gr_server_create(budget_bytes: int, num_slots: int = 4, max_batch: int = 64) -> Server:
+    out = _vp()
+    _check(_lib.gr_server_create(int(budget_bytes), int(num_slots), int(max_batch),
+                                 ctypes.byref(out)), "gr_server_create")
+    return Server(out.value)
+
+
+def gr_server_add_graph(s: Server, g: Graph, batchable: bool = True) -> int:
+    gid = _i32()
+    _check(_lib.gr_server_add_graph(s.handle, g.handle, int(batchable), ctypes.byref(gid)),
+           "gr_server_add_graph")
+    s.graphs.append(g)
+    return gid.value
+
+
+def gr_server_submit(s: Server, graph_id: int, kind: int, src: int = 0, out=None) -> int:
+    t = ctypes.c_uint64()
+    _check(_lib.gr_server_submit(s.handle, int(graph_id), int(kind), int(src), _ptr(out),
+                                 ctypes.byref(t)), "gr_server_submit")
+    return t.value
+
+
+def gr_server_wait(s: Server, ticket: int, timeout_ms: int = -1) -> float:
+    lat = ctypes.c_double()
+    _check(_lib.gr_server_wait(s.handle, ctypes.c_uint64(ticket), int(timeout_ms),
+                               ctypes.byref(lat)), "gr_server_wait")
+    return lat.value
+
+
+def gr_server_drain(s: Server, timeout_ms: int = -1):
+    _check(_lib.gr_server_drain(s.handle, int(timeout_ms)), "gr_server_drain")
+
+
+def gr_server_stats(s: Server) -> dict:
+    c, f, l = _i64(), _i64(), _i64()
+    q, p50, p99, mb = (ctypes.c_double() for _ in range(4))
+    _check(_lib.gr_server_stats(s.handle, ctypes.byref(c), ctypes.byref(f), ctypes.byref(l),
+                                ctypes.byref(q), ctypes.byref(p50), ctypes.byref(p99),
+                                ctypes.byref(mb)), "gr_server_stats")
+    return {"completed": c.value, "failed": f.value, "launches": l.value, "qps": q.value,
+            "p50_ms": p50.value, "p99_ms": p99.value, "mean_batch": mb.value}
+
+
+def gr_server_destroy(s: Server):
+    s.close()
 
 
 def gr_last_error() -> str:

@@ -88,3 +88,19 @@ def test_null_graph_rejected(gr):
     assert gr._lib.gr_bfs(None, 0, d.ctypes.data, None, None, None) == gr.GR_EINVAL
     assert "NULL" in gr.gr_last_error()
     assert gr._lib.gr_graph_destroy(None) == gr.GR_OK
+
+
+def test_server_rejects_bad_arguments(gr):
+    out = ctypes.c_void_p()
+    for budget, slots, batch in [(0, 1, 1), (1 << 20, 0, 1), (1 << 20, 65, 1),
+                                 (1 << 20, 1, 0), (1 << 20, 1, 65)]:
+        assert gr._lib.gr_server_create(budget, slots, batch, ctypes.byref(out)) == gr.GR_EINVAL
+    assert gr._lib.gr_server_destroy(None) == gr.GR_OK
+
+
+def test_batch_and_bc_reject_bad_arguments(gr):
+    srcs = np.zeros(65, np.int32)
+    d = np.zeros(4, np.int32)
+    assert gr._lib.gr_bfs_batch(None, srcs.ctypes.data, 1, d.ctypes.data, None, None) == gr.GR_EINVAL
+    assert gr._lib.gr_bc(None, srcs.ctypes.data, 1, d.ctypes.data, None, None) == gr.GR_EINVAL
+    assert gr._lib.gr_bfs_noalloc(0, 0, None, None, 0, None, None, None) == gr.GR_EINVAL

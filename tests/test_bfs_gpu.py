@@ -11,7 +11,7 @@ from checks import manhattan, validate_bfs
 pytestmark = pytest.mark.gpu
 
 DIRS = ["auto", "push", "pull"]
-MODES = ["graph", "launch"]
+MODES = ["graph", "launch", "persistent"]
 
 
 def opts(gr, direction="auto", mode="auto", **kw):
@@ -84,7 +84,7 @@ def test_grid(cuda_lib, side, p_del, mode):
     r, c = gg.grid(side, p_del=p_del, seed=4)
     with cuda_lib.gr_graph_create(r, c) as g:
         for src in [0, side * side // 2 + side // 3]:
-            o = opts(cuda_lib, "push" if mode == "persistent" else "auto", mode)
+            o = opts(cuda_lib, "auto", mode)
             check(cuda_lib, r, c, g, src, o)
             if p_del == 0.0:
                 d, _ = run_bfs(cuda_lib, g, src, o)
@@ -188,10 +188,11 @@ def test_tuning_knobs_do_not_change_depth(cuda_lib, s14):
     r, c, g = s14
     src = int(gg.sources(r, 1, seed=9)[0])
     ref, _ = oracle.bfs(r, c, src)
-    for alpha, beta in [(1.0, 1.0), (1000.0, 2.0), (2.0, 1000.0), (0.01, 0.01)]:
-        d, p = run_bfs(cuda_lib, g, src, opts(cuda_lib, "auto", "graph", alpha=alpha, beta=beta))
-        assert np.array_equal(d, ref)
-        validate_bfs(r, c, src, d, p)
+    for mode in ["graph", "persistent"]:
+        for alpha, beta in [(1.0, 1.0), (1000.0, 2.0), (2.0, 1000.0), (0.01, 0.01)]:
+            d, p = run_bfs(cuda_lib, g, src, opts(cuda_lib, "auto", mode, alpha=alpha, beta=beta))
+            assert np.array_equal(d, ref)
+            validate_bfs(r, c, src, d, p)
 
 
 @pytest.mark.slow
@@ -210,13 +211,14 @@ def test_rmat_s22_sixteen_sources(cuda_lib):
             validate_bfs(r, c, int(s), d, p, keys=keys, su=su)
 
 
+@pytest.mark.parametrize("mode", ["graph", "persistent"])
 @pytest.mark.parametrize("direction", DIRS)
-def test_trace_frontier_sizes_match_oracle_levels(cuda_lib, s14, direction):
+def test_trace_frontier_sizes_match_oracle_levels(cuda_lib, s14, direction, mode):
     # every frontier is exact (each vertex enters once), so the traced
     # frontier sizes equal the oracle's vertex count per depth
     r, c, g = s14
     src = gg.max_degree_vertex(r)
-    run_bfs(cuda_lib, g, src, opts(cuda_lib, direction, "graph"))
+    run_bfs(cuda_lib, g, src, opts(cuda_lib, direction, mode))
     tr = cuda_lib.gr_bfs_trace(g)
     ref, _ = oracle.bfs(r, c, src)
     hist = np.bincount(ref[ref >= 0])
