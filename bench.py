@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--cpu-sample-sources", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serve 20000 requests over the 24-graph pool (slow)")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale (profiling runs only; the metric is quoted at 22)")
     ap.add_argument("--mode", default="auto", choices=["auto", "graph", "launch", "persistent"],
@@ -131,6 +134,107 @@ def bfs_bytes(r, depth_list, m):
         m_reached = int(deg[reached].sum())
         out.append(4 * m_reached + 4 * (n + 1) + 8 * int(reached.sum()))
     return out
+
+
+# ----------------------------------------------------------------- serving
+def serving_pool(full: bool):
+    """The resident graph pool: R-MAT graphs (a,b,c) = (0.57,0.19,0.19) and
+    grids with 5 % deletions, uint32 weights in [1, 64]. full=True is the
+    24-graph pool (12 R-MAT scale 16 + i mod 7, edge factor 8/16/32 by i mod
+    3, seed 100 + i; 12 grids of side 512/1024/2048/4096 x 3 deletion seeds);
+    otherwise a 6-graph subset that builds in seconds."""
+    import graphgen as gg
+    specs = []
+    if full:
+        for i in range(12):
+            specs.append(("rmat", 16 + i % 7, (8, 16, 32)[i % 3], 100 + i))
+        for j, side in enumerate([512, 1024, 2048, 4096]):
+            for k in range(3):
+                specs.append(("grid", side, 0, 200 + 3 * j + k))
+    else:
+        specs = [("rmat", 16, 8, 100), ("rmat", 18, 16, 101), ("rmat", 20, 16, 102),
+                 ("rmat", 17, 32, 103), ("grid", 512, 0, 200), ("grid", 1024, 0, 201)]
+    out = []
+    for kind, a, b, seed in specs:
+        if kind == "rmat":
+            r, c = gg.rmat(a, b, seed=seed)
+        else:
+            r, c = gg.grid(a, p_del=0.05, seed=seed)
+        w = gg.weights(r, c, seed=seed + 1000, wmin=1, wmax=64)
+        out.append((kind, a, b, seed, r, c, w))
+    return out
+
+
+def serving_requests(pool, count, seed=6):
+    """Seeded request mix: 60 % BFS, 30 % SSSP, 10 % CC, uniform graph, random
+    non-isolated source; Poisson arrivals are drawn per run (unit rate here,
+    scaled by the run's rate)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(count):
+        gi = int(rng.integers(0, len(pool)))
+        u = rng.random()
+        kind = 0 if u < 0.6 else (1 if u < 0.9 else 2)
+        r = pool[gi][4]
+        deg = np.diff(r)
+        while True:
+            s = int(rng.integers(0, r.size - 1))
+            if deg[s] > 0:
+                break
+        reqs.append((gi, kind, s))
+    gaps = rng.exponential(1.0, size=count)
+    return reqs, np.cumsum(gaps)
+
+
+def run_serving(gr, graphs, batchable, reqs, unit_arrivals, rate, slots, batch, budget):
+    """Submit reqs at Poisson times (rate per second) to a fresh server and
+    wait for all; returns the server's stats."""
+    srv = gr.gr_server_create(budget, slots, batch)
+    ids = [gr.gr_server_add_graph(srv, g, b) for g, b in zip(graphs, batchable)]
+    arrivals = unit_arrivals / rate
+    t0 = time.perf_counter()
+    for (gi, kind, src), at in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        gr.gr_server_submit(srv, ids[gi], kind, src, None)
+    gr.gr_server_drain(srv, 600000)
+    st = gr.gr_server_stats(srv)
+    srv.close()
+    return st
+
+
+def serving_bench(gr, full=False, count=2000):
+    pool = serving_pool(full)
+    graphs = [gr.gr_graph_create(r, c, w) for (_, _, _, _, r, c, w) in pool]
+    batchable = [kind == "rmat" for (kind, *_rest) in pool]
+    reqs, unit = serving_requests(pool, count)
+    budget = 16 << 30
+    # warm: one query of each kind per graph on both configurations
+    warm = [(gi, k, int(np.argmax(np.diff(pool[gi][4]))))
+            for gi in range(len(pool)) for k in range(3)]
+    for slots, batch in [(1, 1), (4, 64)]:
+        run_serving(gr, graphs, batchable, warm, np.arange(len(warm), dtype=float), 1e9,
+                    slots, batch, budget)
+    # capacity of the plain path (saturating arrivals), then both paths at
+    # 10x that rate (throughput) and at 0.7x their own capacity (latency)
+    plain_sat = run_serving(gr, graphs, batchable, reqs, unit, 1e9, 1, 1, budget)
+    rate = 10.0 * max(plain_sat["qps"], 1.0)
+    plain = run_serving(gr, graphs, batchable, reqs, unit, rate, 1, 1, budget)
+    served = run_serving(gr, graphs, batchable, reqs, unit, rate, 4, 64, budget)
+    plain_lat = run_serving(gr, graphs, batchable, reqs, unit, 0.7 * plain["qps"], 1, 1, budget)
+    served_lat = run_serving(gr, graphs, batchable, reqs, unit, 0.7 * served["qps"], 4, 64,
+                             budget)
+    for g in graphs:
+        g.close()
+    pick = lambda st: {k: st[k] for k in ("qps", "p50_ms", "p99_ms", "mean_batch", "launches")}
+    return {"requests": count, "graphs": len(pool),
+            "pool": "24-graph pool" if full else "6-graph subset (R-MAT s16-s20, grids 512/1024)",
+            "mix": "60/30/10 BFS/SSSP/CC, Poisson arrivals seed 6",
+            "plain": {"saturated": pick(plain), "at_0.7x_capacity": pick(plain_lat)},
+            "served": {"saturated": pick(served), "at_0.7x_capacity": pick(served_lat),
+                       "slots": 4, "max_batch": 64},
+            "speedup_qps": served["qps"] / max(plain["qps"], 1e-9)}
 
 
 def cpu_baseline(r, c, srcs, m, k):
@@ -300,6 +404,12 @@ def run_gr(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(r, c, srcs, m, args.cpu_sample_sources)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        g.close()
+        g = None
+        serving = serving_bench(gr, full=args.serving_full,
+                                count=20000 if args.serving_full else 2000)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -316,6 +426,7 @@ def run_gr(args):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+                "serving": serving,
                 "bfs_ms": {"mean": float(per_bfs.mean()), "p50": float(np.median(per_bfs)),
                            "p99": float(np.percentile(per_bfs, 99)),
                            "min": float(per_bfs.min()), "max": float(per_bfs.max())},
@@ -324,7 +435,8 @@ def run_gr(args):
                     {"dir": "pull" if d else "push", "frontier": f, "edges": e,
                      "end_us": round(t, 2)} for d, f, e, t in traces[0]]}
         print(json.dumps(line), flush=True)
-    g.close()
+    if g is not None:
+        g.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
