@@ -284,6 +284,17 @@ gr_status gr_server_stats(gr_server *s, int64_t *completed, int64_t *failed,
 /* Stop the workers (queued requests are dropped) and free the server. */
 gr_status gr_server_destroy(gr_server *s);
 
+/* Diagnostics for failure handling (no GPU fault is ever provoked).
+ * gr_diag_wait_timeout: a kernel spins on a flag that nothing sets, with
+ * the library's bounded-wait logic and a limit of spin_limit polls (in
+ * [0, 2^24]); returns GR_ETIMEOUT when the wait gave up, as every bounded
+ * device wait of the library reports it, and the context stays usable.
+ * gr_diag_fail_alloc: after `after` more successful device allocations the
+ * library's allocations fail with GR_ENOMEM (after < 0 restores normal
+ * behaviour); process-wide. */
+gr_status gr_diag_wait_timeout(int64_t spin_limit, void *stream);
+gr_status gr_diag_fail_alloc(int64_t after);
+
 /* This thread's last error message ("" if none). The pointer stays valid
  * until this thread's next gr_* call. */
 const char *gr_last_error(void);

@@ -152,6 +152,56 @@ __device__ __forceinline__ int32_t merge_count_t(const int32_t *S, int32_t q, in
   return lo;
 }
 
+// Block-cooperative merge-path search: the count c in [lo, hi] of
+// positions i whose end marker S[i+1] + i lies before diagonal d (markers
+// are strictly increasing in i). Each round every thread probes one
+// position and the block counts the probes before d, shrinking the range by
+// a factor of THREADS, so c takes ceil(log_THREADS(hi - lo)) + 1 rounds of
+// independent loads instead of log2(hi - lo) dependent ones. s_q stands in
+// for S[q] (pass S[q] when it is stored). Block-uniform call; s_red holds
+// THREADS / 32 ints.
+template <int THREADS>
+__device__ int32_t block_merge_search(const int32_t *S, int32_t q, int32_t s_q, long long d,
+                                      int32_t lo, int32_t hi, int32_t *s_red) {
+  constexpr int WARPS = THREADS / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (;;) {
+    const int32_t len = hi - lo;
+    if (len <= 0) return lo;
+    const int32_t step = len <= THREADS ? 1 : (len + THREADS - 1) / THREADS;
+    const long long p = (long long)lo + (long long)threadIdx.x * step;
+    bool pred = false;
+    if (p < hi) {
+      const int32_t pi = (int32_t)p;
+      const int32_t sv = (pi + 1 == q) ? s_q : S[pi + 1];
+      pred = (long long)sv + pi < d;
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, pred);
+    if (lane == 0) s_red[wid] = __popc(b);
+    __syncthreads();
+    int32_t k = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) k += s_red[w];
+    __syncthreads();
+    if (step == 1) return lo + k;
+    if (k == 0) return lo;
+    const int32_t nlo = lo + (k - 1) * step + 1;
+    const int32_t nhi = (int32_t)min((long long)hi, (long long)lo + (long long)k * step);
+    lo = nlo;
+    hi = nhi;
+  }
+}
+
+// Both ends of a chunk [d0, d1) (d1 - d0 <= chunk): i0 over the whole
+// frontier, then i1 within i0 + chunk.
+template <int THREADS>
+__device__ __forceinline__ void block_chunk_bounds(const int32_t *S, int32_t q, int32_t s_q,
+                                                   long long d0, long long d1, int32_t chunk,
+                                                   int32_t *s_red, int32_t *i0, int32_t *i1) {
+  *i0 = block_merge_search<THREADS>(S, q, s_q, d0, 0, q, s_red);
+  *i1 = block_merge_search<THREADS>(S, q, s_q, d1, *i0, min(q, *i0 + chunk), s_red);
+}
+
 // Append `v` to one of two block-local output buffers selected per thread
 // (code 1 -> buffer 0, code 2 -> buffer 1), warp-aggregated.
 __device__ __forceinline__ void warp_append(int code, int32_t v, int32_t *buf0,
@@ -195,17 +245,14 @@ __device__ void lb_advance(const int32_t *R, const int32_t *C, const int32_t *Q,
   __shared__ int32_t s_row[CHUNK + 1];
   __shared__ int32_t s_out0[CHUNK];
   __shared__ int32_t s_out1[NOUT == 2 ? CHUNK : 1];
-  __shared__ int32_t s_i[2];
+  __shared__ int32_t s_red8[THREADS / 32];
   __shared__ int32_t s_cnt[2], s_base[2];
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * CHUNK;
     const long long d1 = min(d0 + CHUNK, total);
-    if (threadIdx.x < 2) {
-      s_i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
-      s_cnt[threadIdx.x] = 0;
-    }
-    __syncthreads();
-    const int32_t i0 = s_i[0], i1 = s_i[1];
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+    int32_t i0, i1;
+    block_chunk_bounds<THREADS>(S, q, S[q], d0, d1, CHUNK, s_red8, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += THREADS) {
@@ -268,14 +315,13 @@ __device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n
   const long long total = (long long)n + R[n];
   const long long nchunks = (total + CHUNK - 1) / CHUNK;
   __shared__ int32_t s_off[CHUNK + 1];
-  __shared__ int32_t s_i[2];
+  __shared__ int32_t s_red8[THREADS / 32];
   const int lane = threadIdx.x & 31;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * CHUNK;
     const long long d1 = min(d0 + CHUNK, total);
-    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(R, n, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const int32_t i0 = s_i[0], i1 = s_i[1];
+    int32_t i0, i1;
+    block_chunk_bounds<THREADS>(R, n, R[n], d0, d1, CHUNK, s_red8, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= n - 1) ? (min(i1, n - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += THREADS) s_off[k] = R[i0 + k];

@@ -109,7 +109,7 @@ template <bool SIGMA>
 __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
   __shared__ int32_t s_off[kMbChunk + 1];
   __shared__ unsigned long long s_U[kMbChunk + 1];
-  __shared__ int32_t s_i[2];
+  __shared__ int32_t s_red8[kMbThreads / 32];
   const int lane = threadIdx.x & 31;
   const long long total = (long long)a.n + a.R[a.n];
   const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
@@ -117,9 +117,8 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kMbChunk;
     const long long d1 = min(d0 + kMbChunk, total);
-    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(a.R, a.n, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const int32_t i0 = s_i[0], i1 = s_i[1];
+    int32_t i0, i1;
+    block_chunk_bounds<kMbThreads>(a.R, a.n, a.R[a.n], d0, d1, kMbChunk, s_red8, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
     for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
@@ -236,16 +235,15 @@ struct BcBackArgs {
 __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a) {
   __shared__ int32_t s_off[kMbChunk + 1];
   __shared__ unsigned long long s_A[kMbChunk + 1];
-  __shared__ int32_t s_i[2];
+  __shared__ int32_t s_red8[kMbThreads / 32];
   const int lane = threadIdx.x & 31;
   const long long total = (long long)a.n + a.R[a.n];
   const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kMbChunk;
     const long long d1 = min(d0 + kMbChunk, total);
-    if (threadIdx.x < 2) s_i[threadIdx.x] = merge_count(a.R, a.n, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const int32_t i0 = s_i[0], i1 = s_i[1];
+    int32_t i0, i1;
+    block_chunk_bounds<kMbThreads>(a.R, a.n, a.R[a.n], d0, d1, kMbChunk, s_red8, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
     for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {

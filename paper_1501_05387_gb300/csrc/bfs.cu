@@ -62,10 +62,9 @@ struct BfsCtl {
   int32_t barrier_cnt_unused;
   int32_t from_bitmap;  // 1: the current frontier exists only as a bitmap
   int32_t pad_;
-  // persistent kernel: next-frontier and bitmap-compaction counters, a ring
-  // of three so that one can be cleared while the others are in use
+  // persistent kernel: next-frontier counters, a ring of three so that one
+  // can be cleared while the others are in use
   unsigned long long cnt3[3];
-  unsigned long long cq3[3];
   unsigned long long next_packed;  // [31:0] next frontier size, [63:32] its edges
   long long mf;         // edges leaving the current frontier
   long long mu;         // edges of still-unexplored vertices
@@ -110,6 +109,13 @@ struct BfsArgs {
   uint32_t *fb[3];      // frontier bitmaps, rotating by level (cur, next, spare)
   BfsCtl *ctl;
   int32_t do_bitmap;
+  // persistent kernel: per-block segments of the vertices a pull level
+  // found (and their degrees), compacted into a queue by the next level
+  // when it pushes; null in the other drivers
+  int32_t *seg_v;
+  int32_t *seg_d;
+  unsigned long long *seg_cnt;  // per block: [31:0] vertices, [63:32] edges
+  int32_t seg_cap;              // entries per block segment
 };
 
 // launch shape of the level kernel
@@ -121,7 +127,7 @@ constexpr int kPullLane = 3;  // neighbours after the first a lane checks alone 
 constexpr int kLvBlocksPerSm = 6;
 
 struct BfsWorkspace {
-  DevMem q[2], S[2], visited, fb[3], ctl;
+  DevMem q[2], S[2], visited, fb[3], ctl, seg_v, seg_d, seg_cnt;
   PinnedMem h_ctl;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // by do_bitmap
   cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -198,10 +204,7 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     c->alpha = alpha;
     c->beta = beta;
     c->from_bitmap = 0;
-    for (int i = 0; i < 3; ++i) {
-      c->cnt3[i] = 0ull;
-      c->cq3[i] = 0ull;
-    }
+    for (int i = 0; i < 3; ++i) c->cnt3[i] = 0ull;
     c->t_start = globaltimer();
   }
 }
@@ -217,6 +220,8 @@ struct LevelSmem {
   int32_t deg[kLvChunk];
   uint32_t red[33];
   unsigned long long red64[33];
+  int32_t sred[kLvWarps];
+  int32_t segcnt;
   int32_t i[2];
   int32_t cnt;
   int32_t vbase, ebase;
@@ -290,24 +295,28 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kLvChunk;
     const long long d1 = min(d0 + kLvChunk, total);
-    if (threadIdx.x < 2)
-      sm.i[threadIdx.x] = merge_count_t(S, q, q_edges, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const int32_t i0 = sm.i[0], i1 = sm.i[1];
+    int32_t i0, i1;
+    block_chunk_bounds<kLvThreads>(S, q, q_edges, d0, d1, kLvChunk, sm.sred, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += kLvThreads) {
       const int32_t u = Q[i0 + k];
-      sm.off[k] = S[i0 + k];
+      sm.off[k] = (i0 + k == q) ? q_edges : S[i0 + k];
       sm.u[k] = u;
       sm.row[k] = a.R[u];
     }
     __syncthreads();
-    const int32_t ne = (int32_t)(j1 - j0);
-    for (int32_t kb = 0; kb < ne; kb += kLvThreads) {
-      const int32_t k = kb + threadIdx.x;
-      bool won = false;
-      int32_t v = 0, dv = 0;
+    const int32_t ne = (int32_t)(j1 - j0);  // <= kLvChunk: one pass of kLvItems per thread
+    // each thread takes kLvItems edges (ranks tid, tid + T, ...) and issues
+    // the loads of all of them before using any, so the latency chains of
+    // the items overlap
+    int32_t v[kLvItems], uo[kLvItems], dv[kLvItems];
+    bool won[kLvItems];
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) {
+      const int32_t k = j * kLvThreads + threadIdx.x;
+      v[j] = -1;
+      uo[j] = 0;
       if (k < ne) {
         const int32_t er = (int32_t)(j0 + k);
         int32_t lo = 0, hi = nv - 1;
@@ -316,19 +325,33 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
           if (sm.off[mid] <= er) lo = mid;
           else hi = mid - 1;
         }
-        v = a.C[sm.row[lo] + (er - sm.off[lo])];
-        const uint32_t mask = 1u << (v & 31);
-        uint32_t *vw = a.visited + (v >> 5);
-        if (!(*vw & mask)) won = !(atomicOr(vw, mask) & mask);
-        if (won) {
-          depth[v] = L + 1;
-          if (parent) parent[v] = sm.u[lo];
-          if (a.do_bitmap) atomicOr(N + (v >> 5), mask);
-          dv = a.R[v + 1] - a.R[v];
-        }
+        uo[j] = sm.u[lo];
+        v[j] = a.C[sm.row[lo] + (er - sm.off[lo])];
       }
-      emit(sm, won, v, dv);
     }
+    uint32_t vw[kLvItems];
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) vw[j] = v[j] >= 0 ? a.visited[v[j] >> 5] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) {
+      won[j] = false;
+      if (v[j] >= 0) {
+        const uint32_t mask = 1u << (v[j] & 31);
+        if (!(vw[j] & mask)) won[j] = !(atomicOr(a.visited + (v[j] >> 5), mask) & mask);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) {
+      dv[j] = 0;
+      if (won[j]) {
+        depth[v[j]] = L + 1;
+        if (parent) parent[v[j]] = uo[j];
+        if (a.do_bitmap) atomicOr(N + (v[j] >> 5), 1u << (v[j] & 31));
+        dv[j] = a.R[v[j] + 1] - a.R[v[j]];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kLvItems; ++j) emit(sm, won[j], v[j], dv[j]);
     flush(sm, counter, Qn, Sn);
   }
 }
@@ -431,12 +454,72 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
         ++found_cnt;
         found_deg += (unsigned long long)(r1[j] - r0[j]);
       }
+      if (a.seg_v && fm) {  // append to this block's segment (shared-memory slot)
+        int32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(&sm.segcnt, __popc(fm));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (fnd[j]) {
+          const int64_t k = (int64_t)blockIdx.x * a.seg_cap + pos +
+                            __popc(fm & ((1u << lane) - 1u));
+          a.seg_v[k] = v[j];
+          a.seg_d[k] = r1[j] - r0[j];
+        }
+      }
     }
   }
   // one packed atomicAdd per block: [31:0] vertices, [63:32] their edges
   const unsigned long long packed =
       block_sum((found_deg << 32) | (unsigned long long)found_cnt, (unsigned long long *)sm.red64);
-  if (threadIdx.x == 0 && packed) atomicAdd(counter, packed);
+  if (threadIdx.x == 0) {
+    if (packed) atomicAdd(counter, packed);
+    if (a.seg_v) a.seg_cnt[blockIdx.x] = packed;
+  }
+}
+
+// Queue + degree scan of the vertices the last pull level found, from the
+// per-block segments: every block computes, from the per-block totals, the
+// offsets of its segment in the queue and in the edge scan, then compacts
+// its own segment. *q_out / *e_out receive the totals.
+__device__ void segments_to_queue(const BfsArgs &a, LevelSmem &sm, int32_t *Q, int32_t *S,
+                                  int32_t *q_out, int32_t *e_out) {
+  const int32_t G = gridDim.x, b = blockIdx.x;
+  unsigned long long before = 0, all = 0;
+  for (int32_t i = threadIdx.x; i < G; i += kLvThreads) {
+    const unsigned long long x = a.seg_cnt[i];
+    all += x;
+    if (i < b) before += x;
+  }
+  before = block_sum(before, sm.red64);
+  all = block_sum(all, sm.red64);
+  *q_out = (int32_t)(all & 0xFFFFFFFFull);
+  *e_out = (int32_t)(all >> 32);
+  const int32_t vo = (int32_t)(before & 0xFFFFFFFFull);
+  uint32_t eo = (uint32_t)(before >> 32);
+  const int32_t cb = (int32_t)(a.seg_cnt[b] & 0xFFFFFFFFull);
+  const int64_t base = (int64_t)b * a.seg_cap;
+  constexpr int PER = kLvChunk / kLvThreads;
+  for (int32_t t0 = 0; t0 < cb; t0 += kLvChunk) {  // block-uniform
+    const int32_t k0 = t0 + threadIdx.x * PER;
+    int32_t dd[PER];
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      dd[j] = (k0 + j < cb) ? a.seg_d[base + k0 + j] : 0;
+      local += (uint32_t)dd[j];
+    }
+    uint32_t tile_total;
+    uint32_t run = eo + block_excl_sum(local, sm.red, &tile_total);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int32_t k = k0 + j;
+      if (k < cb) {
+        Q[vo + k] = a.seg_v[base + k];
+        S[vo + k] = (int32_t)run;
+        run += (uint32_t)dd[j];
+      }
+    }
+    eo += tile_total;
+  }
 }
 
 // Push level whose frontier exists only as a bitmap (the level after a
@@ -594,29 +677,6 @@ __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
 
 __device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t &gen);
 
-// Queue + degree scan of a frontier given as a bitmap (the level after a
-// pull switches back to push): each warp takes one word per round.
-__device__ void bitmap_to_queue(const BfsArgs &a, LevelSmem &sm, const uint32_t *F, int32_t *Q,
-                                int32_t *S, unsigned long long *counter) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long per_round = (long long)gridDim.x * kLvWarps;
-  const long long rounds = (a.nwords + per_round - 1) / per_round;
-  constexpr int kRoundsPerFlush = kLvChunk / kLvThreads;
-  for (long long r = 0; r < rounds; ++r) {
-    const long long w = (r * gridDim.x + blockIdx.x) * kLvWarps + wid;
-    bool take = false;
-    int32_t v = 0, d = 0;
-    if (w < a.nwords) {
-      const uint32_t fw = F[w];
-      v = (int32_t)(w * 32 + lane);
-      take = (fw >> lane) & 1u;
-      if (take) d = a.R[v + 1] - a.R[v];
-    }
-    emit(sm, take, v, d);
-    if ((r + 1) % kRoundsPerFlush == 0 || r == rounds - 1) flush(sm, counter, Q, S);
-  }
-}
-
 constexpr int kDoBlocksPerSm = 5;
 
 __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a) {
@@ -633,7 +693,6 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
     const int32_t L = level;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       c->cnt3[(L + 1) % 3] = 0ull;
-      c->cq3[(L + 1) % 3] = 0ull;
     }
     if (a.do_bitmap) {
       uint32_t *spare = bits_of(a, L + 2);
@@ -642,17 +701,15 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
         spare[w] = 0u;
     }
     unsigned long long *counter = &c->cnt3[L % 3];
+    if (threadIdx.x == 0) sm.segcnt = 0;
+    __syncthreads();
     if (dir == kPull) {
       pull_level(a, c, sm, L, counter);
     } else {
       int32_t qq = q, qe = (int32_t)mf;
       if (from_bitmap) {
-        bitmap_to_queue(a, sm, bits_of(a, L), queue_of(a, parity), scan_of(a, parity),
-                        &c->cq3[L % 3]);
+        segments_to_queue(a, sm, queue_of(a, parity), scan_of(a, parity), &qq, &qe);
         if (!grid_barrier(c, gridDim.x, gen)) break;
-        const unsigned long long pk = *(volatile unsigned long long *)&c->cq3[L % 3];
-        qq = (int32_t)(pk & 0xFFFFFFFFull);
-        qe = (int32_t)(pk >> 32);
       }
       push_level(a, c, sm, parity, L, qq, qe, counter);
     }
@@ -814,8 +871,11 @@ __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
 // ---------------------------------------------------------------- host
 size_t bfs_ws_bytes(const gr_graph *g) {
   const size_t n = (size_t)g->n;
+  const size_t seg = (size_t)g->nwords * 32 +
+                     (size_t)g->num_sms * kDoBlocksPerSm * kLvWarps * kPullWords * 32;
   return 2 * sizeof(int32_t) * (n + 1) + 2 * sizeof(int32_t) * (n + 2) +
-         4 * sizeof(uint32_t) * (size_t)g->nwords + sizeof(BfsCtl);
+         4 * sizeof(uint32_t) * (size_t)g->nwords + 2 * sizeof(int32_t) * seg +
+         sizeof(BfsCtl);
 }
 
 gr_status bfs_ws_create(gr_graph *g, cudaStream_t s, BfsWorkspace **out) {
@@ -828,6 +888,15 @@ gr_status bfs_ws_create(gr_graph *g, cudaStream_t s, BfsWorkspace **out) {
   GR_TRY(ws->visited.alloc(sizeof(uint32_t) * g->nwords, "visited bitmap"));
   for (int i = 0; i < 3; ++i)
     GR_TRY(ws->fb[i].alloc(sizeof(uint32_t) * g->nwords, "frontier bitmap"));
+  {
+    // segment capacity for any persistent grid of num_sms .. num_sms *
+    // kDoBlocksPerSm blocks (see bfs_run)
+    const size_t max_blocks = (size_t)g->num_sms * kDoBlocksPerSm;
+    const size_t entries = (size_t)g->nwords * 32 + max_blocks * kLvWarps * kPullWords * 32;
+    GR_TRY(ws->seg_v.alloc(sizeof(int32_t) * entries, "pull segments"));
+    GR_TRY(ws->seg_d.alloc(sizeof(int32_t) * entries, "pull segment degrees"));
+    GR_TRY(ws->seg_cnt.alloc(sizeof(unsigned long long) * max_blocks, "pull segment counts"));
+  }
   GR_TRY(ws->ctl.alloc(sizeof(BfsCtl), "BFS control"));
   GR_TRY(ws->h_ctl.alloc(sizeof(BfsCtl), "BFS control mirror"));
   GR_CUDA(cudaMemsetAsync(ws->ctl.p, 0, sizeof(BfsCtl), s));
@@ -852,6 +921,10 @@ static BfsArgs make_args(gr_graph *g, BfsWorkspace *ws, int32_t do_bitmap) {
   for (int i = 0; i < 3; ++i) a.fb[i] = ws->fb[i].as<uint32_t>();
   a.ctl = ws->ctl.as<BfsCtl>();
   a.do_bitmap = do_bitmap;
+  a.seg_v = nullptr;
+  a.seg_d = nullptr;
+  a.seg_cnt = nullptr;
+  a.seg_cap = 0;
   return a;
 }
 
@@ -948,6 +1021,17 @@ gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, in
     const int32_t want = o.block > 0 ? o.block : g->tuned_blocks_per_sm;
     if (want > 0) bps = std::min(bps, want);
     const int blocks = std::max(1, bps) * g->num_sms;
+    // per-block segments for the pull levels: a block handles at most
+    // `rounds` groups of kPullWords words per warp
+    const long long groups = (g->nwords + kPullWords - 1) / kPullWords;
+    const long long per_round = (long long)blocks * kLvWarps;
+    const long long rounds = (groups + per_round - 1) / per_round;
+    a.seg_cap = (int32_t)(rounds * kLvWarps * kPullWords * 32);
+    if ((size_t)blocks * a.seg_cap > ws->seg_v.bytes / sizeof(int32_t))
+      return fail(GR_ECUDA, "pull segment buffer too small");
+    a.seg_v = ws->seg_v.as<int32_t>();
+    a.seg_d = ws->seg_d.as<int32_t>();
+    a.seg_cnt = ws->seg_cnt.as<unsigned long long>();
     void *args[] = {&a};
     GR_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs_do, blocks, kLvThreads, args, 0, s));
   } else {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -31,6 +32,10 @@ gr_status cuda_fail(cudaError_t e, const char *what);
     gr_status s_ = (expr);                  \
     if (s_ != GR_OK) return s_;             \
   } while (0)
+
+// Host-side allocation-failure injection (gr_diag_fail_alloc): when >= 0,
+// the number of device allocations still allowed to succeed.
+extern std::atomic<int64_t> g_fail_alloc_after;
 
 // Device-side error codes written into control blocks.
 enum : int32_t { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2 };

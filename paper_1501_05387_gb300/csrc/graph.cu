@@ -31,6 +31,13 @@ gr_status cuda_fail(cudaError_t e, const char *what) {
 gr_status DevMem::alloc(size_t nbytes, const char *what) {
   reset();
   if (nbytes == 0) nbytes = 16;
+  for (int64_t left = g_fail_alloc_after.load(); left >= 0;
+       left = g_fail_alloc_after.load()) {
+    if (left == 0)
+      return fail(GR_ENOMEM, std::string("device allocation for ") + what +
+                                 " refused (injected failure)");
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) break;
+  }
   cudaError_t e = cudaMalloc(&p, nbytes);
   if (e != cudaSuccess) {
     p = nullptr;

@@ -146,6 +146,7 @@ struct SsspSmem {
   ScannedBuf<kSsspChunk> nearb;
   AppendBuf<kSsspChunk> farb;
   int32_t i[2];
+  int32_t sred[kSsspThreads / 32];
   int32_t last;
 };
 
@@ -160,14 +161,14 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   const unsigned long long T = c->T;
   const int32_t iter = c->iter, epoch = c->far_epoch;
   uint32_t *dist = c->dist;
-  const long long total = (long long)q + S[q];
+  const long long total = (long long)q + c->near_edges;
   const long long nchunks = (total + kSsspChunk - 1) / kSsspChunk;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kSsspChunk;
     const long long d1 = min(d0 + kSsspChunk, total);
-    if (threadIdx.x < 2) sm.i[threadIdx.x] = merge_count(S, q, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const int32_t i0 = sm.i[0], i1 = sm.i[1];
+    int32_t i0, i1;
+    block_chunk_bounds<kSsspThreads>(S, q, (int32_t)c->near_edges, d0, d1, kSsspChunk, sm.sred,
+                                     &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += kSsspThreads) {

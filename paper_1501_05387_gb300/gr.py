@@ -7,8 +7,10 @@ stream. A missing libgr.so raises ImportError: there is no fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -69,6 +71,8 @@ _sig("gr_bfs_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_bc", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_autotune", [_vp, _vp, _i32, _i32, _vp])
 _sig("gr_tuned_opts", [_vp, _P(gr_opts), _P(ctypes.c_double), _P(ctypes.c_double)])
+_sig("gr_diag_wait_timeout", [_i64, _vp])
+_sig("gr_diag_fail_alloc", [_i64])
 _sig("gr_server_create", [ctypes.c_size_t, _i32, _i32, _P(_vp)])
 _sig("gr_server_add_graph", [_vp, _vp, _i32, _P(_i32)])
 _sig("gr_server_submit", [_vp, _i32, _i32, _i32, _vp, _P(ctypes.c_uint64)])
@@ -297,12 +301,27 @@ def gr_tuned_opts(g: Graph):
             "delta": o.delta, "bfs_ms": b.value, "sssp_ms": s.value}
 
 
+_live_servers = weakref.WeakSet()
+
+
+@atexit.register
+def _close_servers():
+    # join every server's workers before the interpreter exits, so that no
+    # device work is in flight when the process ends
+    for srv in list(_live_servers):
+        try:
+            srv.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Owning wrapper of a gr_server handle."""
 
     def __init__(self, handle: int):
         self.handle = handle
         self.graphs = []  # keep the graphs alive as long as the server
+        _live_servers.add(self)
 
     def close(self):
         if self.handle:
@@ -367,6 +386,14 @@ def gr_server_stats(s: Server) -> dict:
 
 def gr_server_destroy(s: Server):
     s.close()
+
+
+def gr_diag_wait_timeout(spin_limit: int, stream=None):
+    _check(_lib.gr_diag_wait_timeout(int(spin_limit), _stream(stream)), "gr_diag_wait_timeout")
+
+
+def gr_diag_fail_alloc(after: int):
+    _check(_lib.gr_diag_fail_alloc(int(after)), "gr_diag_fail_alloc")
 
 
 def gr_last_error() -> str:
