@@ -295,6 +295,13 @@ gr_status gr_server_destroy(gr_server *s);
 gr_status gr_diag_wait_timeout(int64_t spin_limit, void *stream);
 gr_status gr_diag_fail_alloc(int64_t after);
 
+/* Bounds-guard report of a library built with GR_CHECKED (a diagnostic
+ * build whose kernels check every data-dependent index, record the first
+ * one outside its buffer and skip that access): *site identifies the
+ * access (0: no violation), *index and *bound the offending index and its
+ * buffer length. Normal builds always report 0. */
+gr_status gr_diag_guard(int32_t *site, int64_t *index, int64_t *bound);
+
 /* This thread's last error message ("" if none). The pointer stays valid
  * until this thread's next gr_* call. */
 const char *gr_last_error(void);

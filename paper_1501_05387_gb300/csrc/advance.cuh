@@ -397,7 +397,7 @@ __device__ __forceinline__ void emit_scanned(ScannedBuf<CAP> &b, bool take, int3
 // Block-uniform call; leaves b.cnt = 0.
 template <int THREADS, int CAP>
 __device__ void flush_scanned(ScannedBuf<CAP> &b, unsigned long long *packed, int32_t *Qn,
-                              int32_t *Sn) {
+                              int32_t *Sn, long long cap = (1ll << 62)) {
   static_assert(CAP % THREADS == 0, "buffer must split evenly over the block");
   constexpr int PER = CAP / THREADS;
   __syncthreads();
@@ -422,8 +422,10 @@ __device__ void flush_scanned(ScannedBuf<CAP> &b, unsigned long long *packed, in
     for (int j = 0; j < PER; ++j) {
       const int32_t k = k0 + j;
       if (k < cnt) {
-        Qn[vb + k] = b.out[k];
-        Sn[vb + k] = eb + (int32_t)run;
+        if (GR_IN(vb + k, cap, 501)) {
+          Qn[vb + k] = b.out[k];
+          Sn[vb + k] = eb + (int32_t)run;
+        }
         run += (uint32_t)b.deg[k];
       }
     }
@@ -455,15 +457,92 @@ __device__ __forceinline__ void emit_plain(AppendBuf<CAP> &b, bool take, int32_t
 }
 
 template <int THREADS, int CAP>
-__device__ void flush_plain(AppendBuf<CAP> &b, int32_t *len, int32_t *Q) {
+__device__ void flush_plain(AppendBuf<CAP> &b, int32_t *len, int32_t *Q,
+                            long long cap = (1ll << 62)) {
   __syncthreads();
   const int32_t cnt = b.cnt;
   if (threadIdx.x == 0 && cnt) b.base = atomicAdd(len, cnt);
   __syncthreads();
-  for (int32_t k = threadIdx.x; k < cnt; k += THREADS) Q[b.base + k] = b.out[k];
+  for (int32_t k = threadIdx.x; k < cnt; k += THREADS)
+    if (GR_IN((long long)b.base + k, cap, 502)) Q[b.base + k] = b.out[k];
   __syncthreads();
   if (threadIdx.x == 0) b.cnt = 0;
   __syncthreads();
+}
+
+}  // namespace gr
+
+namespace gr {
+
+// ------------------------------------------------------------ grid barrier
+// Barrier of the persistent (cooperative) kernels. Blocks arrive at one of
+// kBarrierGroups group counters; a group's last arriver clears it and
+// arrives at the root; the root's last arriver releases everyone by bumping
+// the generation. Every counter sits on its own 128-byte line so that the
+// waiters' polling does not slow the arrivals. The wait is bounded: after
+// kSpinLimit polls the block records kDevTimeout in *error and returns
+// false (callers then leave their loop; the other blocks time out too).
+constexpr int kBarrierGroups = 16;
+
+struct alignas(128) BarrierLine {
+  int32_t v;
+};
+
+struct GridBarrier {
+  BarrierLine group[kBarrierGroups];
+  BarrierLine root;
+  BarrierLine gen;
+};
+
+__device__ __forceinline__ void grid_barrier_reset(GridBarrier *b) {
+  for (int i = 0; i < kBarrierGroups; ++i) b->group[i].v = 0;
+  b->root.v = 0;
+  b->gen.v = 0;
+}
+
+// `gen` is the block's private count of barriers passed (starts at 0).
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, int32_t *error, int32_t &gen) {
+  __syncthreads();
+  bool ok = true;
+  __shared__ int32_t s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int32_t nblocks = gridDim.x;
+    const int32_t my_gen = gen;
+    const int32_t grp = blockIdx.x % kBarrierGroups;
+    const int32_t members = (nblocks - grp + kBarrierGroups - 1) / kBarrierGroups;
+    const int32_t groups = min(nblocks, kBarrierGroups);
+    bool release = false;
+    if (atomicAdd(&b->group[grp].v, 1) == members - 1) {
+      b->group[grp].v = 0;
+      __threadfence();
+      if (atomicAdd(&b->root.v, 1) == groups - 1) {
+        b->root.v = 0;
+        __threadfence();
+        release = true;
+      }
+    }
+    if (release) {
+      atomicExch(&b->gen.v, my_gen + 1);
+    } else {
+      int64_t spins = 0;
+      unsigned ns = 32;
+      while (*(volatile int32_t *)&b->gen.v == my_gen) {
+        if (++spins > kSpinLimit) {
+          atomicExch(error, kDevTimeout);
+          ok = false;
+          break;
+        }
+        __nanosleep(ns);
+        ns = ns < 256 ? ns * 2 : 256;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  gen += 1;
+  __syncthreads();
+  return s_ok != 0;
 }
 
 }  // namespace gr

@@ -49,12 +49,15 @@ struct BatchWorkspace {
 
 void free_batch(BatchWorkspace *ws) { delete ws; }
 
+GR_GUARD_REPORTER(guard_report_batch)
+
 namespace {
 
 struct MbArgs {
   const int32_t *R;
   const int32_t *C;
   int32_t n;
+  long long m;
   unsigned long long all;  // mask of the lanes in use
   unsigned long long *visit;
   const unsigned long long *cur;  // lm[L]
@@ -91,9 +94,9 @@ __global__ void k_mb_init(unsigned long long *visit, unsigned long long *lm0, do
 }
 
 __global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long *lm0,
-                             double *sigma) {
+                             double *sigma, int32_t n_vertices) {
   const int s = threadIdx.x;
-  if (s < k) {
+  if (s < k && GR_IN(srcs[s], n_vertices, 205)) {
     const int32_t v = srcs[s];
     atomicOr(lm0 + v, 1ull << s);
     if (sigma) sigma[(int64_t)v * 64 + s] = 1.0;
@@ -129,7 +132,8 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
         a.visit[v] = seen;
         if (a.depth) {
           for (int s = 0; s < a.k; ++s)
-            if ((c >> s) & 1ull) a.depth[(int64_t)s * a.n + v] = a.level;
+            if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 204))
+            a.depth[(int64_t)s * a.n + v] = a.level;
         }
       }
       s_off[kk] = a.R[v];
@@ -150,10 +154,11 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
           else hi = mid - 1;
         }
         owner = i0 + lo;
-        const unsigned long long U = s_U[lo];
-        if (U) {
+        if (!GR_IN(owner, a.n, 201)) owner = -1;
+        const unsigned long long U = owner >= 0 ? s_U[lo] : 0ull;
+        if (U && GR_IN(e, a.m, 202)) {
           u = a.C[e];
-          bits = a.cur[u] & U;
+          bits = GR_IN(u, a.n, 203) ? (a.cur[u] & U) : 0ull;
         }
       }
       if (!SIGMA) {
@@ -392,12 +397,13 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
                                  with_sigma ? ws->q.as<double>() : nullptr, g->n);
   GR_CUDA(cudaMemcpyAsync(ws->srcs.p, h_srcs, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
   k_mb_sources<<<1, 64, 0, s>>>(ws->srcs.as<int32_t>(), k, lm0,
-                                with_sigma ? ws->sigma.as<double>() : nullptr);
+                                with_sigma ? ws->sigma.as<double>() : nullptr, g->n);
   GR_CUDA(cudaGetLastError());
   MbArgs a;
   a.R = g->row_off.as<int32_t>();
   a.C = g->col.as<int32_t>();
   a.n = g->n;
+  a.m = g->m;
   a.all = k == 64 ? ~0ull : ((1ull << k) - 1ull);
   a.visit = ws->visit.as<unsigned long long>();
   a.sigma = with_sigma ? ws->sigma.as<double>() : nullptr;

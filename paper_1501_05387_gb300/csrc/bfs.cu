@@ -78,17 +78,9 @@ struct BfsCtl {
   int32_t tr_q[64];
   long long tr_mf[64];
   unsigned long long tr_t[64];
-  // grid barrier of the persistent kernels: group counters, root counter
-  // and release generation, each on its own 128-byte line
-  struct alignas(128) Line {
-    int32_t v;
-  };
-  Line bar_group[16];
-  Line bar_root;
-  Line bar_gen;
+  GridBarrier bar;  // persistent kernels' grid barrier
 };
 constexpr int kTraceLevels = 64;
-constexpr int kBarrierGroups = 16;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -140,6 +132,8 @@ struct BfsWorkspace {
 };
 
 void free_bfs(BfsWorkspace *ws) { delete ws; }
+
+GR_GUARD_REPORTER(guard_report_bfs)
 
 // ------------------------------------------------------------- kernels
 namespace {
@@ -195,9 +189,7 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     c->policy = policy;
     c->max_levels = max_levels;
     c->blocks_done = 0;
-    for (int i = 0; i < kBarrierGroups; ++i) c->bar_group[i].v = 0;
-    c->bar_root.v = 0;
-    c->bar_gen.v = 0;
+    grid_barrier_reset(&c->bar);
     c->next_packed = 0ull;
     c->mf = dsrc;
     c->mu = a.m - dsrc;
@@ -246,7 +238,8 @@ __device__ __forceinline__ void emit(LevelSmem &sm, bool take, int32_t v, int32_
 
 // Write the emit buffer to the next queue with its exclusive degree scan,
 // reserving both ranges with one packed atomicAdd. Block-uniform call.
-__device__ void flush(LevelSmem &sm, unsigned long long *counter, int32_t *Qn, int32_t *Sn) {
+__device__ void flush(LevelSmem &sm, unsigned long long *counter, int32_t *Qn, int32_t *Sn,
+                      int32_t cap) {
   __syncthreads();
   const int32_t cnt = sm.cnt;
   if (cnt) {  // block-uniform
@@ -270,8 +263,10 @@ __device__ void flush(LevelSmem &sm, unsigned long long *counter, int32_t *Qn, i
     for (int j = 0; j < PER; ++j) {
       const int32_t k = k0 + j;
       if (k < cnt) {
-        Qn[vb + k] = sm.out[k];
-        Sn[vb + k] = eb + (int32_t)run;
+        if (GR_IN(vb + k, cap, 118)) {
+          Qn[vb + k] = sm.out[k];
+          Sn[vb + k] = eb + (int32_t)run;
+        }
         run += (uint32_t)sm.deg[k];
       }
     }
@@ -300,10 +295,11 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += kLvThreads) {
-      const int32_t u = Q[i0 + k];
-      sm.off[k] = (i0 + k == q) ? q_edges : S[i0 + k];
+      const int32_t i = i0 + k;
+      const int32_t u = GR_IN(i, a.n + 1, 110) ? Q[i] : 0;
+      sm.off[k] = (i == q) ? q_edges : (GR_IN(i, a.n + 2, 111) ? S[i] : 0);
       sm.u[k] = u;
-      sm.row[k] = a.R[u];
+      sm.row[k] = GR_IN(u, a.n + 1, 112) ? a.R[u] : 0;
     }
     __syncthreads();
     const int32_t ne = (int32_t)(j1 - j0);  // <= kLvChunk: one pass of kLvItems per thread
@@ -326,7 +322,9 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
           else hi = mid - 1;
         }
         uo[j] = sm.u[lo];
-        v[j] = a.C[sm.row[lo] + (er - sm.off[lo])];
+        const long long e = (long long)sm.row[lo] + (er - sm.off[lo]);
+        v[j] = GR_IN(e, a.m, 113) ? a.C[e] : -1;
+        if (v[j] >= 0 && !GR_IN(v[j], a.n, 114)) v[j] = -1;
       }
     }
     uint32_t vw[kLvItems];
@@ -352,7 +350,7 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
     }
 #pragma unroll
     for (int j = 0; j < kLvItems; ++j) emit(sm, won[j], v[j], dv[j]);
-    flush(sm, counter, Qn, Sn);
+    flush(sm, counter, Qn, Sn, a.n + 1);
   }
 }
 
@@ -394,11 +392,15 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
       if (act[j]) {
         r0[j] = a.R[v[j]];
         r1[j] = a.R[v[j] + 1];
+        if (!GR_IN(r0[j], a.m + 1, 120) || !GR_IN(r1[j], a.m + 1, 121)) r1[j] = r0[j] = 0;
       }
     // first neighbour of every vertex, independent loads
     int32_t u1[kPullWords];
 #pragma unroll
-    for (int j = 0; j < kPullWords; ++j) u1[j] = (act[j] && r0[j] < r1[j]) ? a.C[r0[j]] : -1;
+    for (int j = 0; j < kPullWords; ++j) {
+      u1[j] = (act[j] && r0[j] < r1[j]) ? a.C[r0[j]] : -1;
+      if (u1[j] >= 0 && !GR_IN(u1[j], a.n, 122)) u1[j] = -1;
+    }
 #pragma unroll
     for (int j = 0; j < kPullWords; ++j)
       if (u1[j] >= 0 && test_bit(F, u1[j])) {
@@ -413,7 +415,7 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
         const int32_t stop = min(r1[j], r0[j] + 1 + kPullLane);
         for (int32_t e = r0[j] + 1; e < stop; ++e) {
           const int32_t u = a.C[e];
-          if (test_bit(F, u)) {
+          if (GR_IN(u, a.n, 123) && test_bit(F, u)) {
             fnd[j] = true;
             uf[j] = u;
             break;
@@ -430,7 +432,7 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
         for (int32_t base = b0; base < b1; base += 32) {
           const int32_t e = base + lane;
           const int32_t u = e < b1 ? a.C[e] : 0;
-          const bool hit = e < b1 && test_bit(F, u);
+          const bool hit = e < b1 && GR_IN(u, a.n, 124) && test_bit(F, u);
           const uint32_t hb = __ballot_sync(0xffffffffu, hit);
           if (hb) {
             const int32_t hu = __shfl_sync(0xffffffffu, u, __ffs(hb) - 1);
@@ -459,10 +461,12 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
         if (lane == 0) pos = atomicAdd(&sm.segcnt, __popc(fm));
         pos = __shfl_sync(0xffffffffu, pos, 0);
         if (fnd[j]) {
-          const int64_t k = (int64_t)blockIdx.x * a.seg_cap + pos +
-                            __popc(fm & ((1u << lane) - 1u));
-          a.seg_v[k] = v[j];
-          a.seg_d[k] = r1[j] - r0[j];
+          const int64_t kk = pos + __popc(fm & ((1u << lane) - 1u));
+          const int64_t k = (int64_t)blockIdx.x * a.seg_cap + kk;
+          if (GR_IN(kk, a.seg_cap, 125)) {
+            a.seg_v[k] = v[j];
+            a.seg_d[k] = r1[j] - r0[j];
+          }
         }
       }
     }
@@ -504,7 +508,7 @@ __device__ void segments_to_queue(const BfsArgs &a, LevelSmem &sm, int32_t *Q, i
     uint32_t local = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-      dd[j] = (k0 + j < cb) ? a.seg_d[base + k0 + j] : 0;
+      dd[j] = (k0 + j < cb && GR_IN(k0 + j, a.seg_cap, 128)) ? a.seg_d[base + k0 + j] : 0;
       local += (uint32_t)dd[j];
     }
     uint32_t tile_total;
@@ -513,8 +517,10 @@ __device__ void segments_to_queue(const BfsArgs &a, LevelSmem &sm, int32_t *Q, i
     for (int j = 0; j < PER; ++j) {
       const int32_t k = k0 + j;
       if (k < cb) {
-        Q[vo + k] = a.seg_v[base + k];
-        S[vo + k] = (int32_t)run;
+        if (GR_IN(vo + k, a.n + 1, 126) && GR_IN(k, a.seg_cap, 127)) {
+          Q[vo + k] = a.seg_v[base + k];
+          S[vo + k] = (int32_t)run;
+        }
         run += (uint32_t)dd[j];
       }
     }
@@ -549,16 +555,18 @@ __device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t
         const int32_t e = base + lane;
         bool won = false;
         int32_t v = 0, dv = 0;
-        if (e < r1) {
+        if (e < r1 && GR_IN(e, a.m, 130)) {
           v = a.C[e];
-          const uint32_t mask = 1u << (v & 31);
-          uint32_t *vw = a.visited + (v >> 5);
-          if (!(*vw & mask)) won = !(atomicOr(vw, mask) & mask);
-          if (won) {
-            depth[v] = L + 1;
-            if (parent) parent[v] = u;
-            if (a.do_bitmap) atomicOr(N + (v >> 5), mask);
-            dv = a.R[v + 1] - a.R[v];
+          if (GR_IN(v, a.n, 131)) {
+            const uint32_t mask = 1u << (v & 31);
+            uint32_t *vw = a.visited + (v >> 5);
+            if (!(*vw & mask)) won = !(atomicOr(vw, mask) & mask);
+            if (won) {
+              depth[v] = L + 1;
+              if (parent) parent[v] = u;
+              if (a.do_bitmap) atomicOr(N + (v >> 5), mask);
+              dv = a.R[v + 1] - a.R[v];
+            }
           }
         }
         const uint32_t b = __ballot_sync(0xffffffffu, won);
@@ -572,8 +580,10 @@ __device__ void push_from_bitmap(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t
           old = __shfl_sync(0xffffffffu, old, 0);
           if (won) {
             const int32_t k = (int32_t)(old & 0xFFFFFFFFull) + __popc(b & ((1u << lane) - 1u));
-            Qn[k] = v;
-            Sn[k] = (int32_t)(old >> 32) + (int32_t)(incl - dv);
+            if (GR_IN(k, a.n + 1, 132)) {
+              Qn[k] = v;
+              Sn[k] = (int32_t)(old >> 32) + (int32_t)(incl - dv);
+            }
           }
         }
       }
@@ -619,7 +629,7 @@ __device__ void level_end(const BfsArgs &a, BfsCtl *c) {
   c->next_packed = 0ull;
   c->mf = mf;
   c->mu -= mf;
-  if (!was_pull) scan_of(a, c->parity)[qn] = (int32_t)mf;
+  if (!was_pull && GR_IN(qn, a.n + 2, 140)) scan_of(a, c->parity)[qn] = (int32_t)mf;
   if (qn == 0) {
     c->done = 1;
     return;
@@ -755,46 +765,8 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
 constexpr int kPersThreads = 256;
 
 __device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t &gen) {
-  __syncthreads();
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const int32_t my_gen = gen;
-    // arrive at this block's group counter; the group's last arriver
-    // clears it and arrives at the root; the root's last arriver releases
-    const int32_t grp = blockIdx.x % kBarrierGroups;
-    const int32_t members = (nblocks - grp + kBarrierGroups - 1) / kBarrierGroups;
-    const int32_t groups = min(nblocks, kBarrierGroups);
-    bool release = false;
-    if (atomicAdd(&c->bar_group[grp].v, 1) == members - 1) {
-      c->bar_group[grp].v = 0;
-      __threadfence();
-      if (atomicAdd(&c->bar_root.v, 1) == groups - 1) {
-        c->bar_root.v = 0;
-        __threadfence();
-        release = true;
-      }
-    }
-    if (release) {
-      atomicExch(&c->bar_gen.v, my_gen + 1);
-    } else {
-      int64_t spins = 0;
-      unsigned ns = 32;
-      while (*(volatile int32_t *)&c->bar_gen.v == my_gen) {
-        if (++spins > kSpinLimit) {
-          atomicExch(&c->error, kDevTimeout);
-          ok = false;
-          break;
-        }
-        __nanosleep(ns);
-        ns = ns < 256 ? ns * 2 : 256;
-      }
-    }
-    __threadfence();
-  }
-  gen += 1;
-  __syncthreads();
-  return ok;
+  (void)nblocks;
+  return grid_sync(&c->bar, &c->error, gen);
 }
 
 // level end of the persistent kernel (push only, no degree scan)
@@ -856,7 +828,8 @@ __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
             pos = (int32_t)(atomicAdd(&c->next_packed, (unsigned long long)__popc(bal)) &
                             0xFFFFFFFFull);
           pos = __shfl_sync(0xffffffffu, pos, 0);
-          if (won) Qn[pos + __popc(bal & ((1u << lane) - 1u))] = v;
+          const int32_t k = pos + __popc(bal & ((1u << lane) - 1u));
+          if (won && GR_IN(k, a.n + 1, 150)) Qn[k] = v;
         }
       }
     }

@@ -33,6 +33,8 @@ struct CcWorkspace {
 
 void free_cc(CcWorkspace *ws) { delete ws; }
 
+GR_GUARD_REPORTER(guard_report_cc)
+
 namespace {
 
 __global__ void k_cc_init(int32_t *label, int32_t n) {
@@ -56,7 +58,9 @@ __device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x) {
 struct HookF {
   int32_t *label;
   int32_t only_lower;  // symmetric graph: hook each undirected edge once
+  int32_t n;
   __device__ __forceinline__ int operator()(int32_t u, int32_t v, int32_t) const {
+    if (!GR_IN(u, n, 401) || !GR_IN(v, n, 402)) return 0;
     if (only_lower && v >= u) return 0;
     int32_t a = find_root(label, u);
     int32_t b = find_root(label, v);
@@ -75,7 +79,7 @@ struct HookF {
 __global__ void __launch_bounds__(kCcThreads) k_cc_hook(const int32_t *R, const int32_t *C,
                                                          int32_t n, int32_t *label,
                                                          int32_t only_lower) {
-  HookF f{label, only_lower};
+  HookF f{label, only_lower, n};
   int32_t dummy = 0;
   lb_advance<kCcThreads, kCcItems, 1>(R, C, nullptr, n, R, f, nullptr, &dummy, nullptr,
                                       &dummy);

@@ -51,6 +51,24 @@ gr_status gr_diag_wait_timeout(int64_t spin_limit, void *stream) {
   return GR_OK;
 }
 
+gr_status gr_diag_guard(int32_t *site, int64_t *index, int64_t *bound) {
+  clear_error();
+  gr_status (*reporters[])(GuardRec *) = {guard_report_bfs, guard_report_batch,
+                                          guard_report_sssp, guard_report_cc, guard_report_pr};
+  if (site) *site = 0;
+  for (auto rep : reporters) {
+    GuardRec r;
+    GR_TRY(rep(&r));
+    if (r.hit) {
+      if (site) *site = r.site;
+      if (index) *index = r.idx;
+      if (bound) *bound = r.bound;
+      break;
+    }
+  }
+  return GR_OK;
+}
+
 gr_status gr_diag_fail_alloc(int64_t after) {
   clear_error();
   g_fail_alloc_after.store(after < 0 ? -1 : after);

@@ -102,6 +102,8 @@ struct gr_graph {
   int32_t tuned_mode = GR_MODE_AUTO;
   int32_t tuned_direction = GR_DIR_AUTO;  // GR_DIR_PUSH: never pull
   int32_t tuned_blocks_per_sm = 0;  // persistent BFS grid (0: all resident)
+  int32_t tuned_sssp_mode = GR_MODE_GRAPH;
+  int32_t tuned_sssp_blocks_per_sm = 0;
   double tuned_bfs_ms = 0.0, tuned_sssp_ms = 0.0;  // measured by gr_autotune
   double mean_weight = 0.0;
 
@@ -166,6 +168,54 @@ void free_sssp(SsspWorkspace *);
 void free_cc(CcWorkspace *);
 void free_pr(PrWorkspace *);
 void free_batch(BatchWorkspace *);
+
+// ------------------------------------------------------ bounds guards
+// In a GR_CHECKED build every data-dependent index of the kernels is checked
+// before use: an index outside its buffer records (site, index, bound) in a
+// per-translation-unit record and the access is skipped; gr_diag_guard
+// reports the first record. Normal builds compile the checks away.
+struct GuardRec {
+  int32_t hit;
+  int32_t site;
+  long long idx;
+  long long bound;
+};
+
+#ifdef GR_CHECKED
+namespace {
+__device__ GuardRec g_guard_rec;
+__device__ __noinline__ void gr_guard_fail(int site, long long idx, long long bound) {
+  if (atomicCAS(&g_guard_rec.hit, 0, 1) == 0) {
+    g_guard_rec.site = site;
+    g_guard_rec.idx = idx;
+    g_guard_rec.bound = bound;
+  }
+}
+}  // namespace
+#define GR_IN(idx, bound, site)                                                  \
+  ((((long long)(idx)) >= 0 && ((long long)(idx)) < ((long long)(bound)))        \
+       ? true                                                                    \
+       : (gr_guard_fail((site), (long long)(idx), (long long)(bound)), false))
+#define GR_GUARD_REPORTER(name)                                                  \
+  gr_status name(GuardRec *out) {                                                \
+    GR_CUDA(cudaMemcpyFromSymbol(out, g_guard_rec, sizeof(GuardRec)));           \
+    return GR_OK;                                                                \
+  }
+#else
+#define GR_IN(idx, bound, site) true
+#define GR_GUARD_REPORTER(name)                                                  \
+  gr_status name(GuardRec *out) {                                                \
+    out->hit = 0;                                                                \
+    return GR_OK;                                                                \
+  }
+#endif
+
+// one reporter per translation unit with guarded kernels
+gr_status guard_report_bfs(GuardRec *);
+gr_status guard_report_batch(GuardRec *);
+gr_status guard_report_sssp(GuardRec *);
+gr_status guard_report_cc(GuardRec *);
+gr_status guard_report_pr(GuardRec *);
 
 // ------------------------------------------------------ device helpers
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

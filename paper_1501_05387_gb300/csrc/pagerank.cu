@@ -53,6 +53,8 @@ struct PrWorkspace {
 
 void free_pr(PrWorkspace *ws) { delete ws; }
 
+GR_GUARD_REPORTER(guard_report_pr)
+
 namespace {
 
 struct PrArgs {

@@ -147,9 +147,14 @@ gr_status copy_out(const Request &r, const void *dev, size_t bytes, cudaStream_t
 }  // namespace
 
 void Server::worker(int slot) {
+  (void)slot;
   cudaSetDevice(device);
-  cudaStream_t s;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+  cudaStream_t s = nullptr;
+  // a slot without a stream still drains its requests, failing them, so
+  // that waiters never hang
+  const cudaError_t se = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  const std::string stream_err =
+      se == cudaSuccess ? std::string() : std::string("server slot stream: ") + cudaGetErrorString(se);
   std::map<int32_t, SlotGraphState> state;  // per graph
   DevMem buf;                               // result staging for this slot
   for (;;) {
@@ -179,7 +184,8 @@ void Server::worker(int slot) {
     const size_t need = nbytes * rs.size();
     gr_status status = GR_OK;
     std::string err;
-    if (buf.bytes < need) status = buf.alloc(need, "server result buffer");
+    if (!stream_err.empty()) status = fail(GR_ECUDA, stream_err);
+    if (status == GR_OK && buf.bytes < need) status = buf.alloc(need, "server result buffer");
     // graph-mode level loops: several slots may run traversals at once, so
     // no launch may need the whole GPU to itself (cooperative launches do)
     gr_opts o = default_opts();
@@ -224,7 +230,10 @@ void Server::worker(int slot) {
         if (e != cudaSuccess) status = cuda_fail(e, "server stream");
       }
     }
-    if (status != GR_OK) err = gr_last_error();
+    if (status != GR_OK)
+      err = std::string(gr_last_error()) + " [batch: kind " + std::to_string(first.kind) +
+            ", graph " + std::to_string(first.graph) + ", lanes " + std::to_string(rs.size()) +
+            ", first source " + std::to_string(first.src) + "]";
     const double t = now_ms();
     {
       std::lock_guard<std::mutex> lock(mu);
@@ -252,7 +261,7 @@ void Server::worker(int slot) {
     cv_work.notify_all();
   }
   state.clear();
-  cudaStreamDestroy(s);
+  if (s) cudaStreamDestroy(s);
 }
 
 }  // namespace gr

@@ -62,6 +62,11 @@ struct SsspCtl {
   unsigned long long delta;
   long long near_edges;   // edges of the current near frontier
   long long relaxations;  // edges expanded (statistics)
+  // persistent kernel: counter rings and grid barrier
+  unsigned long long ring_near[3];
+  int32_t ring_far[3];
+  uint32_t ring_fmin[3];
+  GridBarrier bar;
 };
 
 struct SsspArgs {
@@ -69,6 +74,7 @@ struct SsspArgs {
   const int32_t *C;
   const uint32_t *W;
   int32_t n;
+  long long m;
   int32_t *nearq[2];
   int32_t *nearS[2];
   int32_t *farq[2];
@@ -92,6 +98,8 @@ struct SsspWorkspace {
 };
 
 void free_sssp(SsspWorkspace *ws) { delete ws; }
+
+GR_GUARD_REPORTER(guard_report_sssp)
 
 namespace {
 
@@ -136,6 +144,12 @@ __global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pr
     c->T_old = 0;
     c->near_edges = dsrc;
     c->relaxations = 0;
+    for (int i = 0; i < 3; ++i) {
+      c->ring_near[i] = 0ull;
+      c->ring_far[i] = 0;
+      c->ring_fmin[i] = 0xFFFFFFFFu;
+    }
+    grid_barrier_reset(&c->bar);
   }
 }
 
@@ -150,32 +164,47 @@ struct SsspSmem {
   int32_t last;
 };
 
-__device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
-  const int32_t np = c->near_parity;
+// The state one iteration reads and the counters it fills; the graph-mode
+// kernel takes them from the control block, the persistent kernel from
+// block-private copies and a ring of counters.
+struct SsspStep {
+  int32_t near_parity, far_parity;
+  int32_t q;              // near frontier size
+  int32_t q_edges;        // its edges (S[q])
+  int32_t far_len;        // current far pile size (split input)
+  unsigned long long T, T_old;
+  int32_t iter, far_epoch;
+  unsigned long long *near_ctr;  // packed (vertices, edges) of the next near frontier
+  int32_t *far_ctr;              // far appends (relax) or far-next size (split)
+  int32_t *far_dest;             // where far appends land (pile start + base)
+  long long far_cap;             // entries available at far_dest
+  uint32_t *fmin;                // min distance sent to the far pile
+};
+
+__device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, const SsspStep &st) {
+  const int32_t np = st.near_parity;
   const int32_t *Q = pick(a.nearq, np);
   const int32_t *S = pick(a.nearS, np);
   int32_t *Qn = pick(a.nearq, np ^ 1);
   int32_t *Sn = pick(a.nearS, np ^ 1);
-  int32_t *F = pick(a.farq, c->far_parity);
-  const int32_t q = c->near_len;
-  const unsigned long long T = c->T;
-  const int32_t iter = c->iter, epoch = c->far_epoch;
-  uint32_t *dist = c->dist;
-  const long long total = (long long)q + c->near_edges;
+  const int32_t q = st.q;
+  const unsigned long long T = st.T;
+  const int32_t iter = st.iter, epoch = st.far_epoch;
+  const long long total = (long long)q + st.q_edges;
   const long long nchunks = (total + kSsspChunk - 1) / kSsspChunk;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kSsspChunk;
     const long long d1 = min(d0 + kSsspChunk, total);
     int32_t i0, i1;
-    block_chunk_bounds<kSsspThreads>(S, q, (int32_t)c->near_edges, d0, d1, kSsspChunk, sm.sred,
-                                     &i0, &i1);
+    block_chunk_bounds<kSsspThreads>(S, q, st.q_edges, d0, d1, kSsspChunk, sm.sred, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += kSsspThreads) {
-      const int32_t u = Q[i0 + k];
-      sm.off[k] = S[i0 + k];
-      sm.u[k] = u;
-      sm.row[k] = a.R[u];
+      const int32_t i = i0 + k;
+      const int32_t u = GR_IN(i, a.n + 1, 301) ? Q[i] : 0;
+      sm.off[k] = GR_IN(i, a.n + 2, 302) ? S[i] : 0;
+      sm.u[k] = GR_IN(u, a.n, 303) ? u : 0;
+      sm.row[k] = a.R[sm.u[k]];
     }
     __syncthreads();
     const int32_t ne = (int32_t)(j1 - j0);
@@ -192,8 +221,11 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
           else hi = mid - 1;
         }
         const int32_t e = sm.row[lo] + (er - sm.off[lo]);
-        v = a.C[e];
-        const unsigned long long nd = (unsigned long long)dist[sm.u[lo]] + a.W[e];
+        const bool e_ok = GR_IN(e, a.m, 304);
+        v = e_ok ? a.C[e] : 0;
+        const bool v_ok = e_ok && GR_IN(v, a.n, 305);
+        const unsigned long long nd =
+            v_ok ? (unsigned long long)dist[sm.u[lo]] + a.W[e] : 0xFFFFFFFFull;
         if (nd < 0xFFFFFFFFull) {  // else not representable: no improvement
           const uint32_t nd32 = (uint32_t)nd;
           if (nd32 < dist[v]) {  // plain-load cull
@@ -205,7 +237,7 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
                   dv = a.R[v + 1] - a.R[v];
                 }
               } else {
-                atomicMin(&c->far_min, nd32);
+                atomicMin(st.fmin, nd32);
                 if (atomicExch(a.far_stamp + v, epoch) != epoch) code = 2;
               }
             }
@@ -215,21 +247,20 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
       emit_scanned(sm.nearb, code == 1, v, dv);
       emit_plain(sm.farb, code == 2, v);
     }
-    flush_scanned<kSsspThreads>(sm.nearb, &c->near_next_packed, Qn, Sn);
-    flush_plain<kSsspThreads>(sm.farb, &c->far_len, F);
+    flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.n + 1);
+    flush_plain<kSsspThreads>(sm.farb, st.far_ctr, st.far_dest, st.far_cap);
   }
 }
 
-__device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
-  const int32_t *F = pick(a.farq, c->far_parity);
-  int32_t *Fn = pick(a.farq, c->far_parity ^ 1);
-  const int32_t np = c->near_parity;
+__device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm,
+                           const SsspStep &st) {
+  const int32_t *F = pick(a.farq, st.far_parity);
+  const int32_t np = st.near_parity;
   int32_t *Qn = pick(a.nearq, np ^ 1);
   int32_t *Sn = pick(a.nearS, np ^ 1);
-  const int32_t len = c->far_len;
-  const unsigned long long T = c->T, T_old = c->T_old;
-  const int32_t iter = c->iter, epoch = c->far_epoch + 1;
-  const uint32_t *dist = c->dist;
+  const int32_t len = st.far_len;
+  const unsigned long long T = st.T, T_old = st.T_old;
+  const int32_t iter = st.iter, epoch = st.far_epoch + 1;
   uint32_t local_min = 0xFFFFFFFFu;
   const long long per_round = (long long)gridDim.x * kSsspThreads;
   const long long rounds = (len + per_round - 1) / per_round;
@@ -237,7 +268,7 @@ __device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
     const long long i = (r * gridDim.x + blockIdx.x) * kSsspThreads + threadIdx.x;
     int code = 0;
     int32_t v = 0, dv = 0;
-    if (i < len) {
+    if (i < len && GR_IN(i, a.n + 1, 310) && GR_IN(F[i], a.n, 311)) {
       v = F[i];
       const uint32_t d = dist[v];
       if ((unsigned long long)d < T_old) {
@@ -255,12 +286,50 @@ __device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
     emit_scanned(sm.nearb, code == 1, v, dv);
     emit_plain(sm.farb, code == 2, v);
     if ((r + 1) % (kSsspChunk / kSsspThreads) == 0 || r == rounds - 1) {
-      flush_scanned<kSsspThreads>(sm.nearb, &c->near_next_packed, Qn, Sn);
-      flush_plain<kSsspThreads>(sm.farb, &c->far_next_len, Fn);
+      flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.n + 1);
+      flush_plain<kSsspThreads>(sm.farb, st.far_ctr, st.far_dest, st.far_cap);
     }
   }
   for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
-  if ((threadIdx.x & 31) == 0 && local_min != 0xFFFFFFFFu) atomicMin(&c->far_min_next, local_min);
+  if ((threadIdx.x & 31) == 0 && local_min != 0xFFFFFFFFu) atomicMin(st.fmin, local_min);
+}
+
+__device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
+  SsspStep st;
+  st.near_parity = c->near_parity;
+  st.far_parity = c->far_parity;
+  st.q = c->near_len;
+  st.q_edges = (int32_t)c->near_edges;
+  st.far_len = c->far_len;
+  st.T = c->T;
+  st.T_old = c->T_old;
+  st.iter = c->iter;
+  st.far_epoch = c->far_epoch;
+  st.near_ctr = &c->near_next_packed;
+  st.far_ctr = &c->far_len;  // absolute positions in the current pile
+  st.far_dest = pick(a.farq, c->far_parity);
+  st.far_cap = a.n + 1;
+  st.fmin = &c->far_min;
+  relax_body(a, c->dist, sm, st);
+}
+
+__device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
+  SsspStep st;
+  st.near_parity = c->near_parity;
+  st.far_parity = c->far_parity;
+  st.q = c->near_len;
+  st.q_edges = (int32_t)c->near_edges;
+  st.far_len = c->far_len;
+  st.T = c->T;
+  st.T_old = c->T_old;
+  st.iter = c->iter;
+  st.far_epoch = c->far_epoch;
+  st.near_ctr = &c->near_next_packed;
+  st.far_ctr = &c->far_next_len;
+  st.far_dest = pick(a.farq, c->far_parity ^ 1);
+  st.far_cap = a.n + 1;
+  st.fmin = &c->far_min_next;
+  split_body(a, c->dist, sm, st);
 }
 
 __device__ __forceinline__ unsigned long long bucket_end(uint32_t d, unsigned long long delta) {
@@ -337,6 +406,106 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
   }
 }
 
+// Persistent form: the whole SSSP in one cooperative kernel, one grid
+// barrier per iteration. After the barrier every block reads the
+// iteration's counters and recomputes the same next state in registers; the
+// counters form rings of three (the one an iteration fills, the one just
+// read, the one block 0 clears for the next iteration).
+__global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(SsspArgs a) {
+  SsspCtl *c = a.ctl;
+  __shared__ SsspSmem sm;
+  if (threadIdx.x == 0) {
+    sm.nearb.cnt = 0;
+    sm.farb.cnt = 0;
+  }
+  __syncthreads();
+  uint32_t *dist = c->dist;
+  const unsigned long long delta = c->delta;
+  const int32_t max_iters = c->max_iters;
+  int32_t mode = kSsspRelax, near_parity = 0, far_parity = 0, near_len = 1, far_len = 0;
+  long long near_edges = c->near_edges, relaxations = 0;
+  int32_t iter = 0, far_epoch = 0, phases = 0, gen = 0;
+  uint32_t far_min = 0xFFFFFFFFu;
+  unsigned long long T = delta, T_old = 0;
+  bool timed_out = false;
+  for (;;) {
+    const int32_t slot = iter % 3, clear = (iter + 1) % 3;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->ring_near[clear] = 0ull;
+      c->ring_far[clear] = 0;
+      c->ring_fmin[clear] = 0xFFFFFFFFu;
+    }
+    SsspStep st;
+    st.near_parity = near_parity;
+    st.far_parity = far_parity;
+    st.q = near_len;
+    st.q_edges = (int32_t)near_edges;
+    st.far_len = far_len;
+    st.T = T;
+    st.T_old = T_old;
+    st.iter = iter;
+    st.far_epoch = far_epoch;
+    st.near_ctr = &c->ring_near[slot];
+    st.far_ctr = &c->ring_far[slot];
+    st.fmin = &c->ring_fmin[slot];
+    if (mode == kSsspRelax) {
+      st.far_dest = pick(a.farq, far_parity) + far_len;  // appended after the pile
+      st.far_cap = (long long)a.n + 1 - far_len;
+      relax_body(a, dist, sm, st);
+    } else {
+      st.far_dest = pick(a.farq, far_parity ^ 1);
+      st.far_cap = a.n + 1;
+      split_body(a, dist, sm, st);
+    }
+    if (!grid_sync(&c->bar, &c->error, gen)) {
+      timed_out = true;
+      break;
+    }
+    const unsigned long long pk = *(volatile unsigned long long *)&c->ring_near[slot];
+    const int32_t fcnt = *(volatile int32_t *)&c->ring_far[slot];
+    const uint32_t fmin = *(volatile uint32_t *)&c->ring_fmin[slot];
+    if (mode == kSsspRelax) {
+      relaxations += near_edges;
+      far_len += fcnt;
+      far_min = min(far_min, fmin);
+    } else {
+      far_len = fcnt;
+      far_parity ^= 1;
+      far_epoch += 1;
+      far_min = fmin;
+      phases += 1;
+    }
+    near_len = (int32_t)(pk & 0xFFFFFFFFull);
+    near_edges = (long long)(pk >> 32);
+    near_parity ^= 1;
+    iter += 1;
+    bool done = false, overflow = false;
+    if (near_len > 0) {
+      mode = kSsspRelax;
+    } else if (far_len > 0) {
+      mode = kSsspSplit;
+      T_old = T;
+      const unsigned long long t = T + delta;
+      const unsigned long long j = bucket_end(far_min, delta);
+      T = t > j ? t : j;
+    } else {
+      done = true;
+    }
+    if (!done && iter >= max_iters) overflow = true;
+    if (done || overflow) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->iter = iter;
+        c->phases = phases;
+        c->relaxations = relaxations;
+        if (overflow) c->error = kDevOverflow;
+        c->done = 1;
+      }
+      break;
+    }
+  }
+  (void)timed_out;
+}
+
 // pred[v] = smallest u with an edge (u, v) and dist[u] + w = dist[v]
 __global__ void k_sssp_pred_init(int32_t *pred, int32_t n) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -399,6 +568,7 @@ static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws) {
   a.C = g->col.as<int32_t>();
   a.W = g->w.as<uint32_t>();
   a.n = g->n;
+  a.m = g->m;
   for (int i = 0; i < 2; ++i) {
     a.nearq[i] = ws->nearq[i].as<int32_t>();
     a.nearS[i] = ws->nearS[i].as<int32_t>();
@@ -466,7 +636,17 @@ gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, 
   SsspArgs a = sssp_args(g, ws);
   k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, dist, pred, delta, max_iters);
   GR_CUDA(cudaGetLastError());
-  if (o.mode == GR_MODE_LAUNCH || o.mode == GR_MODE_PERSISTENT) {
+  const int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
+  if (mode == GR_MODE_PERSISTENT) {
+    int per_sm = 0;
+    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp_do, kSsspThreads, 0));
+    int bps = std::min(per_sm, kSsspBlocksPerSm);
+    const int32_t want = o.block > 0 ? o.block : g->tuned_sssp_blocks_per_sm;
+    if (want > 0) bps = std::min(bps, want);
+    void *args[] = {&a};
+    GR_CUDA(cudaLaunchCooperativeKernel((void *)k_sssp_do, std::max(1, bps) * g->num_sms,
+                                        kSsspThreads, args, 0, s));
+  } else if (mode == GR_MODE_LAUNCH) {
     SsspCtl h;
     int32_t enq = 0, batch = 8;
     for (;;) {

@@ -126,16 +126,28 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
   }
   if (what & GR_TUNE_SSSP) {
     if (!g->sssp) GR_TRY(sssp_ws_create(g, s, &g->sssp));
-    std::vector<uint32_t> deltas;
+    struct SCand {
+      int32_t mode, bps;
+      uint32_t delta;
+    };
+    std::vector<SCand> cands;
     const double mw = std::max(1.0, g->mean_weight);
-    for (double f : {0.5, 1.0, 2.0, 4.0, 8.0, 32.0})
+    std::vector<uint32_t> deltas;
+    for (double f : {1.0, 4.0, 32.0})
       deltas.push_back((uint32_t)std::max(1.0, std::min(4.0e9, f * mw)));
     deltas.push_back(UINT32_MAX);
-    float best = FLT_MAX;
-    uint32_t pick = g->sssp_delta;
     for (uint32_t d : deltas) {
+      cands.push_back({GR_MODE_GRAPH, 0, d});
+      cands.push_back({GR_MODE_PERSISTENT, 1, d});
+      cands.push_back({GR_MODE_PERSISTENT, 0, d});
+    }
+    float best = FLT_MAX;
+    SCand pick = cands[0];
+    for (const SCand &c : cands) {
       gr_opts o = default_opts();
-      o.delta = d;
+      o.delta = c.delta;
+      o.mode = c.mode;
+      o.block = c.bps;
       GR_TRY(sssp_run(g, g->sssp, srcs[0], out.as<uint32_t>(), nullptr, o, s));
       GR_CUDA(cudaEventRecord(t.a, s));
       for (int32_t i = 0; i < k; ++i)
@@ -146,11 +158,13 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
       GR_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
       if (ms < best) {
         best = ms;
-        pick = d;
+        pick = c;
       }
     }
-    // UINT32_MAX selects "one bucket"; store it as the widest delta
-    g->sssp_delta = pick;
+    // UINT32_MAX selects "one bucket"; it is stored as is
+    g->sssp_delta = pick.delta;
+    g->tuned_sssp_mode = pick.mode;
+    g->tuned_sssp_blocks_per_sm = pick.bps;
     g->tuned_sssp_ms = best / k;
   }
   GR_CUDA(cudaStreamSynchronize(s));
@@ -168,6 +182,7 @@ gr_status gr_tuned_opts(const gr_graph *g, gr_opts *out, double *bfs_ms, double 
   out->beta = g->tuned_beta;
   out->block = g->tuned_blocks_per_sm;
   out->delta = g->sssp_delta;
+  out->max_iters = 0;
   if (bfs_ms) *bfs_ms = g->tuned_bfs_ms;
   if (sssp_ms) *sssp_ms = g->tuned_sssp_ms;
   return GR_OK;

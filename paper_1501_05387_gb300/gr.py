@@ -15,7 +15,9 @@ import weakref
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgr.so")
+# GR_LIBRARY selects another build of the same ABI (the GR_CHECKED
+# diagnostic build, libgr_checked.so); default: libgr.so next to this file
+LIB_PATH = os.environ.get("GR_LIBRARY") or os.path.join(_HERE, "libgr.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -73,6 +75,7 @@ _sig("gr_autotune", [_vp, _vp, _i32, _i32, _vp])
 _sig("gr_tuned_opts", [_vp, _P(gr_opts), _P(ctypes.c_double), _P(ctypes.c_double)])
 _sig("gr_diag_wait_timeout", [_i64, _vp])
 _sig("gr_diag_fail_alloc", [_i64])
+_sig("gr_diag_guard", [_P(_i32), _P(_i64), _P(_i64)])
 _sig("gr_server_create", [ctypes.c_size_t, _i32, _i32, _P(_vp)])
 _sig("gr_server_add_graph", [_vp, _vp, _i32, _P(_i32)])
 _sig("gr_server_submit", [_vp, _i32, _i32, _i32, _vp, _P(ctypes.c_uint64)])
@@ -390,6 +393,13 @@ def gr_server_destroy(s: Server):
 
 def gr_diag_wait_timeout(spin_limit: int, stream=None):
     _check(_lib.gr_diag_wait_timeout(int(spin_limit), _stream(stream)), "gr_diag_wait_timeout")
+
+
+def gr_diag_guard():
+    site, idx, bound = _i32(), _i64(), _i64()
+    _check(_lib.gr_diag_guard(ctypes.byref(site), ctypes.byref(idx), ctypes.byref(bound)),
+           "gr_diag_guard")
+    return site.value, idx.value, bound.value
 
 
 def gr_diag_fail_alloc(after: int):

@@ -33,7 +33,8 @@ def check(gr, r, c, w, g, src, o=None):
 
 
 def opts(gr, delta=0, mode="auto"):
-    m = {"auto": gr.GR_MODE_AUTO, "launch": gr.GR_MODE_LAUNCH, "graph": gr.GR_MODE_GRAPH}[mode]
+    m = {"auto": gr.GR_MODE_AUTO, "launch": gr.GR_MODE_LAUNCH, "graph": gr.GR_MODE_GRAPH,
+         "persistent": gr.GR_MODE_PERSISTENT}[mode]
     return gr.gr_opts(delta=delta, mode=m)
 
 
@@ -47,7 +48,7 @@ def s14w(cuda_lib):
 
 
 @pytest.mark.parametrize("delta", [0, 1, 8, 64, 0xFFFFFFFF])
-@pytest.mark.parametrize("mode", ["graph", "launch"])
+@pytest.mark.parametrize("mode", ["graph", "launch", "persistent"])
 def test_rmat_s14_delta_invariance(cuda_lib, s14w, delta, mode):
     r, c, w, g = s14w
     for src in [gg.max_degree_vertex(r)] + list(gg.sources(r, 3, seed=7)):
@@ -71,7 +72,8 @@ def test_grid_weighted(cuda_lib, side, p_del):
     with cuda_lib.gr_graph_create(r, c, w) as g:
         for src in [0, side * side // 2]:
             for delta in [0, 1, 16, 0xFFFFFFFF]:
-                check(cuda_lib, r, c, w, g, src, opts(cuda_lib, delta))
+                for mode in ["graph", "persistent"]:
+                    check(cuda_lib, r, c, w, g, src, opts(cuda_lib, delta, mode))
 
 
 @pytest.mark.parametrize("n", [1, 2, 33, 257])
@@ -81,6 +83,7 @@ def test_ragged_paths(cuda_lib, n):
     with cuda_lib.gr_graph_create(r, c, w) as g:
         for src in sorted({0, n // 2, n - 1}):
             check(cuda_lib, r, c, w, g, src, opts(cuda_lib, 4))
+            check(cuda_lib, r, c, w, g, src, opts(cuda_lib, 4, "persistent"))
 
 
 def test_zero_and_large_weights(cuda_lib):
