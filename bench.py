@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--cpu-sample-sources", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="also run the query-server benchmark (plain vs continuous batching)")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-full", action="store_true",
                     help="serve 20000 requests over the 24-graph pool (slow)")
@@ -427,7 +428,7 @@ def run_gr(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(r, c, srcs, m, args.cpu_sample_sources)
     serving = None
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and args.serving:
         g.close()
         g = None
         serving = serving_bench(gr, full=args.serving_full,

@@ -229,7 +229,8 @@ __device__ __forceinline__ void warp_append(int code, int32_t v, int32_t *buf0,
 // Load-balanced advance over frontier Q[0..q) with scanned degrees S[0..q].
 // For every edge e = (u, v) of a frontier vertex, f(u, v, e) runs once and
 // returns 0 (drop), 1 (append v to out0) or 2 (append v to out1, only when
-// NOUT == 2). Column loads are coalesced: consecutive threads take
+// NOUT == 2); with NOUT == 0 nothing is appended and the output arguments
+// are not used. Column loads are coalesced: consecutive threads take
 // consecutive edge ranks. Outputs are compacted per chunk in shared memory
 // and appended to the global queues with one atomic per chunk and queue.
 // Q == nullptr means the all-vertex frontier (Q[i] = i, S = R, q = n).
@@ -243,7 +244,7 @@ __device__ void lb_advance(const int32_t *R, const int32_t *C, const int32_t *Q,
   __shared__ int32_t s_off[CHUNK + 1];
   __shared__ int32_t s_u[CHUNK + 1];
   __shared__ int32_t s_row[CHUNK + 1];
-  __shared__ int32_t s_out0[CHUNK];
+  __shared__ int32_t s_out0[NOUT > 0 ? CHUNK : 1];
   __shared__ int32_t s_out1[NOUT == 2 ? CHUNK : 1];
   __shared__ int32_t s_red8[THREADS / 32];
   __shared__ int32_t s_cnt[2], s_base[2];
@@ -279,20 +280,23 @@ __device__ void lb_advance(const int32_t *R, const int32_t *C, const int32_t *Q,
         const int32_t e = s_row[lo] + (er - s_off[lo]);
         v = C[e];
         code = f(s_u[lo], v, e);
-        if (NOUT == 1 && code == 2) code = 0;
+        if (NOUT < 2 && code == 2) code = 0;
+        if (NOUT == 0) code = 0;
       }
-      warp_append(code, v, s_out0, &s_cnt[0], s_out1, &s_cnt[1]);
+      if constexpr (NOUT > 0) warp_append(code, v, s_out0, &s_cnt[0], s_out1, &s_cnt[1]);
     }
     __syncthreads();
-    if (threadIdx.x < NOUT) {
-      const int32_t cnt = s_cnt[threadIdx.x];
-      s_base[threadIdx.x] = cnt ? atomicAdd(threadIdx.x ? len1 : len0, cnt) : 0;
+    if constexpr (NOUT > 0) {
+      if (threadIdx.x < NOUT) {
+        const int32_t cnt = s_cnt[threadIdx.x];
+        s_base[threadIdx.x] = cnt ? atomicAdd(threadIdx.x ? len1 : len0, cnt) : 0;
+      }
+      __syncthreads();
+      for (int32_t k = threadIdx.x; k < s_cnt[0]; k += THREADS) out0[s_base[0] + k] = s_out0[k];
+      if (NOUT == 2)
+        for (int32_t k = threadIdx.x; k < s_cnt[1]; k += THREADS) out1[s_base[1] + k] = s_out1[k];
+      __syncthreads();
     }
-    __syncthreads();
-    for (int32_t k = threadIdx.x; k < s_cnt[0]; k += THREADS) out0[s_base[0] + k] = s_out0[k];
-    if (NOUT == 2)
-      for (int32_t k = threadIdx.x; k < s_cnt[1]; k += THREADS) out1[s_base[1] + k] = s_out1[k];
-    __syncthreads();
   }
 }
 

@@ -57,11 +57,11 @@ struct BfsCtl {
   int32_t pull_levels;
   int32_t policy;       // GR_DIR_*
   int32_t max_levels;
-  int32_t blocks_done;  // level-kernel blocks finished (the last one ends the level)
-  int32_t barrier_gen_unused;
-  int32_t barrier_cnt_unused;
   int32_t from_bitmap;  // 1: the current frontier exists only as a bitmap
-  int32_t pad_;
+  int32_t pad_[3];
+  // level-kernel blocks finished so far in this traversal; the block whose
+  // arrival makes it a multiple of the grid size ends the level
+  unsigned long long arrivals;
   // persistent kernel: next-frontier counters, a ring of three so that one
   // can be cleared while the others are in use
   unsigned long long cnt3[3];
@@ -188,7 +188,7 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     c->pull_levels = 0;
     c->policy = policy;
     c->max_levels = max_levels;
-    c->blocks_done = 0;
+    c->arrivals = 0ull;
     grid_barrier_reset(&c->bar);
     c->next_packed = 0ull;
     c->mf = dsrc;
@@ -610,7 +610,7 @@ __device__ __forceinline__ int32_t next_direction(int32_t policy, bool was_pull,
 // Run by the last block of a level: install the next frontier and decide
 // the next level's direction (Sec. 4.5; Beamer et al.'s rule).
 __device__ void level_end(const BfsArgs &a, BfsCtl *c) {
-  const unsigned long long packed = c->next_packed;
+  const unsigned long long packed = *(volatile unsigned long long *)&c->next_packed;
   const int32_t qn = (int32_t)(packed & 0xFFFFFFFFull);
   const long long mf = (long long)(packed >> 32);
   const bool was_pull = c->dir == kPull;
@@ -646,7 +646,13 @@ __device__ void level_end(const BfsArgs &a, BfsCtl *c) {
 __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
     k_bfs_level(BfsArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
   BfsCtl *c = a.ctl;
-  if (c->done) return;  // host-driven batches past the end: every block leaves
+  if (*(volatile int32_t *)&c->done) {
+    // a level kernel after the traversal ended (host-driven batches enqueue
+    // a few extra): every block leaves; inside a graph the loop condition is
+    // cleared here too, so the while loop cannot outlive the traversal
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   __shared__ LevelSmem sm;
   if (threadIdx.x == 0) sm.cnt = 0;
   const int32_t p = c->parity, L = c->level, q = c->q_len, dir = c->dir;
@@ -665,12 +671,12 @@ __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    sm.last = atomicAdd(&c->blocks_done, 1) == (int32_t)gridDim.x - 1;
+    const unsigned long long old = atomicAdd(&c->arrivals, 1ull);
+    sm.last = (old + 1ull) % gridDim.x == 0ull;
   }
   __syncthreads();
   if (sm.last && threadIdx.x == 0) {
     __threadfence();
-    c->blocks_done = 0;
     level_end(a, c);
     if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
   }
@@ -1024,9 +1030,10 @@ gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, in
   return GR_OK;
 }
 
-gr_status bfs_read_ctl_error(BfsWorkspace *ws) {
+gr_status bfs_read_ctl_error(BfsWorkspace *ws, cudaStream_t s) {
   BfsCtl h;
-  GR_CUDA(cudaMemcpy(&h, ws->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost));
+  // pageable destination: the copy has finished when the call returns
+  GR_CUDA(cudaMemcpyAsync(&h, ws->ctl.p, sizeof(BfsCtl), cudaMemcpyDeviceToHost, s));
   if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
   if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "level limit reached");
   return GR_OK;

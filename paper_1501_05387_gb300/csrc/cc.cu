@@ -80,9 +80,10 @@ __global__ void __launch_bounds__(kCcThreads) k_cc_hook(const int32_t *R, const 
                                                          int32_t n, int32_t *label,
                                                          int32_t only_lower) {
   HookF f{label, only_lower, n};
-  int32_t dummy = 0;
-  lb_advance<kCcThreads, kCcItems, 1>(R, C, nullptr, n, R, f, nullptr, &dummy, nullptr,
-                                      &dummy);
+  // every edge is settled in its visit: the edge frontier it would filter
+  // into stays empty, so the advance appends nothing
+  lb_advance<kCcThreads, kCcItems, 0>(R, C, nullptr, n, R, f, nullptr, nullptr, nullptr,
+                                      nullptr);
 }
 
 __global__ void k_cc_jump(int32_t *label, int32_t n, int32_t *num_roots) {

@@ -145,10 +145,12 @@ size_t bfs_ws_bytes(const gr_graph *g);
 gr_status bfs_check(const gr_graph *g, int32_t src, const gr_opts &o);
 gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, int32_t *parent,
                   const gr_opts &o, cudaStream_t s);
-gr_status bfs_read_ctl_error(BfsWorkspace *ws);
+gr_status bfs_read_ctl_error(BfsWorkspace *ws, cudaStream_t s);
 gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out);
 size_t sssp_ws_bytes(const gr_graph *g);
 gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o);
+// GR_ETIMEOUT when the last SSSP on ws stopped at a device-side limit
+gr_status sssp_read_ctl_error(SsspWorkspace *ws, cudaStream_t s);
 gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, int32_t *pred,
                    const gr_opts &o, cudaStream_t s);
 gr_status cc_ws_create(gr_graph *g, CcWorkspace **out);

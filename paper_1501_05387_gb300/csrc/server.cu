@@ -85,6 +85,7 @@ struct Server {
   int device = 0;
   std::vector<GraphEntry> graphs;
   std::mutex mu;
+  std::mutex setup_mu;  // one slot at a time builds workspaces and level-loop graphs
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> queue;                      // tickets waiting
   std::unordered_map<uint64_t, Request> reqs;      // all known requests
@@ -136,6 +137,24 @@ std::vector<uint64_t> take_batch(Server &S, int slot_ws_missing_bytes_unused) {
   return out;
 }
 
+// Longest a batch's device work may take before its slot gives up on it.
+constexpr double kBatchLimitMs = 120000.0;
+
+// Wait for the slot's stream with a time limit (a stream that never drains
+// must not stall the slot's thread, and with it server shutdown, forever).
+gr_status wait_stream(cudaStream_t s, double limit_ms) {
+  const double t0 = now_ms();
+  for (int polls = 0;; ++polls) {
+    const cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return GR_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "server stream");
+    if (now_ms() - t0 > limit_ms)
+      return fail(GR_ETIMEOUT, "device work of the batch did not finish within the slot's limit");
+    if (polls < 2000) std::this_thread::yield();
+    else std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+}
+
 gr_status copy_out(const Request &r, const void *dev, size_t bytes, cudaStream_t s) {
   if (!r.out) return GR_OK;
   GR_CUDA(cudaMemcpyAsync(r.out, dev, bytes,
@@ -155,8 +174,13 @@ void Server::worker(int slot) {
   const cudaError_t se = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   const std::string stream_err =
       se == cudaSuccess ? std::string() : std::string("server slot stream: ") + cudaGetErrorString(se);
-  std::map<int32_t, SlotGraphState> state;  // per graph
-  DevMem buf;                               // result staging for this slot
+  // per-graph workspaces and the result staging of this slot; held by
+  // pointer so that a slot whose stream stopped draining can leave them
+  // (freeing memory that queued work may still use would wait on it)
+  auto *state = new std::map<int32_t, SlotGraphState>();
+  auto *buf_p = new DevMem();
+  DevMem &buf = *buf_p;
+  std::string broken;  // set when the slot's stream stopped draining
   for (;;) {
     std::vector<uint64_t> batch;
     {
@@ -179,18 +203,27 @@ void Server::worker(int slot) {
     first = rs[0];
     GraphEntry &ge = graphs[first.graph];
     gr_graph *g = ge.g;
-    SlotGraphState &st = state[first.graph];
+    SlotGraphState &st = (*state)[first.graph];
     const size_t nbytes = sizeof(int32_t) * (size_t)g->n;
     const size_t need = nbytes * rs.size();
     gr_status status = GR_OK;
     std::string err;
     if (!stream_err.empty()) status = fail(GR_ECUDA, stream_err);
+    if (status == GR_OK && !broken.empty()) status = fail(GR_ECUDA, broken);
     if (status == GR_OK && buf.bytes < need) status = buf.alloc(need, "server result buffer");
     // graph-mode level loops: several slots may run traversals at once, so
     // no launch may need the whole GPU to itself (cooperative launches do)
     gr_opts o = default_opts();
     o.mode = GR_MODE_GRAPH;
     size_t ws_new = 0;
+    // the first request of a kind on a graph creates this slot's workspace
+    // and captures its level-loop graph; slots do that one at a time
+    std::unique_lock<std::mutex> setup(setup_mu, std::defer_lock);
+    const bool fresh = (first.kind == GR_QUERY_BFS && rs.size() > 1) ? !st.batch
+                       : first.kind == GR_QUERY_BFS                 ? !st.bfs
+                       : first.kind == GR_QUERY_SSSP                ? !st.sssp
+                                                                    : !st.cc;
+    if (fresh) setup.lock();
     if (status == GR_OK) {
       if (first.kind == GR_QUERY_BFS && rs.size() > 1) {
         if (!st.batch) {
@@ -225,10 +258,17 @@ void Server::worker(int slot) {
       }
       for (size_t i = 0; status == GR_OK && i < rs.size(); ++i)
         status = copy_out(rs[i], buf.as<char>() + i * nbytes, nbytes, s);
+      if (setup.owns_lock()) setup.unlock();
       if (status == GR_OK) {
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) status = cuda_fail(e, "server stream");
+        status = wait_stream(s, kBatchLimitMs);
+        if (status == GR_ETIMEOUT) broken = std::string("server slot unusable: ") + gr_last_error();
       }
+      // a traversal that stopped at a device-side limit (level or iteration
+      // cap, a timed-out wait) fails its request
+      if (status == GR_OK && first.kind == GR_QUERY_BFS && rs.size() == 1)
+        status = bfs_read_ctl_error(st.bfs, s);
+      if (status == GR_OK && first.kind == GR_QUERY_SSSP)
+        status = sssp_read_ctl_error(st.sssp, s);
     }
     if (status != GR_OK)
       err = std::string(gr_last_error()) + " [batch: kind " + std::to_string(first.kind) +
@@ -260,8 +300,11 @@ void Server::worker(int slot) {
     cv_done.notify_all();
     cv_work.notify_all();
   }
-  state.clear();
-  if (s) cudaStreamDestroy(s);
+  if (broken.empty()) {
+    delete state;
+    delete buf_p;
+    if (s) cudaStreamDestroy(s);
+  }
 }
 
 }  // namespace gr

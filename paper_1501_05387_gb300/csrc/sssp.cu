@@ -53,10 +53,13 @@ struct SsspCtl {
   int32_t far_epoch;      // far-pile stamp
   int32_t max_iters;
   int32_t phases;         // number of splits
-  int32_t blocks_done;    // blocks finished (the last one ends the iteration)
+  int32_t pad_;
   uint32_t far_min;       // lower bound of far-pile distances (atomicMin)
   uint32_t far_min_next;  // min distance of entries kept by a split
   unsigned long long near_next_packed;  // [31:0] next near size, [63:32] its edges
+  // iteration-kernel blocks finished so far in this run; the block whose
+  // arrival makes it a multiple of the grid size ends the iteration
+  unsigned long long arrivals;
   unsigned long long T;   // near criterion: dist < T
   unsigned long long T_old;
   unsigned long long delta;
@@ -135,7 +138,7 @@ __global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pr
     c->far_epoch = 0;
     c->max_iters = max_iters;
     c->phases = 0;
-    c->blocks_done = 0;
+    c->arrivals = 0ull;
     c->far_min = 0xFFFFFFFFu;
     c->far_min_next = 0xFFFFFFFFu;
     c->near_next_packed = 0ull;
@@ -342,16 +345,19 @@ __device__ void sssp_end(const SsspArgs &a, SsspCtl *c) {
     c->done = 1;
     return;
   }
-  const unsigned long long packed = c->near_next_packed;
+  // counters the other blocks filled with atomics: read past L1
+  const unsigned long long packed = *(volatile unsigned long long *)&c->near_next_packed;
   const int32_t qn = (int32_t)(packed & 0xFFFFFFFFull);
   const long long en = (long long)(packed >> 32);
   if (c->mode == kSsspRelax) {
     c->relaxations += c->near_edges;
+    c->far_len = *(volatile int32_t *)&c->far_len;
+    c->far_min = *(volatile uint32_t *)&c->far_min;
   } else {
-    c->far_len = c->far_next_len;
+    c->far_len = *(volatile int32_t *)&c->far_next_len;
     c->far_parity ^= 1;
     c->far_epoch += 1;
-    c->far_min = c->far_min_next;
+    c->far_min = *(volatile uint32_t *)&c->far_min_next;
     c->phases += 1;
   }
   c->near_len = qn;
@@ -383,7 +389,13 @@ __device__ void sssp_end(const SsspArgs &a, SsspCtl *c) {
 __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
     k_sssp_iter(SsspArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
   SsspCtl *c = a.ctl;
-  if (c->done) return;  // host-driven batches past the end: every block leaves
+  if (*(volatile int32_t *)&c->done) {
+    // an iteration kernel after the run ended (host-driven batches enqueue a
+    // few extra): every block leaves; inside a graph the loop condition is
+    // cleared here too, so the while loop cannot outlive the run
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   __shared__ SsspSmem sm;
   if (threadIdx.x == 0) {
     sm.nearb.cnt = 0;
@@ -395,12 +407,12 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    sm.last = atomicAdd(&c->blocks_done, 1) == (int32_t)gridDim.x - 1;
+    const unsigned long long old = atomicAdd(&c->arrivals, 1ull);
+    sm.last = (old + 1ull) % gridDim.x == 0ull;
   }
   __syncthreads();
   if (sm.last && threadIdx.x == 0) {
     __threadfence();
-    c->blocks_done = 0;
     sssp_end(a, c);
     if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
   }
@@ -613,6 +625,15 @@ static gr_status build_sssp_graph(gr_graph *g, SsspWorkspace *ws) {
   GR_CUDA(e);
   GR_CUDA(cudaGraphInstantiate(&ws->exec, graph, 0));
   ws->graph = graph;
+  return GR_OK;
+}
+
+gr_status sssp_read_ctl_error(SsspWorkspace *ws, cudaStream_t s) {
+  SsspCtl h;
+  // pageable destination: the copy has finished when the call returns
+  GR_CUDA(cudaMemcpyAsync(&h, ws->ctl.p, sizeof(SsspCtl), cudaMemcpyDeviceToHost, s));
+  if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
+  if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "iteration limit reached");
   return GR_OK;
 }
 

@@ -108,7 +108,7 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
         GR_TRY(bfs_run(g, g->bfs, srcs[i], out.as<int32_t>(), nullptr, o, s));
       GR_CUDA(cudaEventRecord(t.b, s));
       GR_CUDA(cudaEventSynchronize(t.b));
-      GR_TRY(bfs_read_ctl_error(g->bfs));
+      GR_TRY(bfs_read_ctl_error(g->bfs, s));
       float ms = 0.f;
       GR_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
       if (ms < best) {
@@ -154,6 +154,7 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
         GR_TRY(sssp_run(g, g->sssp, srcs[i], out.as<uint32_t>(), nullptr, o, s));
       GR_CUDA(cudaEventRecord(t.b, s));
       GR_CUDA(cudaEventSynchronize(t.b));
+      GR_TRY(sssp_read_ctl_error(g->sssp, s));
       float ms = 0.f;
       GR_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
       if (ms < best) {
