@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-full", action="store_true",
                     help="serve 20000 requests over the 24-graph pool (slow)")
+    ap.add_argument("--suite", action="store_true",
+                    help="instead of the BFS line, measure every primitive on its workload "
+                         "(SSSP s22, grid 4096^2 BFS/SSSP/CC, s23 PageRank/CC/BC/batched BFS)")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale (profiling runs only; the metric is quoted at 22)")
     ap.add_argument("--mode", default="auto", choices=["auto", "graph", "launch", "persistent"],
@@ -267,6 +270,174 @@ def serving_bench(gr, full=False, count=2000):
             "speedup_qps": served["qps"] / max(plain["qps"], 1e-9)}
 
 
+# ------------------------------------------------------------------- suite
+def _timed_calls(fn, calls, flush, warm=1):
+    """Mean CUDA-event milliseconds of fn() over `calls` calls on the current
+    stream, the L2 flushed (outside the events) before each call."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(calls):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.mean(ms)), ms
+
+
+def _roof(bytes_per_call, ms, peak, model):
+    gbs = bytes_per_call / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "bytes_per_call": float(bytes_per_call), "bytes_model": model}
+
+
+def run_suite(args):
+    """Every primitive on the workload it is specified on, timed with CUDA
+    events (L2 flushed before each call), with its edge-byte roofline."""
+    import torch
+    import graphgen as gg
+    from paper_1501_05387_gb300 import build
+    build.build()
+    from paper_1501_05387_gb300 import gr
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        peak = 6800.0
+    out = []
+    INF = 0xFFFFFFFF
+
+    def reach_bytes(r, reached, per_edge, per_vertex):
+        deg = np.diff(r).astype(np.int64)
+        n = r.size - 1
+        return per_edge * int(deg[reached].sum()) + 4 * (n + 1) + per_vertex * int(reached.sum())
+
+    # --- SSSP on R-MAT s22 (weights [1,64], seed 3), the BFS sources
+    r, c = gg.rmat(22, 16, seed=2)
+    w = gg.weights(r, c, seed=3, wmin=1, wmax=64)
+    srcs = gg.sources(r, 16, seed=2)
+    n, m = r.size - 1, c.size
+    g = gr.gr_graph_create(r, c, w)
+    gr.gr_autotune(g, [int(np.argmax(np.diff(r)))], gr.GR_TUNE_SSSP)
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    per, byts = [], []
+    for s in srcs:
+        ms, _ = _timed_calls(lambda: gr.gr_sssp(g, int(s), dist), 2, flush)
+        d = dist.cpu().numpy().view(np.uint32)
+        per.append(ms)
+        byts.append(reach_bytes(r, d != INF, 8, 4))
+    mean = float(np.mean(per))
+    out.append({"workload": "rmat22_sssp", "primitive": "sssp", "calls": 2 * len(srcs),
+                "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
+                "tuned": gr.gr_tuned_opts(g),
+                "roofline": _roof(float(np.mean(byts)), mean, peak,
+                                  "8 B per column+weight entry of the reached vertices, "
+                                  "4 B per row offset, 4 B per reached distance")})
+    g.close()
+    del r, c, w
+
+    # --- 4096^2 grid, 5 % deletions (seed 4), weights [1,16]: BFS, SSSP, CC
+    r, c = gg.grid(4096, p_del=0.05, seed=4)
+    w = gg.weights(r, c, seed=4, wmin=1, wmax=16)
+    n, m = r.size - 1, c.size
+    g = gr.gr_graph_create(r, c, w)
+    srcs = gg.sources(r, 4, seed=4)
+    depth = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    per, byts, levels = [], [], []
+    for s in srcs:
+        ms, _ = _timed_calls(lambda: gr.gr_bfs(g, int(s), depth, parent), 1, flush)
+        levels.append(gr.gr_bfs_stats(g)[0])
+        per.append(ms)
+        byts.append(reach_bytes(r, depth.cpu().numpy() >= 0, 4, 8))
+    mean = float(np.mean(per))
+    out.append({"workload": "grid4096_bfs", "primitive": "bfs", "calls": len(srcs),
+                "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
+                "levels": levels, "us_per_level": 1e3 * mean / float(np.mean(levels)),
+                "tuned": gr.gr_tuned_opts(g),
+                "roofline": _roof(float(np.mean(byts)), mean, peak,
+                                  "4 B per column entry of the reached vertices, 4 B per "
+                                  "row offset, 8 B depth+parent per reached vertex")})
+    per, byts, iters = [], [], []
+    dist_g = torch.empty(n, dtype=torch.int32, device=dev)
+    for s in srcs[:2]:
+        ms, _ = _timed_calls(lambda: gr.gr_sssp(g, int(s), dist_g), 1, flush)
+        iters.append(gr.gr_sssp_stats(g)[0])
+        per.append(ms)
+        byts.append(reach_bytes(r, dist_g.cpu().numpy().view(np.uint32) != INF, 8, 4))
+    mean = float(np.mean(per))
+    out.append({"workload": "grid4096_sssp", "primitive": "sssp", "calls": 2,
+                "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
+                "iterations": iters,
+                "roofline": _roof(float(np.mean(byts)), mean, peak,
+                                  "8 B per column+weight entry of the reached vertices, "
+                                  "4 B per row offset, 4 B per reached distance")})
+    label = torch.empty(n, dtype=torch.int32, device=dev)
+    ms, _ = _timed_calls(lambda: gr.gr_cc(g, label, count=False), 3, flush)
+    out.append({"workload": "grid4096_cc", "primitive": "cc", "calls": 3, "ms_per_call": ms,
+                "throughput": m / (ms * 1e-3) / 1e9, "unit": "G edges/s",
+                "components": gr.gr_cc(g, label),
+                "roofline": _roof(4 * m + 4 * (n + 1) + 8 * n, ms, peak,
+                                  "4 B per column entry, 4 B per row offset, label write "
+                                  "at init and after pointer jumping")})
+    g.close()
+    del r, c, w
+
+    # --- R-MAT s23 (seed 5): PageRank, CC, batched BFS and BC over 64 sources
+    r, c = gg.rmat(23, 16, seed=5)
+    n, m = r.size - 1, c.size
+    g = gr.gr_graph_create(r, c)
+    rank = torch.empty(n, dtype=torch.float32, device=dev)
+    it = gr.gr_pagerank(g, rank)
+    ms, _ = _timed_calls(lambda: gr.gr_pagerank(g, rank, count=False), 2, flush)
+    per_iter = 4 * m + 4 * (n + 1) + 12 * n
+    out.append({"workload": "rmat23_pagerank", "primitive": "pagerank", "calls": 2,
+                "ms_per_call": ms, "iterations": it,
+                "throughput": it / (ms * 1e-3), "unit": "iterations/s",
+                "roofline": _roof(per_iter * it, ms, peak,
+                                  "per iteration: 4 B per column entry, 4 B per row offset, "
+                                  "contribution write, rank read+write (12 B per vertex)")})
+    label = torch.empty(n, dtype=torch.int32, device=dev)
+    ms, _ = _timed_calls(lambda: gr.gr_cc(g, label, count=False), 3, flush)
+    out.append({"workload": "rmat23_cc", "primitive": "cc", "calls": 3, "ms_per_call": ms,
+                "throughput": m / (ms * 1e-3) / 1e9, "unit": "G edges/s",
+                "roofline": _roof(4 * m + 4 * (n + 1) + 8 * n, ms, peak,
+                                  "4 B per column entry, 4 B per row offset, label write "
+                                  "at init and after pointer jumping")})
+    srcs64 = gg.sources(r, 64, seed=5)
+    depth64 = torch.empty(64 * n, dtype=torch.int32, device=dev)
+    ms, _ = _timed_calls(lambda: gr.gr_bfs_batch(g, srcs64, depth64), 2, flush)
+    lv = int(depth64.view(64, n).max().item()) + 1
+    out.append({"workload": "rmat23_bfs64", "primitive": "batched bfs (64 lanes)", "calls": 2,
+                "ms_per_call": ms, "levels": lv,
+                "throughput": 64 * m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+                "roofline": _roof(lv * (4 * m + 4 * (n + 1) + 24 * n) + 4 * 64 * n, ms, peak,
+                                  "per level a sweep of every column entry and row offset "
+                                  "with three 8 B lane masks per vertex; 4 B per lane "
+                                  "depth written")})
+    bc = torch.empty(n, dtype=torch.float64, device=dev)
+    ms, _ = _timed_calls(lambda: gr.gr_bc(g, srcs64, bc), 1, flush)
+    out.append({"workload": "rmat23_bc64", "primitive": "bc (64 sources, FP64)", "calls": 1,
+                "ms_per_call": ms, "levels": lv,
+                "throughput": 64 * 2 * m / (ms * 1e-3) / 1e9, "unit": "GTEPS (2|E| per source)",
+                "roofline": _roof(2 * lv * (4 * m + 4 * (n + 1) + 16 * n) + 4 * 512 * n,
+                                  ms, peak,
+                                  "forward and backward: per level a sweep of every column "
+                                  "entry and row offset with two 8 B lane masks per vertex; "
+                                  "sigma and dependency rows (512 B per vertex) written and "
+                                  "read once each")})
+    g.close()
+    print(json.dumps({"suite": out, "peak_hbm_gbs": peak}), flush=True)
+
+
 def cpu_baseline(r, c, srcs, m, k):
     import oracle
     t0 = time.perf_counter()
@@ -466,6 +637,9 @@ def run_gr(args):
 
 def main():
     args = parse()
+    if args.suite:
+        run_suite(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
