@@ -101,6 +101,7 @@ struct BfsArgs {
   uint32_t *fb[3];      // frontier bitmaps, rotating by level (cur, next, spare)
   BfsCtl *ctl;
   int32_t do_bitmap;
+  int32_t low_degree;   // push-only on a graph of small maximum degree: per-thread expansion
   // persistent kernel: per-block segments of the vertices a pull level
   // found (and their degrees), compacted into a queue by the next level
   // when it pushes; null in the other drivers
@@ -117,6 +118,10 @@ constexpr int kLvChunk = kLvThreads * kLvItems;    // merge items per chunk
 constexpr int kLvWarps = kLvThreads / 32;
 constexpr int kPullLane = 3;  // neighbours after the first a lane checks alone (pull)
 constexpr int kLvBlocksPerSm = 6;
+// Largest maximum degree for which push levels expand one frontier vertex per
+// thread (mesh-like graphs), and the neighbours a thread loads at once.
+constexpr int32_t kLowDegreeMax = 16;
+constexpr int kTpvItems = 4;
 
 struct BfsWorkspace {
   DevMem q[2], S[2], visited, fb[3], ctl, seg_v, seg_d, seg_cnt;
@@ -351,6 +356,90 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
 #pragma unroll
     for (int j = 0; j < kLvItems; ++j) emit(sm, won[j], v[j], dv[j]);
     flush(sm, counter, Qn, Sn, a.n + 1);
+  }
+}
+
+// Push level for graphs of small maximum degree (meshes): one thread per
+// frontier vertex walks its whole neighbour list (the per-thread expansion
+// of Sec. 4.4, which is balanced when every degree is small), so the level
+// needs neither a merge-path search nor the queue's degree scan. The
+// candidates' row offsets are loaded with their visited words, so a
+// winner's degree (for the next frontier's edge count) costs no extra round
+// trip; winners are appended with one packed atomic per warp.
+__device__ void push_level_thread(const BfsArgs &a, BfsCtl *c, int32_t p, int32_t L, int32_t q,
+                                  unsigned long long *counter) {
+  const int32_t *Q = queue_of(a, p);
+  int32_t *Qn = queue_of(a, p ^ 1);
+  int32_t *depth = c->depth;
+  int32_t *parent = c->parent;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t qr = ((int64_t)q + 31) & ~31ll;  // warp-uniform bound
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < qr; i += stride) {
+    int32_t u = 0, r0 = 0, r1 = 0;
+    if (i < q) {
+      u = Q[i];
+      if (GR_IN(u, a.n, 170)) {
+        r0 = a.R[u];
+        r1 = a.R[u + 1];
+      }
+    }
+    for (int32_t e0 = r0; __any_sync(0xffffffffu, e0 < r1); e0 += kTpvItems) {
+      int32_t v[kTpvItems], d0[kTpvItems], d1[kTpvItems];
+      uint32_t vw[kTpvItems];
+      bool won[kTpvItems];
+#pragma unroll
+      for (int j = 0; j < kTpvItems; ++j) {
+        v[j] = (e0 + j < r1 && GR_IN(e0 + j, a.m, 171)) ? a.C[e0 + j] : -1;
+        if (v[j] >= 0 && !GR_IN(v[j], a.n, 172)) v[j] = -1;
+      }
+#pragma unroll
+      for (int j = 0; j < kTpvItems; ++j) {
+        vw[j] = 0xFFFFFFFFu;
+        d0[j] = d1[j] = 0;
+        if (v[j] >= 0) {
+          vw[j] = a.visited[v[j] >> 5];
+          d0[j] = a.R[v[j]];
+          d1[j] = a.R[v[j] + 1];
+        }
+      }
+      uint32_t cnt = 0, deg = 0;
+#pragma unroll
+      for (int j = 0; j < kTpvItems; ++j) {
+        won[j] = false;
+        if (v[j] >= 0) {
+          const uint32_t mask = 1u << (v[j] & 31);
+          if (!(vw[j] & mask)) won[j] = !(atomicOr(a.visited + (v[j] >> 5), mask) & mask);
+        }
+        if (won[j]) {
+          depth[v[j]] = L + 1;
+          if (parent) parent[v[j]] = u;
+          cnt += 1;
+          deg += (uint32_t)(d1[j] - d0[j]);
+        }
+      }
+      // warp-level exclusive scan of (edges, vertices), one packed atomic
+      const unsigned long long mine = ((unsigned long long)deg << 32) | cnt;
+      unsigned long long incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        int32_t k = (int32_t)((base + (incl - mine)) & 0xFFFFFFFFull);
+#pragma unroll
+        for (int j = 0; j < kTpvItems; ++j)
+          if (won[j]) {
+            if (GR_IN(k, a.n + 1, 173)) Qn[k] = v[j];
+            ++k;
+          }
+      }
+    }
   }
 }
 
@@ -666,6 +755,7 @@ __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
   __syncthreads();
   if (dir == kPull) pull_level(a, c, sm, L, &c->next_packed);
   else if (c->from_bitmap) push_from_bitmap(a, c, p, L, &c->next_packed);
+  else if (a.low_degree) push_level_thread(a, c, p, L, q, &c->next_packed);
   else push_level(a, c, sm, p, L, q, (int32_t)c->mf, &c->next_packed);
   // the last block to finish ends the level
   __syncthreads();
@@ -727,7 +817,8 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
         segments_to_queue(a, sm, queue_of(a, parity), scan_of(a, parity), &qq, &qe);
         if (!grid_barrier(c, gridDim.x, gen)) break;
       }
-      push_level(a, c, sm, parity, L, qq, qe, counter);
+      if (a.low_degree) push_level_thread(a, c, parity, L, qq, counter);
+      else push_level(a, c, sm, parity, L, qq, qe, counter);
     }
     if (!grid_barrier(c, gridDim.x, gen)) break;
     const unsigned long long pk = *(volatile unsigned long long *)counter;
@@ -900,6 +991,7 @@ static BfsArgs make_args(gr_graph *g, BfsWorkspace *ws, int32_t do_bitmap) {
   for (int i = 0; i < 3; ++i) a.fb[i] = ws->fb[i].as<uint32_t>();
   a.ctl = ws->ctl.as<BfsCtl>();
   a.do_bitmap = do_bitmap;
+  a.low_degree = (!do_bitmap && g->max_degree <= kLowDegreeMax) ? 1 : 0;
   a.seg_v = nullptr;
   a.seg_d = nullptr;
   a.seg_cnt = nullptr;

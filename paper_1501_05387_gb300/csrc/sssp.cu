@@ -84,11 +84,16 @@ struct SsspArgs {
   int32_t *stamp;
   int32_t *far_stamp;
   SsspCtl *ctl;
+  int32_t low_degree;  // graph of small maximum degree: per-thread relaxation
 };
 
 constexpr int kSsspThreads = 256, kSsspItems = 4;
 constexpr int kSsspChunk = kSsspThreads * kSsspItems;
 constexpr int kSsspBlocksPerSm = 5;
+// Largest maximum degree for which relaxation takes one frontier vertex per
+// thread (mesh-like graphs), and the neighbours a thread loads at once.
+constexpr int32_t kSsspLowDegreeMax = 16;
+constexpr int kSsspTpvItems = 4;
 
 struct SsspWorkspace {
   DevMem nearq[2], nearS[2], farq[2], stamp, far_stamp, ctl;
@@ -255,6 +260,125 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
   }
 }
 
+// Relaxation for graphs of small maximum degree (meshes): one thread per
+// near-frontier vertex relaxes its whole neighbour list (the per-thread
+// expansion of Sec. 4.4, balanced when every degree is small), so no
+// merge-path search is needed. Each candidate's row offsets are loaded with
+// its distance, so a vertex entering the near frontier brings its degree (for
+// the frontier's edge count) without an extra round trip. Near and far
+// entries are appended with one atomic per warp each.
+__device__ void relax_body_thread(const SsspArgs &a, uint32_t *dist, const SsspStep &st) {
+  const int32_t *Q = pick(a.nearq, st.near_parity);
+  int32_t *Qn = pick(a.nearq, st.near_parity ^ 1);
+  const int32_t q = st.q;
+  const unsigned long long T = st.T;
+  const int32_t iter = st.iter, epoch = st.far_epoch;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t qr = ((int64_t)q + 31) & ~31ll;  // warp-uniform bound
+  uint32_t local_min = 0xFFFFFFFFu;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < qr; i += stride) {
+    int32_t u = 0, r0 = 0, r1 = 0;
+    uint32_t du = 0xFFFFFFFFu;
+    if (i < q && GR_IN(i, a.n + 1, 320)) {
+      u = Q[i];
+      if (GR_IN(u, a.n, 321)) {
+        r0 = a.R[u];
+        r1 = a.R[u + 1];
+        du = dist[u];
+      }
+    }
+    for (int32_t e0 = r0; __any_sync(0xffffffffu, e0 < r1); e0 += kSsspTpvItems) {
+      int32_t v[kSsspTpvItems], d0[kSsspTpvItems], d1[kSsspTpvItems];
+      uint32_t w[kSsspTpvItems], dv[kSsspTpvItems];
+      int code[kSsspTpvItems];
+#pragma unroll
+      for (int j = 0; j < kSsspTpvItems; ++j) {
+        const int32_t e = e0 + j;
+        v[j] = -1;
+        w[j] = 0u;
+        if (e < r1 && GR_IN(e, a.m, 322)) {
+          v[j] = a.C[e];
+          w[j] = a.W[e];
+          if (!GR_IN(v[j], a.n, 323)) v[j] = -1;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kSsspTpvItems; ++j) {
+        dv[j] = 0u;
+        d0[j] = d1[j] = 0;
+        if (v[j] >= 0) {
+          dv[j] = dist[v[j]];
+          d0[j] = a.R[v[j]];
+          d1[j] = a.R[v[j] + 1];
+        }
+      }
+      uint32_t ncnt = 0, ndeg = 0, fcnt = 0;
+#pragma unroll
+      for (int j = 0; j < kSsspTpvItems; ++j) {
+        code[j] = 0;
+        if (v[j] < 0) continue;
+        const unsigned long long nd = (unsigned long long)du + w[j];
+        if (nd >= 0xFFFFFFFFull) continue;  // not representable: no improvement
+        const uint32_t nd32 = (uint32_t)nd;
+        if (nd32 >= dv[j]) continue;  // plain-load cull
+        const uint32_t old = atomicMin(dist + v[j], nd32);
+        if (nd32 >= old) continue;
+        if (nd < T) {
+          if (atomicExch(a.stamp + v[j], iter) != iter) {
+            code[j] = 1;
+            ncnt += 1;
+            ndeg += (uint32_t)(d1[j] - d0[j]);
+          }
+        } else {
+          local_min = min(local_min, nd32);
+          if (atomicExch(a.far_stamp + v[j], epoch) != epoch) {
+            code[j] = 2;
+            fcnt += 1;
+          }
+        }
+      }
+      // near: warp scan of (edges, vertices), one packed atomic
+      const unsigned long long nmine = ((unsigned long long)ndeg << 32) | ncnt;
+      unsigned long long nincl = nmine;
+      uint32_t fincl = fcnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, nincl, o);
+        const uint32_t tf = __shfl_up_sync(0xffffffffu, fincl, o);
+        if (lane >= o) {
+          nincl += t;
+          fincl += tf;
+        }
+      }
+      const unsigned long long ntot = __shfl_sync(0xffffffffu, nincl, 31);
+      const uint32_t ftot = __shfl_sync(0xffffffffu, fincl, 31);
+      unsigned long long nbase = 0;
+      int32_t fbase = 0;
+      if (lane == 0) {
+        if (ntot) nbase = atomicAdd(st.near_ctr, ntot);
+        if (ftot) fbase = atomicAdd(st.far_ctr, (int32_t)ftot);
+      }
+      nbase = __shfl_sync(0xffffffffu, nbase, 0);
+      fbase = __shfl_sync(0xffffffffu, fbase, 0);
+      int32_t kn = (int32_t)((nbase + (nincl - nmine)) & 0xFFFFFFFFull);
+      long long kf = (long long)fbase + (fincl - fcnt);
+#pragma unroll
+      for (int j = 0; j < kSsspTpvItems; ++j) {
+        if (code[j] == 1) {
+          if (GR_IN(kn, a.n + 1, 324)) Qn[kn] = v[j];
+          ++kn;
+        } else if (code[j] == 2) {
+          if (GR_IN(kf, st.far_cap, 325)) st.far_dest[kf] = v[j];
+          ++kf;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+  if (lane == 0 && local_min != 0xFFFFFFFFu) atomicMin(st.fmin, local_min);
+}
+
 __device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm,
                            const SsspStep &st) {
   const int32_t *F = pick(a.farq, st.far_parity);
@@ -297,6 +421,7 @@ __device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm
   if ((threadIdx.x & 31) == 0 && local_min != 0xFFFFFFFFu) atomicMin(st.fmin, local_min);
 }
 
+template <bool LOW>
 __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   SsspStep st;
   st.near_parity = c->near_parity;
@@ -313,7 +438,8 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   st.far_dest = pick(a.farq, c->far_parity);
   st.far_cap = a.n + 1;
   st.fmin = &c->far_min;
-  relax_body(a, c->dist, sm, st);
+  if (LOW) relax_body_thread(a, c->dist, st);
+  else relax_body(a, c->dist, sm, st);
 }
 
 __device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
@@ -386,6 +512,8 @@ __device__ void sssp_end(const SsspArgs &a, SsspCtl *c) {
   }
 }
 
+// LOW: per-thread relaxation (graphs of small maximum degree)
+template <bool LOW>
 __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
     k_sssp_iter(SsspArgs a, cudaGraphConditionalHandle h, int32_t use_cond) {
   SsspCtl *c = a.ctl;
@@ -402,7 +530,7 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
     sm.farb.cnt = 0;
   }
   __syncthreads();
-  if (c->mode == kSsspRelax) relax_mode(a, c, sm);
+  if (c->mode == kSsspRelax) relax_mode<LOW>(a, c, sm);
   else split_mode(a, c, sm);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -423,6 +551,7 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
 // iteration's counters and recomputes the same next state in registers; the
 // counters form rings of three (the one an iteration fills, the one just
 // read, the one block 0 clears for the next iteration).
+template <bool LOW>
 __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(SsspArgs a) {
   SsspCtl *c = a.ctl;
   __shared__ SsspSmem sm;
@@ -439,7 +568,6 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
   int32_t iter = 0, far_epoch = 0, phases = 0, gen = 0;
   uint32_t far_min = 0xFFFFFFFFu;
   unsigned long long T = delta, T_old = 0;
-  bool timed_out = false;
   for (;;) {
     const int32_t slot = iter % 3, clear = (iter + 1) % 3;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -463,16 +591,14 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
     if (mode == kSsspRelax) {
       st.far_dest = pick(a.farq, far_parity) + far_len;  // appended after the pile
       st.far_cap = (long long)a.n + 1 - far_len;
-      relax_body(a, dist, sm, st);
+      if (LOW) relax_body_thread(a, dist, st);
+      else relax_body(a, dist, sm, st);
     } else {
       st.far_dest = pick(a.farq, far_parity ^ 1);
       st.far_cap = a.n + 1;
       split_body(a, dist, sm, st);
     }
-    if (!grid_sync(&c->bar, &c->error, gen)) {
-      timed_out = true;
-      break;
-    }
+    if (!grid_sync(&c->bar, &c->error, gen)) break;  // a wait gave up: error is set
     const unsigned long long pk = *(volatile unsigned long long *)&c->ring_near[slot];
     const int32_t fcnt = *(volatile int32_t *)&c->ring_far[slot];
     const uint32_t fmin = *(volatile uint32_t *)&c->ring_fmin[slot];
@@ -515,7 +641,6 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
       break;
     }
   }
-  (void)timed_out;
 }
 
 // pred[v] = smallest u with an edge (u, v) and dist[u] + w = dist[v]
@@ -589,12 +714,16 @@ static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws) {
   a.stamp = ws->stamp.as<int32_t>();
   a.far_stamp = ws->far_stamp.as<int32_t>();
   a.ctl = ws->ctl.as<SsspCtl>();
+  a.low_degree = g->max_degree <= kSsspLowDegreeMax ? 1 : 0;
   return a;
 }
 
 static gr_status sssp_enqueue_iter(gr_graph *g, const SsspArgs &a, cudaStream_t s,
                                    cudaGraphConditionalHandle h, int use_cond) {
-  k_sssp_iter<<<g->num_sms * kSsspBlocksPerSm, kSsspThreads, 0, s>>>(a, h, use_cond);
+  if (a.low_degree)
+    k_sssp_iter<true><<<g->num_sms * kSsspBlocksPerSm, kSsspThreads, 0, s>>>(a, h, use_cond);
+  else
+    k_sssp_iter<false><<<g->num_sms * kSsspBlocksPerSm, kSsspThreads, 0, s>>>(a, h, use_cond);
   GR_CUDA(cudaGetLastError());
   return GR_OK;
 }
@@ -660,12 +789,13 @@ gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, 
   const int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
   if (mode == GR_MODE_PERSISTENT) {
     int per_sm = 0;
-    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp_do, kSsspThreads, 0));
+    void *kern = a.low_degree ? (void *)k_sssp_do<true> : (void *)k_sssp_do<false>;
+    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSsspThreads, 0));
     int bps = std::min(per_sm, kSsspBlocksPerSm);
     const int32_t want = o.block > 0 ? o.block : g->tuned_sssp_blocks_per_sm;
     if (want > 0) bps = std::min(bps, want);
     void *args[] = {&a};
-    GR_CUDA(cudaLaunchCooperativeKernel((void *)k_sssp_do, std::max(1, bps) * g->num_sms,
+    GR_CUDA(cudaLaunchCooperativeKernel(kern, std::max(1, bps) * g->num_sms,
                                         kSsspThreads, args, 0, s));
   } else if (mode == GR_MODE_LAUNCH) {
     SsspCtl h;

@@ -30,6 +30,9 @@ void tune_prior(gr_graph *g) {
   if (g->max_degree <= 32) {
     g->tuned_direction = GR_DIR_PUSH;  // never pull: frontiers stay thin
     g->tuned_blocks_per_sm = 1;
+    // thousands of thin iterations: one kernel with a cheap grid barrier
+    g->tuned_sssp_mode = GR_MODE_PERSISTENT;
+    g->tuned_sssp_blocks_per_sm = 1;
   } else {
     g->tuned_direction = GR_DIR_AUTO;
     g->tuned_blocks_per_sm = 0;  // all resident blocks
