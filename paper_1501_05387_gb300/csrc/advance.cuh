@@ -482,11 +482,13 @@ namespace gr {
 // Barrier of the persistent (cooperative) kernels. Blocks arrive at one of
 // kBarrierGroups group counters; a group's last arriver clears it and
 // arrives at the root; the root's last arriver releases everyone by bumping
-// the generation. Every counter sits on its own 128-byte line so that the
+// the generation (grids of at most kFlatBarrierBlocks blocks arrive at the
+// root directly). Every counter sits on its own 128-byte line so that the
 // waiters' polling does not slow the arrivals. The wait is bounded: after
 // kSpinLimit polls the block records kDevTimeout in *error and returns
 // false (callers then leave their loop; the other blocks time out too).
 constexpr int kBarrierGroups = 16;
+constexpr int kFlatBarrierBlocks = 256;  // grids up to this size use a one-level barrier
 
 struct alignas(128) BarrierLine {
   int32_t v;
@@ -513,17 +515,27 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, int32_t *error, int32_
     __threadfence();
     const int32_t nblocks = gridDim.x;
     const int32_t my_gen = gen;
-    const int32_t grp = blockIdx.x % kBarrierGroups;
-    const int32_t members = (nblocks - grp + kBarrierGroups - 1) / kBarrierGroups;
-    const int32_t groups = min(nblocks, kBarrierGroups);
     bool release = false;
-    if (atomicAdd(&b->group[grp].v, 1) == members - 1) {
-      b->group[grp].v = 0;
-      __threadfence();
-      if (atomicAdd(&b->root.v, 1) == groups - 1) {
+    if (nblocks <= kFlatBarrierBlocks) {
+      // small grids: every block arrives at the root directly (one atomic
+      // round trip less than the two-level form)
+      if (atomicAdd(&b->root.v, 1) == nblocks - 1) {
         b->root.v = 0;
         __threadfence();
         release = true;
+      }
+    } else {
+      const int32_t grp = blockIdx.x % kBarrierGroups;
+      const int32_t members = (nblocks - grp + kBarrierGroups - 1) / kBarrierGroups;
+      const int32_t groups = min(nblocks, kBarrierGroups);
+      if (atomicAdd(&b->group[grp].v, 1) == members - 1) {
+        b->group[grp].v = 0;
+        __threadfence();
+        if (atomicAdd(&b->root.v, 1) == groups - 1) {
+          b->root.v = 0;
+          __threadfence();
+          release = true;
+        }
       }
     }
     if (release) {
