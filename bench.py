@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--suite", action="store_true",
                     help="instead of the BFS line, measure every primitive on its workload "
                          "(SSSP s22, grid 4096^2 BFS/SSSP/CC, s23 PageRank/CC/BC/batched BFS)")
+    ap.add_argument("--suite-part", default="all",
+                    choices=["all", "sssp", "grid", "rmat", "pagerank", "cc", "bfs64", "bc64"],
+                    help="run one part of the suite (profiling runs)")
+    ap.add_argument("--suite-scale", type=int, default=0,
+                    help="R-MAT scale of the suite part (profiling runs; 0: the specified one)")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale (profiling runs only; the metric is quoted at 22)")
     ap.add_argument("--mode", default="auto", choices=["auto", "graph", "launch", "persistent"],
@@ -313,15 +318,32 @@ def run_suite(args):
     except Exception:
         peak = 6800.0
     out = []
-    INF = 0xFFFFFFFF
 
     def reach_bytes(r, reached, per_edge, per_vertex):
         deg = np.diff(r).astype(np.int64)
         n = r.size - 1
         return per_edge * int(deg[reached].sum()) + 4 * (n + 1) + per_vertex * int(reached.sum())
 
+    part = args.suite_part
+    want = lambda *names: part == "all" or part in names
+
     # --- SSSP on R-MAT s22 (weights [1,64], seed 3), the BFS sources
-    r, c = gg.rmat(22, 16, seed=2)
+    if want("sssp"):
+        suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes)
+    if want("grid"):
+        suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes)
+    if want("rmat", "pagerank", "cc", "bfs64", "bc64"):
+        suite_rmat(args, gr, gg, torch, dev, flush, peak, out, want)
+    print(json.dumps({"suite": out, "peak_hbm_gbs": peak}), flush=True)
+
+
+INF32 = 0xFFFFFFFF
+
+
+def suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
+    INF = INF32
+    scale = args.suite_scale or 22
+    r, c = gg.rmat(scale, 16, seed=2)
     w = gg.weights(r, c, seed=3, wmin=1, wmax=64)
     srcs = gg.sources(r, 16, seed=2)
     n, m = r.size - 1, c.size
@@ -335,15 +357,19 @@ def run_suite(args):
         per.append(ms)
         byts.append(reach_bytes(r, d != INF, 8, 4))
     mean = float(np.mean(per))
-    out.append({"workload": "rmat22_sssp", "primitive": "sssp", "calls": 2 * len(srcs),
+    it, ph, rl = gr.gr_sssp_stats(g)
+    out.append({"workload": f"rmat{scale}_sssp", "primitive": "sssp", "calls": 2 * len(srcs),
+                "last_call": {"iterations": it, "phases": ph, "edges_relaxed_per_m": rl / m},
                 "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
                 "tuned": gr.gr_tuned_opts(g),
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
                                   "8 B per column+weight entry of the reached vertices, "
                                   "4 B per row offset, 4 B per reached distance")})
     g.close()
-    del r, c, w
 
+
+def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
+    INF = INF32
     # --- 4096^2 grid, 5 % deletions (seed 4), weights [1,16]: BFS, SSSP, CC
     r, c = gg.grid(4096, p_del=0.05, seed=4)
     w = gg.weights(r, c, seed=4, wmin=1, wmax=16)
@@ -366,6 +392,8 @@ def run_suite(args):
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
                                   "4 B per column entry of the reached vertices, 4 B per "
                                   "row offset, 8 B depth+parent per reached vertex")})
+    # SSSP bucket width and driver tuned once on one sample source
+    gr.gr_autotune(g, [int(srcs[0])], gr.GR_TUNE_SSSP)
     per, byts, iters = [], [], []
     dist_g = torch.empty(n, dtype=torch.int32, device=dev)
     for s in srcs[:2]:
@@ -375,6 +403,7 @@ def run_suite(args):
         byts.append(reach_bytes(r, dist_g.cpu().numpy().view(np.uint32) != INF, 8, 4))
     mean = float(np.mean(per))
     out.append({"workload": "grid4096_sssp", "primitive": "sssp", "calls": 2,
+                "tuned_delta": gr.gr_tuned_opts(g)["delta"],
                 "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
                 "iterations": iters,
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
@@ -389,53 +418,71 @@ def run_suite(args):
                                   "4 B per column entry, 4 B per row offset, label write "
                                   "at init and after pointer jumping")})
     g.close()
-    del r, c, w
 
+
+def suite_rmat(args, gr, gg, torch, dev, flush, peak, out, want):
     # --- R-MAT s23 (seed 5): PageRank, CC, batched BFS and BC over 64 sources
-    r, c = gg.rmat(23, 16, seed=5)
+    scale = args.suite_scale or 23
+    tag = f"rmat{scale}"
+    r, c = gg.rmat(scale, 16, seed=5)
     n, m = r.size - 1, c.size
     g = gr.gr_graph_create(r, c)
+    srcs64 = gg.sources(r, 64, seed=5)
+    lv = 0
+    if want("rmat", "pagerank"):
+        suite_pagerank(gr, torch, dev, flush, peak, out, g, n, m, tag, args.mode)
+    if want("rmat", "cc"):
+        label = torch.empty(n, dtype=torch.int32, device=dev)
+        ms, _ = _timed_calls(lambda: gr.gr_cc(g, label, count=False), 3, flush)
+        out.append({"workload": f"{tag}_cc", "primitive": "cc", "calls": 3, "ms_per_call": ms,
+                    "throughput": m / (ms * 1e-3) / 1e9, "unit": "G edges/s",
+                    "roofline": _roof(4 * m + 4 * (n + 1) + 8 * n, ms, peak,
+                                      "4 B per column entry, 4 B per row offset, label write "
+                                      "at init and after pointer jumping")})
+    if want("rmat", "bfs64", "bc64"):
+        depth64 = torch.empty(64 * n, dtype=torch.int32, device=dev)
+        ms, _ = _timed_calls(lambda: gr.gr_bfs_batch(g, srcs64, depth64), 2, flush)
+        lv = int(depth64.view(64, n).max().item()) + 1
+        if want("rmat", "bfs64"):
+            out.append({"workload": f"{tag}_bfs64", "primitive": "batched bfs (64 lanes)",
+                        "calls": 2, "ms_per_call": ms, "levels": lv,
+                        "throughput": 64 * m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+                        "roofline": _roof(lv * (4 * m + 4 * (n + 1) + 24 * n) + 4 * 64 * n, ms,
+                                          peak,
+                                          "per level a sweep of every column entry and row "
+                                          "offset with three 8 B lane masks per vertex; 4 B "
+                                          "per lane depth written")})
+        del depth64
+    if want("rmat", "bc64"):
+        bc = torch.empty(n, dtype=torch.float64, device=dev)
+        ms, _ = _timed_calls(lambda: gr.gr_bc(g, srcs64, bc), 1, flush)
+        out.append({"workload": f"{tag}_bc64", "primitive": "bc (64 sources, FP64)", "calls": 1,
+                    "ms_per_call": ms, "levels": lv,
+                    "throughput": 64 * 2 * m / (ms * 1e-3) / 1e9,
+                    "unit": "GTEPS (2|E| per source)",
+                    "roofline": _roof(2 * lv * (4 * m + 4 * (n + 1) + 16 * n) + 4 * 512 * n,
+                                      ms, peak,
+                                      "forward and backward: per level a sweep of every column "
+                                      "entry and row offset with two 8 B lane masks per vertex; "
+                                      "sigma and dependency rows (512 B per vertex) written and "
+                                      "read once each")})
+    g.close()
+
+
+def suite_pagerank(gr, torch, dev, flush, peak, out, g, n, m, tag, mode="auto"):
     rank = torch.empty(n, dtype=torch.float32, device=dev)
-    it = gr.gr_pagerank(g, rank)
-    ms, _ = _timed_calls(lambda: gr.gr_pagerank(g, rank, count=False), 2, flush)
+    # launch mode (host-enqueued iterations) only for profiling runs: ncu
+    # cannot profile the kernels inside a graph's while loop one by one
+    o = gr.gr_opts(mode=gr.GR_MODE_LAUNCH) if mode == "launch" else None
+    it = gr.gr_pagerank(g, rank, opts=o)
+    ms, _ = _timed_calls(lambda: gr.gr_pagerank(g, rank, opts=o, count=False), 2, flush)
     per_iter = 4 * m + 4 * (n + 1) + 12 * n
-    out.append({"workload": "rmat23_pagerank", "primitive": "pagerank", "calls": 2,
+    out.append({"workload": f"{tag}_pagerank", "primitive": "pagerank", "calls": 2,
                 "ms_per_call": ms, "iterations": it,
                 "throughput": it / (ms * 1e-3), "unit": "iterations/s",
                 "roofline": _roof(per_iter * it, ms, peak,
                                   "per iteration: 4 B per column entry, 4 B per row offset, "
                                   "contribution write, rank read+write (12 B per vertex)")})
-    label = torch.empty(n, dtype=torch.int32, device=dev)
-    ms, _ = _timed_calls(lambda: gr.gr_cc(g, label, count=False), 3, flush)
-    out.append({"workload": "rmat23_cc", "primitive": "cc", "calls": 3, "ms_per_call": ms,
-                "throughput": m / (ms * 1e-3) / 1e9, "unit": "G edges/s",
-                "roofline": _roof(4 * m + 4 * (n + 1) + 8 * n, ms, peak,
-                                  "4 B per column entry, 4 B per row offset, label write "
-                                  "at init and after pointer jumping")})
-    srcs64 = gg.sources(r, 64, seed=5)
-    depth64 = torch.empty(64 * n, dtype=torch.int32, device=dev)
-    ms, _ = _timed_calls(lambda: gr.gr_bfs_batch(g, srcs64, depth64), 2, flush)
-    lv = int(depth64.view(64, n).max().item()) + 1
-    out.append({"workload": "rmat23_bfs64", "primitive": "batched bfs (64 lanes)", "calls": 2,
-                "ms_per_call": ms, "levels": lv,
-                "throughput": 64 * m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
-                "roofline": _roof(lv * (4 * m + 4 * (n + 1) + 24 * n) + 4 * 64 * n, ms, peak,
-                                  "per level a sweep of every column entry and row offset "
-                                  "with three 8 B lane masks per vertex; 4 B per lane "
-                                  "depth written")})
-    bc = torch.empty(n, dtype=torch.float64, device=dev)
-    ms, _ = _timed_calls(lambda: gr.gr_bc(g, srcs64, bc), 1, flush)
-    out.append({"workload": "rmat23_bc64", "primitive": "bc (64 sources, FP64)", "calls": 1,
-                "ms_per_call": ms, "levels": lv,
-                "throughput": 64 * 2 * m / (ms * 1e-3) / 1e9, "unit": "GTEPS (2|E| per source)",
-                "roofline": _roof(2 * lv * (4 * m + 4 * (n + 1) + 16 * n) + 4 * 512 * n,
-                                  ms, peak,
-                                  "forward and backward: per level a sweep of every column "
-                                  "entry and row offset with two 8 B lane masks per vertex; "
-                                  "sigma and dependency rows (512 B per vertex) written and "
-                                  "read once each")})
-    g.close()
-    print(json.dumps({"suite": out, "peak_hbm_gbs": peak}), flush=True)
 
 
 def cpu_baseline(r, c, srcs, m, k):

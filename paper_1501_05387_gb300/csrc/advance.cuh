@@ -307,20 +307,27 @@ namespace gr {
 // --------------------------------------------------- neighbourhood reduce
 // Gather-reduce over the neighbourhoods of all vertices (the operator the
 // paper proposes in Sec. 7 for reductions over neighbour lists):
-// acc[v] += sum over edges e = (v, u) of g(u, e), for every v, with the same
-// merge-path chunking as lb_advance over the all-vertex frontier (S = R).
-// Consecutive lanes hold consecutive edge ranks, so the owners within a warp
-// are sorted; a segmented warp sum leaves one total per owner run, added
-// with one atomicAdd. acc must be zero (or hold a partial sum) beforehand.
+// acc[v] += sum over edges e = (v, u) of g(u, e), for every v.
+//
+// Merge-based form: the vertex-end markers (R[v+1] + v) and the edge ranks
+// form one merged sequence split into equal chunks (as in lb_advance). A
+// block stages its chunk's end markers and the gathered values g(C[e], e) of
+// its edges in shared memory (coalesced column loads, all gathers of the
+// chunk in flight at once); then each thread takes ITEMS consecutive items
+// of the chunk, finds its start with one search in shared memory and walks
+// them in order, adding values and closing a vertex at each end marker. A
+// vertex whose edges lie inside one thread's items is written with a plain
+// store; the pieces of a vertex split between threads or chunks are added
+// with atomicAdd. acc must be zero beforehand.
 template <int THREADS, int ITEMS, class T, class G>
 __device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n, G &g,
                                    T *acc) {
   constexpr int CHUNK = THREADS * ITEMS;
   const long long total = (long long)n + R[n];
   const long long nchunks = (total + CHUNK - 1) / CHUNK;
-  __shared__ int32_t s_off[CHUNK + 1];
+  __shared__ int32_t s_end[CHUNK + 1];  // end marker of each vertex, chunk-local
+  __shared__ T s_val[CHUNK];
   __shared__ int32_t s_red8[THREADS / 32];
-  const int lane = threadIdx.x & 31;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * CHUNK;
     const long long d1 = min(d0 + CHUNK, total);
@@ -328,34 +335,47 @@ __device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n
     block_chunk_bounds<THREADS>(R, n, R[n], d0, d1, CHUNK, s_red8, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= n - 1) ? (min(i1, n - 1) - i0 + 1) : 0;
-    for (int32_t k = threadIdx.x; k < nv; k += THREADS) s_off[k] = R[i0 + k];
-    __syncthreads();
     const int32_t ne = (int32_t)(j1 - j0);
-    for (int32_t kb = 0; kb < ne; kb += THREADS) {
-      const int32_t k = kb + threadIdx.x;
-      int32_t owner = -1;
-      T val = T(0);
-      if (k < ne) {
-        const int32_t e = (int32_t)(j0 + k);
-        int32_t lo = 0, hi = nv - 1;
-        while (lo < hi) {
-          const int32_t mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= e) lo = mid;
-          else hi = mid - 1;
+    const int32_t len = (int32_t)(d1 - d0);
+    for (int32_t k = threadIdx.x; k < nv; k += THREADS)
+      s_end[k] = (int32_t)((long long)R[i0 + k + 1] + i0 + k - d0);
+#pragma unroll 4
+    for (int32_t k = threadIdx.x; k < ne; k += THREADS) {
+      const int32_t e = (int32_t)(j0 + k);
+      s_val[k] = g(C[e], e);
+    }
+    __syncthreads();
+    // this thread's items [k0, k1) of the chunk
+    const int32_t k0 = min(len, (int32_t)threadIdx.x * ITEMS);
+    const int32_t k1 = min(len, k0 + ITEMS);
+    if (k0 < k1) {
+      // vertices whose end marker lies before k0
+      int32_t lo = 0, hi = nv;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (s_end[mid] < k0) lo = mid + 1;
+        else hi = mid;
+      }
+      int32_t r = lo;
+      int32_t e = k0 - r;   // chunk-local edge index
+      T sum = T(0);
+      bool first = true;    // the current vertex may have edges before k0
+      for (int32_t k = k0; k < k1; ++k) {
+        if (r < nv && s_end[r] == k) {  // end marker of vertex i0 + r
+          if (first) {
+            if (sum != T(0)) atomicAdd(acc + i0 + r, sum);
+          } else if (sum != T(0)) {
+            acc[i0 + r] = sum;
+          }
+          sum = T(0);
+          first = false;
+          ++r;
+        } else {
+          sum += s_val[e];
+          ++e;
         }
-        owner = i0 + lo;
-        val = g(C[e], e);
       }
-      // segmented suffix sum over runs of equal owners
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const T vo = __shfl_down_sync(0xffffffffu, val, o);
-        const int32_t oo = __shfl_down_sync(0xffffffffu, owner, o);
-        if (lane + o < 32 && oo == owner) val += vo;
-      }
-      const int32_t prev = __shfl_up_sync(0xffffffffu, owner, 1);
-      const bool head = owner >= 0 && (lane == 0 || prev != owner);
-      if (head) atomicAdd(acc + owner, val);
+      if (sum != T(0) && r < nv) atomicAdd(acc + i0 + r, sum);  // continues past k1
     }
     __syncthreads();
   }

@@ -228,7 +228,7 @@ static PrArgs pr_args(gr_graph *g) {
 
 static gr_status pr_enqueue_iter(gr_graph *g, const PrArgs &a, cudaStream_t s,
                                  cudaGraphConditionalHandle h, int use_cond) {
-  k_pr_gather<<<g->num_sms * 4, kPrThreads, 0, s>>>(a);
+  k_pr_gather<<<g->num_sms * 8, kPrThreads, 0, s>>>(a);
   k_pr_update<<<g->num_sms * 4, 256, 0, s>>>(a);
   k_pr_end<<<1, 32, 0, s>>>(a, h, use_cond);
   GR_CUDA(cudaGetLastError());
