@@ -339,10 +339,20 @@ __device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n
     const int32_t len = (int32_t)(d1 - d0);
     for (int32_t k = threadIdx.x; k < nv; k += THREADS)
       s_end[k] = (int32_t)((long long)R[i0 + k + 1] + i0 + k - d0);
-#pragma unroll 4
-    for (int32_t k = threadIdx.x; k < ne; k += THREADS) {
-      const int32_t e = (int32_t)(j0 + k);
-      s_val[k] = g(C[e], e);
+    {
+      // all column loads of the thread first, then all gathers: ITEMS
+      // independent gathers in flight per thread
+      int32_t col[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = threadIdx.x + i * THREADS;
+        col[i] = k < ne ? C[j0 + k] : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = threadIdx.x + i * THREADS;
+        if (k < ne) s_val[k] = g(col[i], (int32_t)(j0 + k));
+      }
     }
     __syncthreads();
     // this thread's items [k0, k1) of the chunk

@@ -37,10 +37,14 @@
 namespace gr {
 
 constexpr int kMbThreads = 256, kMbItems = 4;
+// Batched BFS keeps the lane masks of its first kKeepLevels levels and
+// writes their depths in one pass (k_mb_depth); deeper levels write depths
+// as they are reached.
+constexpr int32_t kKeepLevels = 64;
 constexpr int kMbChunk = kMbThreads * kMbItems;
 
 struct BatchWorkspace {
-  DevMem visit, sigma, q, counter, srcs;
+  DevMem visit, sigma, q, counter, srcs, lmp;
   std::vector<DevMem *> lm;  // lm[L]: lane masks of level L
   ~BatchWorkspace() {
     for (DevMem *p : lm) delete p;
@@ -339,6 +343,38 @@ __global__ void k_bc_finalize(const unsigned long long *lv, const double *sigma,
   }
 }
 
+// Depths of a batched BFS from its per-level lane masks, written once, in
+// full coalesced rows: for each lane s, depth[s][v] = the level L whose mask
+// lm[L][v] holds bit s (-1 if none). The masks of one vertex are disjoint,
+// so the level of every lane follows from six bit slices: slice j is the OR
+// of the masks of the levels whose index has bit j set.
+__global__ void k_mb_depth(const unsigned long long *const *lm, int32_t levels, int32_t n,
+                           int32_t k, int32_t *depth) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nr = ((int64_t)n + 31) & ~31ll;  // warp-uniform bound
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nr; v += stride) {
+    unsigned long long b[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull}, reached = 0ull;
+    if (v < n) {
+      for (int32_t L = 0; L < levels; ++L) {
+        const unsigned long long m = lm[L][v];
+        reached |= m;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+          if ((L >> j) & 1) b[j] |= m;
+      }
+    }
+    for (int32_t s = 0; s < k; ++s) {
+      int32_t d = -1;
+      if ((reached >> s) & 1ull) {
+        d = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) d |= (int32_t)((b[j] >> s) & 1ull) << j;
+      }
+      if (v < n) depth[(int64_t)s * n + v] = d;
+    }
+  }
+}
+
 __global__ void k_fill_f64(double *x, int64_t n, double val) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -354,6 +390,7 @@ size_t batch_ws_bytes(const gr_graph *g) {
 
 gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out) {
   std::unique_ptr<BatchWorkspace> ws(new BatchWorkspace());
+  GR_TRY(ws->lmp.alloc(sizeof(unsigned long long *) * kKeepLevels, "level mask table"));
   GR_TRY(ws->visit.alloc(sizeof(unsigned long long) * (size_t)g->n, "lane visit masks"));
   GR_TRY(ws->counter.alloc(sizeof(unsigned long long) * 4, "batch counters"));
   GR_TRY(ws->srcs.alloc(sizeof(int32_t) * 64, "batch sources"));
@@ -411,20 +448,38 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
   a.k = k;
   a.count = ws->counter.as<unsigned long long>();
   int32_t L = 0;
-  // BC keeps every level's masks for the backward pass; BFS needs only the
-  // current and the next level, so it alternates two arrays
-  auto slot = [&](int32_t lvl) { return with_sigma ? (size_t)lvl : (size_t)(lvl & 1); };
+  // BC keeps every level's masks for the backward pass; BFS keeps those of
+  // its first kKeepLevels levels (their depths are written in one pass) and
+  // then alternates two arrays, writing depths level by level
+  auto slot = [&](int32_t lvl) {
+    if (with_sigma || lvl < kKeepLevels) return (size_t)lvl;
+    return (size_t)(kKeepLevels + ((lvl - kKeepLevels) & 1));
+  };
+  bool depth_pass_done = false;
+  auto depth_pass = [&](int32_t levels) -> gr_status {
+    std::vector<unsigned long long *> ptrs(kKeepLevels, nullptr);
+    for (int32_t i = 0; i < levels; ++i) ptrs[i] = ws->lm[i]->as<unsigned long long>();
+    GR_CUDA(cudaMemcpyAsync(ws->lmp.p, ptrs.data(), sizeof(unsigned long long *) * kKeepLevels,
+                            cudaMemcpyHostToDevice, s));
+    k_mb_depth<<<grid, 256, 0, s>>>((const unsigned long long *const *)ws->lmp.p, levels, g->n,
+                                    k, depth);
+    GR_CUDA(cudaGetLastError());
+    depth_pass_done = true;
+    return GR_OK;
+  };
   for (;;) {
+    if (depth && L == kKeepLevels) GR_TRY(depth_pass(kKeepLevels));
     unsigned long long *nxt;
     GR_TRY(level_mask(g, ws, slot(L + 1), s, &nxt));
     a.cur = ws->lm[slot(L)]->as<unsigned long long>();
     a.nxt = nxt;
     a.level = L;
+    a.depth = (depth && L >= kKeepLevels) ? depth : nullptr;
     GR_CUDA(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
     if (with_sigma)
       k_mb_forward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
     else
-      k_mb_forward<false><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
+      k_mb_forward<false><<<g->num_sms * 8, kMbThreads, 0, s>>>(a);
     GR_CUDA(cudaGetLastError());
     unsigned long long cnt = 0;
     GR_CUDA(cudaMemcpyAsync(&cnt, a.count, sizeof(cnt), cudaMemcpyDeviceToHost, s));
@@ -433,6 +488,7 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     if (cnt == 0) break;  // level L is empty; levels 0..L-1 hold vertices
     if (L >= max_levels) return fail(GR_ETIMEOUT, "level limit reached");
   }
+  if (depth && !depth_pass_done) GR_TRY(depth_pass(L));
   *levels_out = L;
   return GR_OK;
 }
@@ -440,8 +496,7 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
 // Batched BFS into a device depth array [k][n] with an explicit workspace.
 gr_status bfs_batch_run(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
                         int32_t *depth, int32_t max_levels, cudaStream_t s) {
-  GR_CUDA(cudaMemsetAsync(depth, 0xFF, sizeof(int32_t) * (size_t)k * (size_t)g->n, s));
-  int32_t levels = 0;
+  int32_t levels = 0;  // every depth entry is written by run_forward
   return run_forward(g, ws, h_srcs, k, depth, false, s, max_levels, &levels);
 }
 

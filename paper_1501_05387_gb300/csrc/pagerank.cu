@@ -93,7 +93,7 @@ __global__ void k_pr_init(PrArgs a, float *rank, float damping, int32_t max_iter
 
 struct ContribG {
   const float *contrib;
-  __device__ __forceinline__ float operator()(int32_t u, int32_t) const { return contrib[u]; }
+  __device__ __forceinline__ float operator()(int32_t u, int32_t) const { return __ldg(contrib + u); }
 };
 
 __global__ void __launch_bounds__(kPrThreads) k_pr_gather(PrArgs a) {

@@ -63,6 +63,19 @@ def test_batch_bfs_repeats_isolated_and_grid(cuda_lib):
             assert np.array_equal(d[i], oracle.bfs(r, c, s)[0])
 
 
+@pytest.mark.parametrize("n", [63, 64, 65, 66, 130, 300])
+def test_batch_bfs_long_paths(cuda_lib, n):
+    # the depths of the first 64 levels come from the kept level masks, those
+    # of deeper levels are written as they are reached: cover both and the
+    # boundary between them
+    r, c = gg.from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    srcs = [0, n // 2, n - 1, 0]
+    with cuda_lib.gr_graph_create(r, c) as g:
+        d = run_batch(cuda_lib, g, srcs)
+        for i, s in enumerate(srcs):
+            assert np.array_equal(d[i], np.abs(np.arange(n) - s).astype(np.int32))
+
+
 def test_batch_bfs_bad_args(cuda_lib):
     import torch
     r, c = gg.from_edges(5, [(0, 1)])
