@@ -16,19 +16,32 @@
 // only ever hooked under a smaller id, the root of each component is its
 // smallest vertex id, which is the canonical label.
 //
-// Symmetric graphs store each undirected edge twice; only the (u, v) with
-// u > v copy hooks. For a directed CSR every arc hooks, giving weakly
-// connected components.
+// Symmetric graphs store each undirected edge twice, so most edges need no
+// visit at all: the sampling form of the hooking sweep first hooks every
+// vertex to its first kCcSample neighbours and compresses, which on graphs
+// with one giant component already places most vertices in it; the
+// component that most of a fixed sample of vertices lies in is then
+// skipped, and only the vertices outside it hook all their edges (an edge
+// between two vertices of that component needs no visit, one leaving it is
+// visited from its other end). Labels are the same as with a full sweep:
+// hooking under the smaller root makes every root its component's smallest
+// id whatever the order. For a directed CSR every arc hooks in one sweep,
+// giving weakly connected components (an arc is not visible from its head).
 #include <algorithm>
+#include <vector>
 
 #include "advance.cuh"
 
 namespace gr {
 
 constexpr int kCcThreads = 256, kCcItems = 8;
+constexpr int kCcSample = 2;    // neighbours per vertex hooked before the skip
+constexpr int kCcPicks = 1024;  // vertices whose roots choose the skipped component
+constexpr int kCcFrontierCap = 1024;
 
 struct CcWorkspace {
-  DevMem counter;
+  DevMem counter;  // [0] components, [1] scratch; [2..3] packed frontier counter
+  DevMem q, sc, picks;
 };
 
 void free_cc(CcWorkspace *ws) { delete ws; }
@@ -44,6 +57,13 @@ __global__ void k_cc_init(int32_t *label, int32_t n) {
 }
 
 // root of x with path halving (pointers only ever decrease)
+__device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x);
+
+// Join the trees of u and v: the larger root is re-pointed to the smaller
+// one with a CAS, retried from the current roots if another thread moved
+// the root first.
+__device__ __forceinline__ void hook(int32_t *label, int32_t u, int32_t v);
+
 __device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x) {
   int32_t p = label[x];
   while (p != x) {
@@ -55,6 +75,19 @@ __device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x) {
   return x;
 }
 
+__device__ __forceinline__ void hook(int32_t *label, int32_t u, int32_t v) {
+  int32_t a = find_root(label, u);
+  int32_t b = find_root(label, v);
+  while (a != b) {
+    const int32_t hi = max(a, b), lo = min(a, b);
+    const int32_t prev = atomicCAS(label + hi, hi, lo);
+    if (prev == hi) break;  // hooked
+    // hi stopped being a root: continue from the roots as they are now
+    a = find_root(label, prev);
+    b = find_root(label, lo);
+  }
+}
+
 struct HookF {
   int32_t *label;
   int32_t only_lower;  // symmetric graph: hook each undirected edge once
@@ -62,19 +95,75 @@ struct HookF {
   __device__ __forceinline__ int operator()(int32_t u, int32_t v, int32_t) const {
     if (!GR_IN(u, n, 401) || !GR_IN(v, n, 402)) return 0;
     if (only_lower && v >= u) return 0;
-    int32_t a = find_root(label, u);
-    int32_t b = find_root(label, v);
-    while (a != b) {
-      const int32_t hi = max(a, b), lo = min(a, b);
-      const int32_t prev = atomicCAS(label + hi, hi, lo);
-      if (prev == hi) break;  // hooked
-      // hi stopped being a root: continue from the roots as they are now
-      a = find_root(label, prev);
-      b = find_root(label, lo);
-    }
+    hook(label, u, v);
     return 0;  // edge settled: filtered out of the edge frontier
   }
 };
+
+// Each vertex hooks to its first kCcSample neighbours.
+__global__ void k_cc_sample(const int32_t *R, const int32_t *C, int32_t n, int32_t *label) {
+  for (int64_t vv = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; vv < n;
+       vv += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = (int32_t)vv;
+    const int32_t r0 = R[v], r1 = min(R[v + 1], r0 + kCcSample);
+    for (int32_t e = r0; e < r1; ++e) {
+      const int32_t u = C[e];
+      if (GR_IN(u, n, 403)) hook(label, v, u);
+    }
+  }
+}
+
+// Roots (labels after compression) of kCcPicks vertices spread over the ids
+// by a multiplicative hash.
+__global__ void k_cc_pick(const int32_t *label, int32_t n, int32_t *picks) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kCcPicks) picks[i] = label[(int32_t)(((unsigned long long)i * 2654435761ull) % n)];
+}
+
+// The vertices outside component `skip` that have edges, with their
+// degrees (an exclusive scan, emitted block by block with one packed atomic):
+// the frontier whose edges the last hooking pass visits.
+__global__ void __launch_bounds__(kCcThreads) k_cc_rest_frontier(const int32_t *R,
+                                                                  const int32_t *label, int32_t n,
+                                                                  int32_t skip, int32_t *Q,
+                                                                  int32_t *S,
+                                                                  unsigned long long *packed) {
+  __shared__ ScannedBuf<kCcFrontierCap> buf;
+  if (threadIdx.x == 0) buf.cnt = 0;
+  __syncthreads();
+  constexpr int PER = kCcFrontierCap / kCcThreads;
+  for (int64_t base = (int64_t)blockIdx.x * kCcFrontierCap; base < n;
+       base += (int64_t)gridDim.x * kCcFrontierCap) {  // block-uniform
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int64_t v = base + j * kCcThreads + threadIdx.x;
+      int32_t d = 0;
+      bool take = false;
+      if (v < n) {
+        d = R[v + 1] - R[v];
+        take = d > 0 && label[v] != skip;
+      }
+      emit_scanned(buf, take, (int32_t)v, d);
+    }
+    flush_scanned<kCcThreads>(buf, packed, Q, S, (long long)n + 1);
+  }
+}
+
+// S[q] = the frontier's edge total (the advance reads it as the scan's end).
+__global__ void k_cc_close(const unsigned long long *packed, int32_t *S) {
+  const unsigned long long p = *packed;
+  S[(int32_t)(p & 0xFFFFFFFFull)] = (int32_t)(p >> 32);
+}
+
+// Hook every edge of the frontier Q (size and scan from k_cc_rest_frontier).
+__global__ void __launch_bounds__(kCcThreads) k_cc_hook_rest(const int32_t *R, const int32_t *C,
+                                                              int32_t n, int32_t *label,
+                                                              const int32_t *Q, const int32_t *S,
+                                                              const unsigned long long *packed) {
+  HookF f{label, 0, n};
+  const int32_t q = (int32_t)(*packed & 0xFFFFFFFFull);
+  lb_advance<kCcThreads, kCcItems, 0>(R, C, Q, q, S, f, nullptr, nullptr, nullptr, nullptr);
+}
 
 __global__ void __launch_bounds__(kCcThreads) k_cc_hook(const int32_t *R, const int32_t *C,
                                                          int32_t n, int32_t *label,
@@ -101,11 +190,19 @@ __global__ void k_cc_jump(int32_t *label, int32_t n, int32_t *num_roots) {
 
 }  // namespace
 
-size_t cc_ws_bytes(const gr_graph *) { return sizeof(int32_t) * 4; }
+size_t cc_ws_bytes(const gr_graph *g) {
+  return sizeof(int32_t) * 4 + sizeof(int32_t) * (2 * (size_t)g->n + 3) +
+         sizeof(int32_t) * kCcPicks;
+}
 
-gr_status cc_ws_create(gr_graph *, CcWorkspace **out) {
+gr_status cc_ws_create(gr_graph *g, CcWorkspace **out) {
   std::unique_ptr<CcWorkspace> ws(new CcWorkspace());
   GR_TRY(ws->counter.alloc(sizeof(int32_t) * 4, "CC counters"));
+  if (g->symmetric) {
+    GR_TRY(ws->q.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "CC frontier"));
+    GR_TRY(ws->sc.alloc(sizeof(int32_t) * ((size_t)g->n + 2), "CC frontier degree scan"));
+    GR_TRY(ws->picks.alloc(sizeof(int32_t) * kCcPicks, "CC root sample"));
+  }
   *out = ws.release();
   return GR_OK;
 }
@@ -115,11 +212,37 @@ gr_status cc_ws_create(gr_graph *, CcWorkspace **out) {
 gr_status cc_run(gr_graph *g, CcWorkspace *ws, int32_t *label, cudaStream_t s) {
   int32_t *cnt = ws->counter.as<int32_t>();
   const int grid = g->num_sms * 8;
-  GR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), s));
+  const int32_t *R = g->row_off.as<int32_t>(), *C = g->col.as<int32_t>();
+  GR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 4, s));
   k_cc_init<<<grid, 256, 0, s>>>(label, g->n);
-  k_cc_hook<<<g->num_sms * 4, kCcThreads, 0, s>>>(g->row_off.as<int32_t>(),
-                                                  g->col.as<int32_t>(), g->n, label,
-                                                  g->symmetric ? 1 : 0);
+  if (!g->symmetric) {
+    k_cc_hook<<<g->num_sms * 4, kCcThreads, 0, s>>>(R, C, g->n, label, 0);
+  } else {
+    k_cc_sample<<<grid, 256, 0, s>>>(R, C, g->n, label);
+    k_cc_jump<<<grid, 256, 0, s>>>(label, g->n, cnt + 1);  // compress (count unused)
+    k_cc_pick<<<(kCcPicks + 255) / 256, 256, 0, s>>>(label, g->n, ws->picks.as<int32_t>());
+    GR_CUDA(cudaGetLastError());
+    std::vector<int32_t> picks(kCcPicks);
+    GR_CUDA(cudaMemcpyAsync(picks.data(), ws->picks.p, sizeof(int32_t) * kCcPicks,
+                            cudaMemcpyDeviceToHost, s));
+    GR_CUDA(cudaStreamSynchronize(s));
+    std::sort(picks.begin(), picks.end());
+    int32_t skip = picks[0], best = 0;
+    for (size_t i = 0; i < picks.size();) {
+      size_t j = i;
+      while (j < picks.size() && picks[j] == picks[i]) ++j;
+      if ((int32_t)(j - i) > best) {
+        best = (int32_t)(j - i);
+        skip = picks[i];
+      }
+      i = j;
+    }
+    unsigned long long *packed = ws->counter.as<unsigned long long>() + 1;
+    int32_t *Q = ws->q.as<int32_t>(), *S = ws->sc.as<int32_t>();
+    k_cc_rest_frontier<<<grid, kCcThreads, 0, s>>>(R, label, g->n, skip, Q, S, packed);
+    k_cc_close<<<1, 1, 0, s>>>(packed, S);
+    k_cc_hook_rest<<<g->num_sms * 4, kCcThreads, 0, s>>>(R, C, g->n, label, Q, S, packed);
+  }
   k_cc_jump<<<grid, 256, 0, s>>>(label, g->n, cnt);
   GR_CUDA(cudaGetLastError());
   return GR_OK;
