@@ -41,10 +41,14 @@ constexpr int kMbThreads = 256, kMbItems = 4;
 // writes their depths in one pass (k_mb_depth); deeper levels write depths
 // as they are reached.
 constexpr int32_t kKeepLevels = 64;
+// A batched BFS level pushes when its frontier has fewer than m / kPushDiv
+// edges, and pulls over every vertex otherwise.
+constexpr long long kPushDiv = 16;
 constexpr int kMbChunk = kMbThreads * kMbItems;
 
 struct BatchWorkspace {
   DevMem visit, sigma, q, counter, srcs, lmp;
+  DevMem fq, fs;  // frontier list and degree scan of the push levels
   std::vector<DevMem *> lm;  // lm[L]: lane masks of level L
   ~BatchWorkspace() {
     for (DevMem *p : lm) delete p;
@@ -70,8 +74,13 @@ struct MbArgs {
   int32_t *depth;                 // [k][n] or null (BC)
   int32_t k;
   int32_t level;
-  unsigned long long *count;      // vertices that joined lm[L+1]
+  unsigned long long *count;      // [31:0] vertices that joined lm[L+1], [63:32] their edges
 };
+
+// Packed (vertices, edges) increment for a vertex that joined the next level.
+__device__ __forceinline__ unsigned long long joined(const MbArgs &a, int32_t v) {
+  return 1ull | ((unsigned long long)(uint32_t)(a.R[v + 1] - a.R[v]) << 32);
+}
 
 __device__ __forceinline__ unsigned long long shfl_u64(unsigned long long x, int src) {
   return __shfl_sync(0xffffffffu, x, src);
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
         const int32_t prev = __shfl_up_sync(0xffffffffu, owner, 1);
         if (owner >= 0 && (lane == 0 || prev != owner) && acc) {
           const unsigned long long old = atomicOr(a.nxt + owner, acc);
-          if (!old) ++new_vertices;
+          if (!old) new_vertices += joined(a, owner);
         }
       } else {
         // the warp serves the edges with bits one at a time: lane l handles
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
               if ((orbits >> (lane + 32)) & 1ull) atomicAdd(sg + lane + 32, acc1);
               if (lane == 0) {
                 const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
-                if (!old) ++new_vertices;
+                if (!old) new_vertices += joined(a, cur_owner);
               }
             }
             cur_owner = ov;
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
           if ((orbits >> (lane + 32)) & 1ull) atomicAdd(sg + lane + 32, acc1);
           if (lane == 0) {
             const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
-            if (!old) ++new_vertices;
+            if (!old) new_vertices += joined(a, cur_owner);
           }
         }
       }
@@ -225,7 +234,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
     __syncthreads();
   }
   // new_vertices counts runs whose atomicOr found an empty mask: exactly the
-  // vertices that joined lm[L+1]
+  // vertices that joined lm[L+1] (and their edges)
   for (int o = 16; o > 0; o >>= 1) new_vertices += __shfl_xor_sync(0xffffffffu, new_vertices, o);
   if (lane == 0 && new_vertices) atomicAdd(a.count, new_vertices);
 }
@@ -343,6 +352,109 @@ __global__ void k_bc_finalize(const unsigned long long *lv, const double *sigma,
   }
 }
 
+// Push form of a batched BFS level, for frontiers with few edges (the
+// sources' level and the last levels): instead of every vertex pulling from
+// all its neighbours, the frontier's vertices push their lanes.
+// k_mb_compact lists the frontier (vertices with lanes in lm[L]) with its
+// degree scan, folds lm[L] into visit (the pull's vertex loader does that)
+// and, past the kept levels, writes the level's depths; k_mb_push sends, over
+// every edge (u, v) of the frontier, u's lanes that v has not seen to v's
+// mask in lm[L+1] (merge-path chunks over the listed vertices' edges).
+__global__ void __launch_bounds__(kMbThreads) k_mb_compact(MbArgs a, int32_t *Q, int32_t *S,
+                                                            unsigned long long *fpacked) {
+  __shared__ ScannedBuf<kMbChunk> buf;
+  if (threadIdx.x == 0) buf.cnt = 0;
+  __syncthreads();
+  constexpr int PER = kMbChunk / kMbThreads;
+  for (int64_t base = (int64_t)blockIdx.x * kMbChunk; base < a.n;
+       base += (int64_t)gridDim.x * kMbChunk) {  // block-uniform
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int64_t v = base + j * kMbThreads + threadIdx.x;
+      int32_t d = 0;
+      bool take = false;
+      if (v < a.n) {
+        const unsigned long long c = a.cur[v];
+        if (c) {
+          a.visit[v] |= c;
+          if (a.depth) {
+            for (int s = 0; s < a.k; ++s)
+              if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 206))
+                a.depth[(int64_t)s * a.n + v] = a.level;
+          }
+          d = a.R[v + 1] - a.R[v];
+          take = d > 0;
+        }
+      }
+      emit_scanned(buf, take, (int32_t)v, d);
+    }
+    flush_scanned<kMbThreads>(buf, fpacked, Q, S, (long long)a.n + 1);
+  }
+}
+
+__global__ void k_mb_close(const unsigned long long *fpacked, int32_t *S) {
+  const unsigned long long p = *fpacked;
+  S[(int32_t)(p & 0xFFFFFFFFull)] = (int32_t)(p >> 32);
+}
+
+__global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t *Q,
+                                                         const int32_t *S,
+                                                         const unsigned long long *fpacked) {
+  __shared__ int32_t s_off[kMbChunk + 1];
+  __shared__ int32_t s_row[kMbChunk + 1];
+  __shared__ unsigned long long s_cur[kMbChunk + 1];
+  __shared__ int32_t s_red8[kMbThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long fp = *fpacked;
+  const int32_t q = (int32_t)(fp & 0xFFFFFFFFull);
+  const int32_t qe = (int32_t)(fp >> 32);
+  const long long total = (long long)q + qe;
+  const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
+  unsigned long long added = 0;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * kMbChunk;
+    const long long d1 = min(d0 + kMbChunk, total);
+    int32_t i0, i1;
+    block_chunk_bounds<kMbThreads>(S, q, qe, d0, d1, kMbChunk, s_red8, &i0, &i1);
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += kMbThreads) {
+      const int32_t i = i0 + k;
+      const int32_t u = GR_IN(i, a.n + 1, 207) ? Q[i] : 0;
+      const bool ok = GR_IN(u, a.n, 208);
+      s_off[k] = (i == q) ? qe : S[i];
+      s_row[k] = ok ? a.R[u] : 0;
+      s_cur[k] = ok ? a.cur[u] : 0ull;
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
+      const int32_t k = kb + threadIdx.x;
+      if (k < ne) {
+        const int32_t er = (int32_t)(j0 + k);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= er) lo = mid;
+          else hi = mid - 1;
+        }
+        const long long e = (long long)s_row[lo] + (er - s_off[lo]);
+        const int32_t v = GR_IN(e, a.m, 209) ? a.C[e] : -1;
+        if (v >= 0 && GR_IN(v, a.n, 210)) {
+          const unsigned long long bits = s_cur[lo] & ~a.visit[v];
+          if (bits) {
+            const unsigned long long old = atomicOr(a.nxt + v, bits);
+            if (!old) added += joined(a, v);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) added += __shfl_xor_sync(0xffffffffu, added, o);
+  if (lane == 0 && added) atomicAdd(a.count, added);
+}
+
 // Depths of a batched BFS from its per-level lane masks, written once, in
 // full coalesced rows: for each lane s, depth[s][v] = the level L whose mask
 // lm[L][v] holds bit s (-1 if none). The masks of one vertex are disjoint,
@@ -384,8 +496,8 @@ __global__ void k_fill_f64(double *x, int64_t n, double val) {
 }  // namespace
 
 size_t batch_ws_bytes(const gr_graph *g) {
-  // visit masks + the two level masks batched BFS alternates
-  return 3 * sizeof(unsigned long long) * (size_t)g->n + 512;
+  // visit masks, the level masks of a typical traversal, the push frontier
+  return 12 * sizeof(unsigned long long) * (size_t)g->n + 512;
 }
 
 gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out) {
@@ -456,6 +568,13 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     return (size_t)(kKeepLevels + ((lvl - kKeepLevels) & 1));
   };
   bool depth_pass_done = false;
+  // level 0 (the sources) pushes; later levels choose by frontier edges
+  bool push = !with_sigma;
+  unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
+  if (push && !ws->fq.p) {
+    GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "batch push frontier"));
+    GR_TRY(ws->fs.alloc(sizeof(int32_t) * ((size_t)g->n + 2), "batch push frontier scan"));
+  }
   auto depth_pass = [&](int32_t levels) -> gr_status {
     std::vector<unsigned long long *> ptrs(kKeepLevels, nullptr);
     for (int32_t i = 0; i < levels; ++i) ptrs[i] = ws->lm[i]->as<unsigned long long>();
@@ -476,17 +595,27 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     a.level = L;
     a.depth = (depth && L >= kKeepLevels) ? depth : nullptr;
     GR_CUDA(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
-    if (with_sigma)
+    if (with_sigma) {
       k_mb_forward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
-    else
+    } else if (push) {
+      int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
+      GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
+      k_mb_compact<<<grid, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+      k_mb_close<<<1, 1, 0, s>>>(fpacked, fs);
+      k_mb_push<<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+    } else {
       k_mb_forward<false><<<g->num_sms * 8, kMbThreads, 0, s>>>(a);
+    }
     GR_CUDA(cudaGetLastError());
     unsigned long long cnt = 0;
     GR_CUDA(cudaMemcpyAsync(&cnt, a.count, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     GR_CUDA(cudaStreamSynchronize(s));
     ++L;
-    if (cnt == 0) break;  // level L is empty; levels 0..L-1 hold vertices
+    const uint32_t joined_vertices = (uint32_t)(cnt & 0xFFFFFFFFull);
+    const long long joined_edges = (long long)(cnt >> 32);
+    if (joined_vertices == 0) break;  // level L is empty; levels 0..L-1 hold vertices
     if (L >= max_levels) return fail(GR_ETIMEOUT, "level limit reached");
+    push = !with_sigma && joined_edges * kPushDiv < g->m;
   }
   if (depth && !depth_pass_done) GR_TRY(depth_pass(L));
   *levels_out = L;
