@@ -243,6 +243,7 @@ struct BcBackArgs {
   const int32_t *R;
   const int32_t *C;
   int32_t n;
+  long long m;
   const unsigned long long *lv;   // lm[L]
   const unsigned long long *lw;   // lm[L+1]
   double *q;                      // [n][64]
@@ -250,43 +251,59 @@ struct BcBackArgs {
 
 // Backward level L: q[v][s] += q[w][s] over edges (v, w) with v in lane s's
 // level L and w in its level L+1 (w's q is final: level L+1 was finished).
-__global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a) {
+// Only the vertices of level L (listed with their degrees by k_mb_list) are
+// visited, so the whole backward pass reads every edge about once instead of
+// once per level.
+__global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const int32_t *Q,
+                                                             const int32_t *S,
+                                                             const unsigned long long *fpacked) {
   __shared__ int32_t s_off[kMbChunk + 1];
+  __shared__ int32_t s_row[kMbChunk + 1];
+  __shared__ int32_t s_v[kMbChunk + 1];
   __shared__ unsigned long long s_A[kMbChunk + 1];
   __shared__ int32_t s_red8[kMbThreads / 32];
   const int lane = threadIdx.x & 31;
-  const long long total = (long long)a.n + a.R[a.n];
+  const unsigned long long fp = *fpacked;
+  const int32_t q = (int32_t)(fp & 0xFFFFFFFFull);
+  const int32_t qe = (int32_t)(fp >> 32);
+  const long long total = (long long)q + qe;
   const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kMbChunk;
     const long long d1 = min(d0 + kMbChunk, total);
     int32_t i0, i1;
-    block_chunk_bounds<kMbThreads>(a.R, a.n, a.R[a.n], d0, d1, kMbChunk, s_red8, &i0, &i1);
+    block_chunk_bounds<kMbThreads>(S, q, qe, d0, d1, kMbChunk, s_red8, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
-    const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
-    for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
-      s_off[kk] = a.R[i0 + kk];
-      s_A[kk] = a.lv[i0 + kk];
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += kMbThreads) {
+      const int32_t i = i0 + k;
+      const int32_t v = GR_IN(i, a.n + 1, 220) ? Q[i] : 0;
+      const bool ok = GR_IN(v, a.n, 221);
+      s_off[k] = S[i];
+      s_v[k] = ok ? v : -1;
+      s_row[k] = ok ? a.R[v] : 0;
+      s_A[k] = ok ? a.lv[v] : 0ull;
     }
     __syncthreads();
     const int32_t ne = (int32_t)(j1 - j0);
     for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
-      const int32_t kk = kb + threadIdx.x;
+      const int32_t k = kb + threadIdx.x;
       int32_t owner = -1, w = 0;
       unsigned long long bits = 0ull;
-      if (kk < ne) {
-        const int32_t e = (int32_t)(j0 + kk);
+      if (k < ne) {
+        const int32_t er = (int32_t)(j0 + k);
         int32_t lo = 0, hi = nv - 1;
         while (lo < hi) {
           const int32_t mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= e) lo = mid;
+          if (s_off[mid] <= er) lo = mid;
           else hi = mid - 1;
         }
-        owner = i0 + lo;
+        owner = s_v[lo];
+        const long long e = (long long)s_row[lo] + (er - s_off[lo]);
         const unsigned long long A = s_A[lo];
-        if (A) {
+        if (owner >= 0 && A && GR_IN(e, a.m, 222)) {
           w = a.C[e];
-          bits = A & a.lw[w];
+          bits = GR_IN(w, a.n, 223) ? (A & a.lw[w]) : 0ull;
         }
       }
       uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
@@ -321,6 +338,33 @@ __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a) {
       }
     }
     __syncthreads();
+  }
+}
+
+// The vertices with lanes in `lv` and at least one edge, with their degree
+// scan (block-wise compaction, one packed atomic per block).
+__global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long *lv,
+                                                         const int32_t *R, int32_t n,
+                                                         int32_t *Q, int32_t *S,
+                                                         unsigned long long *fpacked) {
+  __shared__ ScannedBuf<kMbChunk> buf;
+  if (threadIdx.x == 0) buf.cnt = 0;
+  __syncthreads();
+  constexpr int PER = kMbChunk / kMbThreads;
+  for (int64_t base = (int64_t)blockIdx.x * kMbChunk; base < n;
+       base += (int64_t)gridDim.x * kMbChunk) {  // block-uniform
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int64_t v = base + j * kMbThreads + threadIdx.x;
+      int32_t d = 0;
+      bool take = false;
+      if (v < n && lv[v]) {
+        d = R[v + 1] - R[v];
+        take = d > 0;
+      }
+      emit_scanned(buf, take, (int32_t)v, d);
+    }
+    flush_scanned<kMbThreads>(buf, fpacked, Q, S, (long long)n + 1);
   }
 }
 
@@ -397,12 +441,17 @@ __global__ void k_mb_close(const unsigned long long *fpacked, int32_t *S) {
   S[(int32_t)(p & 0xFFFFFFFFull)] = (int32_t)(p >> 32);
 }
 
+// With SIGMA (BC's forward pass) the lanes newly sent to v also add u's path
+// counts to v's: the warp serves such edges one at a time, lane l adding
+// lanes l and l + 32.
+template <bool SIGMA>
 __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t *Q,
                                                          const int32_t *S,
                                                          const unsigned long long *fpacked) {
   __shared__ int32_t s_off[kMbChunk + 1];
   __shared__ int32_t s_row[kMbChunk + 1];
   __shared__ unsigned long long s_cur[kMbChunk + 1];
+  __shared__ int32_t s_u[SIGMA ? kMbChunk + 1 : 1];
   __shared__ int32_t s_red8[kMbThreads / 32];
   const int lane = threadIdx.x & 31;
   const unsigned long long fp = *fpacked;
@@ -425,11 +474,14 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t 
       s_off[k] = (i == q) ? qe : S[i];
       s_row[k] = ok ? a.R[u] : 0;
       s_cur[k] = ok ? a.cur[u] : 0ull;
+      if (SIGMA) s_u[k] = ok ? u : 0;
     }
     __syncthreads();
     const int32_t ne = (int32_t)(j1 - j0);
     for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
       const int32_t k = kb + threadIdx.x;
+      unsigned long long bits = 0ull;
+      int32_t v = -1, u = 0;
       if (k < ne) {
         const int32_t er = (int32_t)(j0 + k);
         int32_t lo = 0, hi = nv - 1;
@@ -439,13 +491,28 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t 
           else hi = mid - 1;
         }
         const long long e = (long long)s_row[lo] + (er - s_off[lo]);
-        const int32_t v = GR_IN(e, a.m, 209) ? a.C[e] : -1;
+        v = GR_IN(e, a.m, 209) ? a.C[e] : -1;
         if (v >= 0 && GR_IN(v, a.n, 210)) {
-          const unsigned long long bits = s_cur[lo] & ~a.visit[v];
+          bits = s_cur[lo] & ~a.visit[v];
           if (bits) {
             const unsigned long long old = atomicOr(a.nxt + v, bits);
             if (!old) added += joined(a, v);
           }
+          if (SIGMA) u = s_u[lo];
+        }
+      }
+      if (SIGMA) {
+        uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
+        while (act) {
+          const int j = __ffs(act) - 1;
+          act &= act - 1u;
+          const int32_t vj = __shfl_sync(0xffffffffu, v, j);
+          const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+          const unsigned long long bj = shfl_u64(bits, j);
+          const double *su = a.sigma + (int64_t)uj * 64;
+          double *sv = a.sigma + (int64_t)vj * 64;
+          if ((bj >> lane) & 1ull) atomicAdd(sv + lane, su[lane]);
+          if ((bj >> (lane + 32)) & 1ull) atomicAdd(sv + lane + 32, su[lane + 32]);
         }
       }
     }
@@ -517,6 +584,10 @@ static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_b
     GR_TRY(ws->sigma.alloc(sizeof(double) * 64 * (size_t)g->n, "BC path counts"));
     GR_TRY(ws->q.alloc(sizeof(double) * 64 * (size_t)g->n, "BC dependencies"));
   }
+  if (need_bc && !ws->fq.p) {
+    GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "BC level list"));
+    GR_TRY(ws->fs.alloc(sizeof(int32_t) * ((size_t)g->n + 2), "BC level list scan"));
+  }
   return GR_OK;
 }
 
@@ -569,9 +640,9 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
   };
   bool depth_pass_done = false;
   // level 0 (the sources) pushes; later levels choose by frontier edges
-  bool push = !with_sigma;
+  bool push = true;
   unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
-  if (push && !ws->fq.p) {
+  if (!ws->fq.p) {
     GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "batch push frontier"));
     GR_TRY(ws->fs.alloc(sizeof(int32_t) * ((size_t)g->n + 2), "batch push frontier scan"));
   }
@@ -595,14 +666,17 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     a.level = L;
     a.depth = (depth && L >= kKeepLevels) ? depth : nullptr;
     GR_CUDA(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
-    if (with_sigma) {
-      k_mb_forward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
-    } else if (push) {
+    if (push) {
       int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
       GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
       k_mb_compact<<<grid, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
       k_mb_close<<<1, 1, 0, s>>>(fpacked, fs);
-      k_mb_push<<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+      if (with_sigma)
+        k_mb_push<true><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+      else
+        k_mb_push<false><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+    } else if (with_sigma) {
+      k_mb_forward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
     } else {
       k_mb_forward<false><<<g->num_sms * 8, kMbThreads, 0, s>>>(a);
     }
@@ -615,7 +689,7 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     const long long joined_edges = (long long)(cnt >> 32);
     if (joined_vertices == 0) break;  // level L is empty; levels 0..L-1 hold vertices
     if (L >= max_levels) return fail(GR_ETIMEOUT, "level limit reached");
-    push = !with_sigma && joined_edges * kPushDiv < g->m;
+    push = joined_edges * kPushDiv < g->m;
   }
   if (depth && !depth_pass_done) GR_TRY(depth_pass(L));
   *levels_out = L;
@@ -691,12 +765,17 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     ba.R = g->row_off.as<int32_t>();
     ba.C = g->col.as<int32_t>();
     ba.n = g->n;
+    ba.m = g->m;
     ba.q = ws->q.as<double>();
+    unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
+    int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
     for (int32_t L = levels - 1; L >= 1; --L) {
       if (L + 1 < levels) {
         ba.lv = ws->lm[L]->as<unsigned long long>();
         ba.lw = ws->lm[L + 1]->as<unsigned long long>();
-        k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba);
+        GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
+        k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
+        k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
       }
       k_bc_finalize<<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
                                          ws->sigma.as<double>(), ws->q.as<double>(),
