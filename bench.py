@@ -33,6 +33,32 @@ WORKLOAD = "rmat22_bfs"
 METRIC = "BFS GTEPS (R-MAT s22, 16 sources)"
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM traffic of one traversal (k_bfs_init + k_bfs_do), from one ncu capture
+# of the 16 timed traversals at R-MAT s21 (cold caches; the command and the
+# numbers are in profiles/k_bfs_do_rmat21_full.md), scaled to other scales by
+# the edge count. It is reported only while the traversal's sources hash to
+# the value they had when it was measured (null after any change).
+TRAFFIC_S21 = {"bytes_per_traversal": 65833072, "m": 63540402,
+               "sources_sha256": "b2b34d617844219241b097054256ece2668ebd325406185ff675edec3f21b778"}
+TRAFFIC_SOURCES = ("paper_1501_05387_gb300/csrc/bfs.cu", "paper_1501_05387_gb300/csrc/advance.cuh",
+                   "paper_1501_05387_gb300/csrc/gr_internal.cuh")
+
+
+def traversal_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(m):
+    t = TRAFFIC_S21
+    if t["bytes_per_traversal"] is None or t["sources_sha256"] != traversal_sources_sha256():
+        return None
+    return t["bytes_per_traversal"] * m / t["m"]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -617,7 +643,9 @@ def run_gr(args):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "frac_of_nominal_8TBs": achieved / 8000.0,
                 "algorithmic_bytes_per_launch": float(np.mean(bytes_per_bfs)),
-                "traffic": None}
+                "traffic": measured_traffic(m),
+                "traffic_source": "ncu dram bytes of k_bfs_init + k_bfs_do at R-MAT s21, "
+                                  "16 traversals, scaled by the edge count"}
 
     # end to end: the same traversals through the C ABI with host outputs
     e2e_times = [float("nan")]

@@ -65,6 +65,9 @@ struct BfsCtl {
   // persistent kernel: next-frontier counters, a ring of three so that one
   // can be cleared while the others are in use
   unsigned long long cnt3[3];
+  // persistent kernel: largest degree a pull level found, by level (ring)
+  int32_t maxdeg3[3];
+  int32_t pad3_;
   unsigned long long next_packed;  // [31:0] next frontier size, [63:32] its edges
   long long mf;         // edges leaving the current frontier
   long long mu;         // edges of still-unexplored vertices
@@ -201,7 +204,10 @@ __global__ void k_bfs_init(BfsArgs a, int32_t src, int32_t *depth, int32_t *pare
     c->alpha = alpha;
     c->beta = beta;
     c->from_bitmap = 0;
-    for (int i = 0; i < 3; ++i) c->cnt3[i] = 0ull;
+    for (int i = 0; i < 3; ++i) {
+      c->cnt3[i] = 0ull;
+      c->maxdeg3[i] = 0;
+    }
     c->t_start = globaltimer();
   }
 }
@@ -281,10 +287,12 @@ __device__ void flush(LevelSmem &sm, unsigned long long *counter, int32_t *Qn, i
   __syncthreads();
 }
 
-__device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p, int32_t L,
-                           int32_t q, int32_t q_edges, unsigned long long *counter) {
-  const int32_t *Q = queue_of(a, p);
-  const int32_t *S = scan_of(a, p);
+// Push over the frontier Q[0..q) with its exclusive degree scan S (S[q] =
+// q_edges); this block takes chunks chunk0, chunk0 + step, ... of the merge
+// path. The next frontier goes to the queue of parity p ^ 1.
+__device__ void push_range(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, const int32_t *Q,
+                           const int32_t *S, int32_t p, int32_t L, int32_t q, int32_t q_edges,
+                           unsigned long long *counter, long long chunk0, long long step) {
   int32_t *Qn = queue_of(a, p ^ 1);
   int32_t *Sn = scan_of(a, p ^ 1);
   uint32_t *N = bits_of(a, L + 1);
@@ -292,7 +300,7 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
   int32_t *parent = c->parent;
   const long long total = (long long)q + q_edges;
   const long long nchunks = (total + kLvChunk - 1) / kLvChunk;
-  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+  for (long long chunk = chunk0; chunk < nchunks; chunk += step) {
     const long long d0 = chunk * kLvChunk;
     const long long d1 = min(d0 + kLvChunk, total);
     int32_t i0, i1;
@@ -357,6 +365,13 @@ __device__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p
     for (int j = 0; j < kLvItems; ++j) emit(sm, won[j], v[j], dv[j]);
     flush(sm, counter, Qn, Sn, a.n + 1);
   }
+}
+
+__device__ __forceinline__ void push_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm,
+                                           int32_t p, int32_t L, int32_t q, int32_t q_edges,
+                                           unsigned long long *counter) {
+  push_range(a, c, sm, queue_of(a, p), scan_of(a, p), p, L, q, q_edges, counter, blockIdx.x,
+             gridDim.x);
 }
 
 // Push level for graphs of small maximum degree (meshes): one thread per
@@ -450,7 +465,7 @@ __device__ void push_level_thread(const BfsArgs &a, BfsCtl *c, int32_t p, int32_
 constexpr int kPullWords = 2;
 
 __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L,
-                           unsigned long long *counter) {
+                           unsigned long long *counter, int32_t *maxdeg = nullptr) {
   const uint32_t *F = bits_of(a, L);
   uint32_t *N = bits_of(a, L + 1);
   int32_t *depth = c->depth;
@@ -461,6 +476,7 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
   const long long groups = (a.nwords + kPullWords - 1) / kPullWords;
   uint32_t found_cnt = 0;
   unsigned long long found_deg = 0;
+  uint32_t found_max = 0;
   for (long long gi = gw; gi < groups; gi += nw) {  // warp-uniform loop
     const long long w0 = gi * kPullWords;
     uint32_t vis[kPullWords];
@@ -544,6 +560,7 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
         if (parent) parent[v[j]] = uf[j];
         ++found_cnt;
         found_deg += (unsigned long long)(r1[j] - r0[j]);
+        found_max = max(found_max, (uint32_t)(r1[j] - r0[j]));
       }
       if (a.seg_v && fm) {  // append to this block's segment (shared-memory slot)
         int32_t pos = 0;
@@ -559,6 +576,10 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
         }
       }
     }
+  }
+  if (maxdeg) {
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, found_max);
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(maxdeg, (int32_t)wmax);
   }
   // one packed atomicAdd per block: [31:0] vertices, [63:32] their edges
   const unsigned long long packed =
@@ -615,6 +636,42 @@ __device__ void segments_to_queue(const BfsArgs &a, LevelSmem &sm, int32_t *Q, i
     }
     eo += tile_total;
   }
+}
+
+// The level after a pull whose vertices all have small degree: every block
+// pushes the vertices it found itself (its pull segment), after an in-place
+// exclusive scan of their degrees, so the level needs no grid-wide
+// compaction and no extra grid barrier. Blocks carry unequal work, bounded by
+// the segment sizes and the small degrees.
+__device__ void push_own_segment(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t p,
+                                 int32_t L, unsigned long long *counter) {
+  const unsigned long long pk = a.seg_cnt[blockIdx.x];
+  const int32_t cb = (int32_t)(pk & 0xFFFFFFFFull), eb = (int32_t)(pk >> 32);
+  const int64_t base = (int64_t)blockIdx.x * a.seg_cap;
+  int32_t *V = a.seg_v + base;
+  int32_t *D = a.seg_d + base;
+  constexpr int PER = kLvChunk / kLvThreads;
+  uint32_t run_base = 0;
+  for (int32_t t0 = 0; t0 < cb; t0 += kLvChunk) {  // block-uniform
+    const int32_t k0 = t0 + threadIdx.x * PER;
+    int32_t dd[PER];
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      dd[j] = (k0 + j < cb && GR_IN(k0 + j, a.seg_cap, 180)) ? D[k0 + j] : 0;
+      local += (uint32_t)dd[j];
+    }
+    uint32_t tile_total;
+    uint32_t run = run_base + block_excl_sum(local, sm.red, &tile_total);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      if (k0 + j < cb && GR_IN(k0 + j, a.seg_cap, 181)) D[k0 + j] = (int32_t)run;
+      run += (uint32_t)dd[j];
+    }
+    run_base += tile_total;
+  }
+  __syncthreads();
+  push_range(a, c, sm, V, D, p, L, cb, eb, counter, 0, 1);
 }
 
 // Push level whose frontier exists only as a bitmap (the level after a
@@ -784,6 +841,9 @@ __global__ void __launch_bounds__(kLvThreads, kLvBlocksPerSm)
 __device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t &gen);
 
 constexpr int kDoBlocksPerSm = 5;
+// After a pull level whose found vertices all have at most this degree, each
+// block pushes its own pull segment (no grid-wide compaction).
+constexpr int32_t kSegPushMaxDeg = 1024;
 
 __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a) {
   BfsCtl *c = a.ctl;
@@ -793,12 +853,14 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
   int32_t level = 0, parity = 0, dir = kPush, q = 1, q_prev = 0, from_bitmap = 0;
   long long mf = c->mf, mu = c->mu;
   int32_t gen = 0, pulls = 0;
+  int32_t seg_maxdeg = 0;  // largest degree the last pull level found
   if (threadIdx.x == 0) sm.cnt = 0;
   __syncthreads();
   for (;;) {
     const int32_t L = level;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       c->cnt3[(L + 1) % 3] = 0ull;
+      c->maxdeg3[(L + 1) % 3] = 0;
     }
     if (a.do_bitmap) {
       uint32_t *spare = bits_of(a, L + 2);
@@ -810,7 +872,9 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
     if (threadIdx.x == 0) sm.segcnt = 0;
     __syncthreads();
     if (dir == kPull) {
-      pull_level(a, c, sm, L, counter);
+      pull_level(a, c, sm, L, counter, &c->maxdeg3[L % 3]);
+    } else if (from_bitmap && seg_maxdeg <= kSegPushMaxDeg) {
+      push_own_segment(a, c, sm, parity, L, counter);
     } else {
       int32_t qq = q, qe = (int32_t)mf;
       if (from_bitmap) {
@@ -822,6 +886,7 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
     }
     if (!grid_barrier(c, gridDim.x, gen)) break;
     const unsigned long long pk = *(volatile unsigned long long *)counter;
+    seg_maxdeg = dir == kPull ? *(volatile int32_t *)&c->maxdeg3[L % 3] : 0;
     const int32_t qn = (int32_t)(pk & 0xFFFFFFFFull);
     const long long mfn = (long long)(pk >> 32);
     const bool was_pull = dir == kPull;
