@@ -98,6 +98,7 @@ struct BfsArgs {
   int32_t nwords;
   long long m;
   const uint32_t *iso;
+  const int32_t *first;  // first neighbour per vertex (-1: none); pull levels test it first
   int32_t *q[2];
   int32_t *S[2];        // exclusive degree scan of q[p], S[p][q_len] = edges
   uint32_t *visited;
@@ -492,18 +493,25 @@ __device__ void pull_level(const BfsArgs &a, BfsCtl *c, LevelSmem &sm, int32_t L
       uf[j] = -1;
       r0[j] = r1[j] = 0;
     }
-#pragma unroll
-    for (int j = 0; j < kPullWords; ++j)
-      if (act[j]) {
-        r0[j] = a.R[v[j]];
-        r1[j] = a.R[v[j] + 1];
-        if (!GR_IN(r0[j], a.m + 1, 120) || !GR_IN(r1[j], a.m + 1, 121)) r1[j] = r0[j] = 0;
-      }
-    // first neighbour of every vertex, independent loads
+    // row bounds and the first neighbour (from the dense first-neighbour
+    // array: coalesced, and not waiting for the row offset) of every
+    // unvisited vertex, independent loads
     int32_t u1[kPullWords];
 #pragma unroll
     for (int j = 0; j < kPullWords; ++j) {
-      u1[j] = (act[j] && r0[j] < r1[j]) ? a.C[r0[j]] : -1;
+      u1[j] = -1;
+      if (act[j]) {
+        r0[j] = a.R[v[j]];
+        r1[j] = a.R[v[j] + 1];
+        u1[j] = a.first[v[j]];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j) {
+      if (!GR_IN(r0[j], a.m + 1, 120) || !GR_IN(r1[j], a.m + 1, 121)) {
+        r1[j] = r0[j] = 0;
+        u1[j] = -1;
+      }
       if (u1[j] >= 0 && !GR_IN(u1[j], a.n, 122)) u1[j] = -1;
     }
 #pragma unroll
@@ -1048,6 +1056,7 @@ static BfsArgs make_args(gr_graph *g, BfsWorkspace *ws, int32_t do_bitmap) {
   a.nwords = g->nwords;
   a.m = g->m;
   a.iso = g->isolated_bits.as<uint32_t>();
+  a.first = g->first_col.as<int32_t>();
   for (int i = 0; i < 2; ++i) {
     a.q[i] = ws->q[i].as<int32_t>();
     a.S[i] = ws->S[i].as<int32_t>();

@@ -90,6 +90,7 @@ struct gr_graph {
   int32_t nwords = 0;  // ceil(n / 32): words of one vertex bitmap
   gr::DevMem row_off, col, w;
   gr::DevMem isolated_bits;  // bit v set iff deg(v) == 0
+  gr::DevMem first_col;      // first neighbour of v (C[R[v]]), -1 if deg(v) == 0
   gr::DevMem degree;         // int32 deg(v), used by PageRank
   int32_t max_degree = 0;
   int32_t num_isolated = 0;

@@ -123,6 +123,16 @@ __global__ void k_validate_csr(const int32_t *R, const int32_t *C, int32_t n,
   }
 }
 
+// first neighbour of every vertex, stored densely: the bottom-up (pull)
+// BFS level tests it first and reads it with coalesced loads
+__global__ void k_first_col(const int32_t *R, const int32_t *C, int32_t n, int32_t *first) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r0 = R[v];
+    first[v] = R[v + 1] > r0 ? C[r0] : -1;
+  }
+}
+
 // degree statistics + isolated-vertex bitmap, one warp per 32 vertices
 __global__ void k_graph_stats(const int32_t *R, int32_t n, int32_t nwords,
                               uint32_t *iso_bits, int32_t *deg_out,
@@ -300,6 +310,10 @@ gr_status gr_graph_create(int32_t n, int64_t m, const int32_t *row_off,
                                      g->degree.as<int32_t>(), f + 1, f + 2);
   GR_CUDA(cudaGetLastError());
   k_rows_sorted<<<grid, 256, 0, s>>>(g->row_off.as<int32_t>(), g->col.as<int32_t>(), n, f + 3);
+  GR_CUDA(cudaGetLastError());
+  GR_TRY(g->first_col.alloc(sizeof(int32_t) * (size_t)n, "first neighbours"));
+  k_first_col<<<grid, 256, 0, s>>>(g->row_off.as<int32_t>(), g->col.as<int32_t>(), n,
+                                   g->first_col.as<int32_t>());
   GR_CUDA(cudaGetLastError());
   GR_CUDA(cudaMemcpyAsync(hf, f, sizeof(hf), cudaMemcpyDeviceToHost, s));
   GR_CUDA(cudaStreamSynchronize(s));
