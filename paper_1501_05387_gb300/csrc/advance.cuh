@@ -17,141 +17,7 @@
 
 namespace gr {
 
-// ------------------------------------------------------------------ scan
-// Decoupled look-back status word of a scan tile:
-// [63:34] epoch tag, [33:32] flag (1 aggregate, 2 inclusive prefix),
-// [31:0] value. The epoch changes on every scan, so the status array never
-// needs clearing.
-constexpr unsigned long long kScanFlagAgg = 1ull, kScanFlagPrefix = 2ull;
-
-struct ScanState {
-  unsigned long long *status;  // one word per tile
-  int32_t *tile_ctr;           // dynamic tile counter, zero before the scan
-  int32_t *error;              // set to kDevTimeout if a look-back gives up
-  uint32_t epoch;
-};
-
-__device__ __forceinline__ void scan_publish(unsigned long long *st, int32_t tile,
-                                             uint32_t epoch, unsigned long long flag,
-                                             uint32_t val) {
-  unsigned long long w =
-      ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | (flag << 32) | val;
-  atomicExch(st + tile, w);
-}
-
-__device__ __forceinline__ uint32_t scan_look_back(const ScanState &s, int32_t tile) {
-  uint32_t excl = 0;
-  int32_t j = tile - 1;
-  int64_t spins = 0;
-  const unsigned long long tag = s.epoch & 0x3FFFFFFFu;
-  while (j >= 0) {
-    unsigned long long w = *(volatile unsigned long long *)(s.status + j);
-    unsigned long long flag = (w >> 32) & 3ull;
-    if ((w >> 34) != tag || flag == 0) {
-      if (++spins > kSpinLimit) {
-        atomicExch(s.error, kDevTimeout);
-        return excl;
-      }
-      continue;
-    }
-    excl += (uint32_t)w;
-    if (flag == kScanFlagPrefix) break;
-    --j;
-  }
-  return excl;
-}
-
-// Exclusive scan of deg(Q[i]) into S[0..q], S[q] = total, by every block of
-// the grid (tiles taken in order from a counter; blocks wait only on earlier
-// tiles, which are held by running blocks). Returns true, on thread 0 of the
-// block that scanned the last tile, with *total set.
-template <int THREADS, int ITEMS>
-__device__ bool frontier_degree_scan(const int32_t *R, const int32_t *Q, int32_t q,
-                                     int32_t *S, const ScanState &st, long long *total) {
-  constexpr int TILE = THREADS * ITEMS;
-  const int32_t ntiles = (q + TILE - 1) / TILE;
-  __shared__ int32_t s_tile;
-  __shared__ uint32_t s_excl;
-  __shared__ uint32_t s_red[33];
-  bool last = false;
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(st.tile_ctr, 1);
-    __syncthreads();
-    const int32_t tile = s_tile;
-    __syncthreads();
-    if (tile >= ntiles) break;
-    const int64_t base = (int64_t)tile * TILE + threadIdx.x * ITEMS;
-    uint32_t deg[ITEMS];
-    uint32_t local = 0;
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const int64_t i = base + k;
-      uint32_t d = 0;
-      if (i < q) {
-        const int32_t u = Q[i];
-        d = (uint32_t)(R[u + 1] - R[u]);
-      }
-      deg[k] = d;
-      local += d;
-    }
-    uint32_t agg;
-    const uint32_t texcl = block_excl_sum(local, s_red, &agg);
-    if (threadIdx.x == 0) {
-      uint32_t excl = 0;
-      if (tile == 0) {
-        scan_publish(st.status, tile, st.epoch, kScanFlagPrefix, agg);
-      } else {
-        scan_publish(st.status, tile, st.epoch, kScanFlagAgg, agg);
-        excl = scan_look_back(st, tile);
-        scan_publish(st.status, tile, st.epoch, kScanFlagPrefix, excl + agg);
-      }
-      s_excl = excl;
-    }
-    __syncthreads();
-    uint32_t run = s_excl + texcl;
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const int64_t i = base + k;
-      if (i < q) S[i] = (int32_t)run;
-      run += deg[k];
-    }
-    if (tile == ntiles - 1 && threadIdx.x == 0) {
-      *total = (long long)s_excl + agg;
-      S[q] = (int32_t)*total;
-      last = true;
-    }
-    __syncthreads();
-  }
-  return last;
-}
-
 // ------------------------------------------------------------- advance
-// Number of frontier positions i in [0, q) whose merge-path end marker (at
-// merged position S[i+1] + i) lies before diagonal d.
-__device__ __forceinline__ int32_t merge_count(const int32_t *S, int32_t q, long long d) {
-  int32_t lo = 0, hi = q;
-  while (lo < hi) {
-    const int32_t mid = lo + ((hi - lo) >> 1);
-    if ((long long)S[mid + 1] + mid < d) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// merge_count with S[q] supplied by the caller (when the array's last entry
-// is not stored)
-__device__ __forceinline__ int32_t merge_count_t(const int32_t *S, int32_t q, int32_t s_q,
-                                                 long long d) {
-  int32_t lo = 0, hi = q;
-  while (lo < hi) {
-    const int32_t mid = lo + ((hi - lo) >> 1);
-    const int32_t sv = (mid + 1 == q) ? s_q : S[mid + 1];
-    if ((long long)sv + mid < d) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // Block-cooperative merge-path search: the count c in [lo, hi] of
 // positions i whose end marker S[i+1] + i lies before diagonal d (markers
 // are strictly increasing in i). Each round every thread probes one
