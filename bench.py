@@ -376,9 +376,11 @@ def suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     g = gr.gr_graph_create(r, c, w)
     gr.gr_autotune(g, [int(np.argmax(np.diff(r)))], gr.GR_TUNE_SSSP)
     dist = torch.empty(n, dtype=torch.int32, device=dev)
+    # launch mode (host-enqueued iterations) only for profiling runs
+    o = gr.gr_opts(mode=gr.GR_MODE_LAUNCH) if args.mode == "launch" else None
     per, byts = [], []
     for s in srcs:
-        ms, _ = _timed_calls(lambda: gr.gr_sssp(g, int(s), dist), 2, flush)
+        ms, _ = _timed_calls(lambda: gr.gr_sssp(g, int(s), dist, opts=o), 2, flush)
         d = dist.cpu().numpy().view(np.uint32)
         per.append(ms)
         byts.append(reach_bytes(r, d != INF, 8, 4))
