@@ -144,7 +144,12 @@ gr_status gr_sssp_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
  * components for a directed CSR). *num_components (host, may be NULL)
  * receives the number of components; asking for it synchronises. Hooking
  * links the larger root under the smaller over the edge frontier, pointer
- * jumping then points every vertex at its root. opts is unused. */
+ * jumping then points every vertex at its root. On a symmetric CSR the
+ * hooking pass is sampled: every vertex first hooks to its first two
+ * neighbours, the trees are compressed, and only the vertices outside the
+ * component most of a fixed sample of vertices falls in hook all their
+ * edges (the labels are the same; the call synchronises once to read the
+ * sample). opts is unused. */
 gr_status gr_cc(gr_graph *g, int32_t *label, int32_t *num_components,
                 const gr_opts *opts, void *stream);
 
@@ -161,9 +166,11 @@ gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
                       float *rank, int32_t *iters, const gr_opts *opts,
                       void *stream);
 
-/* Batched BFS from k in [1, 64] sources at once (one bit lane per source;
- * every level reads each column index once for all lanes). srcs[k] is a
- * host array of vertices (repeats allowed). depth[k*n] (int32) receives
+/* Batched BFS from k in [1, 64] sources at once (one bit lane per source).
+ * A level whose frontier (over all lanes) has fewer than m/16 edges pushes
+ * the lanes of the frontier's vertices to their neighbours; the others pull
+ * over every vertex, reading each column index once for all lanes. srcs[k]
+ * is a host array of vertices (repeats allowed). depth[k*n] (int32) receives
  * source-major results: depth[i*n + v] is the hop count from srcs[i] to v,
  * -1 where unreached, equal to gr_bfs's depth for that source. Synchronises
  * once per level (the level loop is host-driven). */
@@ -203,7 +210,7 @@ gr_status gr_bfs_noalloc(int32_t n, int64_t m, const int32_t *row_off,
                          const int32_t *col, int32_t src, int32_t *depth,
                          int32_t *parent, void *stream);
 
-/* Per-level trace of the last completed gr_bfs (graph and launch modes;
+/* Per-level trace of the last completed gr_bfs (every level-loop driver;
  * host outputs, any may be NULL; synchronises). For level i < min(cap,
  * *levels): dir[i] 0 = push, 1 = pull; frontier[i] the frontier size the
  * level expanded; edges[i] that frontier's edge count; end_us[i] device
@@ -243,7 +250,11 @@ gr_status gr_tuned_opts(const gr_graph *g, gr_opts *out, double *bfs_ms, double 
  * requests for that graph and runs them as lanes of one gr_bfs_batch
  * traversal. Results equal those of gr_bfs / gr_sssp / gr_cc alone. With
  * num_slots = 1 and max_batch = 1 the server is the plain path: one query
- * per launch sequence, in arrival order, on one stream.
+ * per launch sequence, in arrival order, on one stream. A request whose
+ * traversal stops at a device-side level or iteration limit fails with
+ * GR_ETIMEOUT; a slot waits at most 120 s for a batch's device work, after
+ * which that batch fails with GR_ETIMEOUT and the slot fails its later
+ * requests (its stream may still hold work).
  * ---------------------------------------------------------------------- */
 typedef struct gr_server gr_server;
 
