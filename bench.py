@@ -38,8 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # numbers are in profiles/k_bfs_do_rmat21_full.md), scaled to other scales by
 # the edge count. It is reported only while the traversal's sources hash to
 # the value they had when it was measured (null after any change).
-TRAFFIC_S21 = {"bytes_per_traversal": 44877296, "m": 63540402,
-               "sources_sha256": "1a9f3ce02ef4fdbd8993b367f77893c200e4bc548009a900fa18e0ccf3790e6c"}
+TRAFFIC_S21 = {"bytes_per_traversal": 44866416, "m": 63540402,
+               "sources_sha256": "64ba29ab72c8d8d68a0e3233aeb3bdf9738b0f3d304280828ae781ae9d0cc1d0"}
 TRAFFIC_SOURCES = ("paper_1501_05387_gb300/csrc/bfs.cu", "paper_1501_05387_gb300/csrc/advance.cuh",
                    "paper_1501_05387_gb300/csrc/gr_internal.cuh")
 
@@ -389,7 +389,7 @@ def suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     out.append({"workload": f"rmat{scale}_sssp", "primitive": "sssp", "calls": 2 * len(srcs),
                 "last_call": {"iterations": it, "phases": ph, "edges_relaxed_per_m": rl / m},
                 "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
-                "tuned": gr.gr_tuned_opts(g),
+                "tuned": gr.gr_tuned_opts(g), "tuned_sssp": gr.gr_tuned_sssp(g),
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
                                   "8 B per column+weight entry of the reached vertices, "
                                   "4 B per row offset, 4 B per reached distance")})
@@ -432,6 +432,7 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     mean = float(np.mean(per))
     out.append({"workload": "grid4096_sssp", "primitive": "sssp", "calls": 2,
                 "tuned_delta": gr.gr_tuned_opts(g)["delta"],
+                "tuned_sssp": gr.gr_tuned_sssp(g),
                 "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
                 "iterations": iters,
                 "roofline": _roof(float(np.mean(byts)), mean, peak,

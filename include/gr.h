@@ -238,6 +238,12 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
  * over the tuning sample. */
 gr_status gr_tuned_opts(const gr_graph *g, gr_opts *out, double *bfs_ms, double *sssp_ms);
 
+/* The graph's current SSSP settings (host outputs, any may be NULL): the
+ * level-loop driver (GR_MODE_*), blocks per SM of the persistent kernel
+ * (0 = all resident) and the near/far bucket width (UINT32_MAX: one bucket). */
+gr_status gr_tuned_sssp(const gr_graph *g, int32_t *mode, int32_t *blocks_per_sm,
+                        uint32_t *delta);
+
 /* ------------------------------------------------------------------------
  * Query server (not in the paper): BFS / SSSP / CC queries on resident
  * graphs with continuous batching. Worker slots each own a CUDA stream and

@@ -73,6 +73,7 @@ _sig("gr_bfs_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_bc", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_autotune", [_vp, _vp, _i32, _i32, _vp])
 _sig("gr_tuned_opts", [_vp, _P(gr_opts), _P(ctypes.c_double), _P(ctypes.c_double)])
+_sig("gr_tuned_sssp", [_vp, _P(_i32), _P(_i32), _P(ctypes.c_uint32)])
 _sig("gr_diag_wait_timeout", [_i64, _vp])
 _sig("gr_diag_fail_alloc", [_i64])
 _sig("gr_diag_guard", [_P(_i32), _P(_i64), _P(_i64)])
@@ -302,6 +303,14 @@ def gr_tuned_opts(g: Graph):
            "gr_tuned_opts")
     return {"mode": o.mode, "direction": o.direction, "alpha": o.alpha, "beta": o.beta, "blocks_per_sm": o.block,
             "delta": o.delta, "bfs_ms": b.value, "sssp_ms": s.value}
+
+
+def gr_tuned_sssp(g: Graph):
+    m, b = _i32(), _i32()
+    d = ctypes.c_uint32()
+    _check(_lib.gr_tuned_sssp(g.handle, ctypes.byref(m), ctypes.byref(b), ctypes.byref(d)),
+           "gr_tuned_sssp")
+    return {"mode": m.value, "blocks_per_sm": b.value, "delta": d.value}
 
 
 _live_servers = weakref.WeakSet()
