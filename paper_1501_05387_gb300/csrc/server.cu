@@ -101,15 +101,14 @@ struct Server {
     const gr_graph *g = graphs[r.graph].g;
     return sizeof(int32_t) * (size_t)g->n;
   }
-  void worker(int slot);
+  void worker();
 };
 
 namespace {
 
 // Pick the next batch for a slot (caller holds the lock): the oldest
 // request whose memory fits, plus same-graph BFS requests behind it.
-std::vector<uint64_t> take_batch(Server &S, int slot_ws_missing_bytes_unused) {
-  (void)slot_ws_missing_bytes_unused;
+std::vector<uint64_t> take_batch(Server &S) {
   std::vector<uint64_t> out;
   for (auto it = S.queue.begin(); it != S.queue.end(); ++it) {
     Request &r = S.reqs[*it];
@@ -165,8 +164,7 @@ gr_status copy_out(const Request &r, const void *dev, size_t bytes, cudaStream_t
 
 }  // namespace
 
-void Server::worker(int slot) {
-  (void)slot;
+void Server::worker() {
   cudaSetDevice(device);
   cudaStream_t s = nullptr;
   // a slot without a stream still drains its requests, failing them, so
@@ -187,7 +185,7 @@ void Server::worker(int slot) {
       std::unique_lock<std::mutex> lock(mu);
       cv_work.wait(lock, [&] {
         if (stopping) return true;
-        batch = take_batch(*this, 0);
+        batch = take_batch(*this);
         return !batch.empty();
       });
       if (batch.empty()) break;  // stopping
@@ -385,7 +383,7 @@ gr_status gr_server_submit(gr_server *srv, int32_t graph_id, int32_t kind, int32
   S.queue.push_back(r.ticket);
   *ticket = r.ticket;
   if (S.workers.empty())
-    for (int i = 0; i < S.nslots; ++i) S.workers.emplace_back([&S, i] { S.worker(i); });
+    for (int i = 0; i < S.nslots; ++i) S.workers.emplace_back([&S] { S.worker(); });
   lock.unlock();
   S.cv_work.notify_one();
   return GR_OK;
