@@ -374,10 +374,11 @@ def suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     srcs = gg.sources(r, 16, seed=2)
     n, m = r.size - 1, c.size
     g = gr.gr_graph_create(r, c, w)
-    gr.gr_autotune(g, [int(np.argmax(np.diff(r)))], gr.GR_TUNE_SSSP)
-    dist = torch.empty(n, dtype=torch.int32, device=dev)
-    # launch mode (host-enqueued iterations) only for profiling runs
+    # launch mode (host-enqueued iterations, untuned) only for profiling runs
     o = gr.gr_opts(mode=gr.GR_MODE_LAUNCH) if args.mode == "launch" else None
+    if o is None:
+        gr.gr_autotune(g, [int(np.argmax(np.diff(r)))], gr.GR_TUNE_SSSP)
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
     per, byts = [], []
     for s in srcs:
         ms, _ = _timed_calls(lambda: gr.gr_sssp(g, int(s), dist, opts=o), 2, flush)
@@ -420,8 +421,8 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
                                   "4 B per column entry of the reached vertices, 4 B per "
                                   "row offset, 8 B depth+parent per reached vertex")})
-    # SSSP bucket width and driver tuned once on one sample source
-    gr.gr_autotune(g, [int(srcs[0])], gr.GR_TUNE_SSSP)
+    # SSSP bucket width and driver tuned once on two sample sources
+    gr.gr_autotune(g, [int(srcs[0]), int(srcs[1])], gr.GR_TUNE_SSSP)
     per, byts, iters = [], [], []
     dist_g = torch.empty(n, dtype=torch.int32, device=dev)
     for s in srcs[:2]:
