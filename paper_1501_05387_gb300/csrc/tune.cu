@@ -155,11 +155,15 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
     }
     float best = FLT_MAX;
     SCand pick = cands[0];
+    const int32_t saved_sbps = g->tuned_sssp_blocks_per_sm;
     for (const SCand &c : cands) {
       gr_opts o = default_opts();
       o.delta = c.delta;
       o.mode = c.mode;
-      o.block = c.bps;
+      // the candidate's grid size goes through the graph's tuned value, as
+      // it will be used afterwards (o.block = 0 would mean "tuned", and 0
+      // here means "all resident blocks")
+      g->tuned_sssp_blocks_per_sm = c.bps;
       GR_TRY(sssp_run(g, g->sssp, srcs[0], out.as<uint32_t>(), nullptr, o, s));
       float ms = FLT_MAX;
       for (int rep = 0; rep < kTuneReps; ++rep) {
@@ -181,7 +185,7 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
     // UINT32_MAX selects "one bucket"; it is stored as is
     g->sssp_delta = pick.delta;
     g->tuned_sssp_mode = pick.mode;
-    g->tuned_sssp_blocks_per_sm = pick.bps;
+    g->tuned_sssp_blocks_per_sm = pick.mode == GR_MODE_PERSISTENT ? pick.bps : saved_sbps;
     g->tuned_sssp_ms = best / k;
   }
   GR_CUDA(cudaStreamSynchronize(s));
