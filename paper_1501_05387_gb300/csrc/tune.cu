@@ -145,7 +145,7 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
     std::vector<SCand> cands;
     const double mw = std::max(1.0, g->mean_weight);
     std::vector<uint32_t> deltas;
-    for (double f : {0.5, 1.0, 2.0, 4.0, 8.0, 32.0})
+    for (double f : {0.5, 1.0, 2.0, 4.0, 8.0, 32.0, 64.0})
       deltas.push_back((uint32_t)std::max(1.0, std::min(4.0e9, f * mw)));
     deltas.push_back(UINT32_MAX);
     for (uint32_t d : deltas) {
