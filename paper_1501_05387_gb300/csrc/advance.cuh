@@ -390,23 +390,40 @@ struct alignas(128) BarrierLine {
   int32_t v;
 };
 
+// A value the releasing block publishes with the release: two 64-bit words,
+// each [63:32] the barrier's generation and [31:0] one half of the value, so a
+// waiter that sees both tags equal to the generation it waits for holds the
+// value without another round trip (each word is read atomically).
+struct alignas(128) PayloadLine {
+  unsigned long long w[2];
+};
+
 struct GridBarrier {
   BarrierLine group[kBarrierGroups];
   BarrierLine root;
   BarrierLine gen;
+  PayloadLine pay;
 };
 
 __device__ __forceinline__ void grid_barrier_reset(GridBarrier *b) {
   for (int i = 0; i < kBarrierGroups; ++i) b->group[i].v = 0;
   b->root.v = 0;
   b->gen.v = 0;
+  b->pay.w[0] = 0ull;
+  b->pay.w[1] = 0ull;
 }
 
 // `gen` is the block's private count of barriers passed (starts at 0).
-__device__ __forceinline__ bool grid_sync(GridBarrier *b, int32_t *error, int32_t &gen) {
+// With pay_src, the releasing block reads *pay_src (a 64-bit value every
+// block finished writing before it arrived) and publishes it with the
+// release; every block receives it in *pay_out.
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, int32_t *error, int32_t &gen,
+                                          const unsigned long long *pay_src = nullptr,
+                                          unsigned long long *pay_out = nullptr) {
   __syncthreads();
   bool ok = true;
   __shared__ int32_t s_ok;
+  __shared__ unsigned long long s_pay;
   if (threadIdx.x == 0) {
     __threadfence();
     const int32_t nblocks = gridDim.x;
@@ -434,12 +451,31 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, int32_t *error, int32_
         }
       }
     }
+    const unsigned long long tag = (unsigned long long)(uint32_t)(my_gen + 1) << 32;
     if (release) {
+      if (pay_src) {
+        const unsigned long long v = *(const volatile unsigned long long *)pay_src;
+        s_pay = v;
+        volatile unsigned long long *pw = b->pay.w;
+        pw[0] = tag | (v & 0xFFFFFFFFull);
+        pw[1] = tag | (v >> 32);
+        __threadfence();
+      }
       atomicExch(&b->gen.v, my_gen + 1);
     } else {
       int64_t spins = 0;
       unsigned ns = 32;
-      while (*(volatile int32_t *)&b->gen.v == my_gen) {
+      for (;;) {
+        if (pay_src) {
+          const volatile unsigned long long *pw = b->pay.w;
+          const unsigned long long w0 = pw[0], w1 = pw[1];
+          if ((w0 & ~0xFFFFFFFFull) == tag && (w1 & ~0xFFFFFFFFull) == tag) {
+            s_pay = (w0 & 0xFFFFFFFFull) | (w1 << 32);
+            break;
+          }
+        } else if (*(volatile int32_t *)&b->gen.v != my_gen) {
+          break;
+        }
         if (++spins > kSpinLimit) {
           atomicExch(error, kDevTimeout);
           ok = false;
@@ -454,6 +490,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, int32_t *error, int32_
   }
   gen += 1;
   __syncthreads();
+  if (pay_out) *pay_out = s_pay;
   return s_ok != 0;
 }
 

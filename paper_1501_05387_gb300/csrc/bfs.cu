@@ -892,8 +892,15 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
       if (a.low_degree) push_level_thread(a, c, parity, L, qq, counter);
       else push_level(a, c, sm, parity, L, qq, qe, counter);
     }
-    if (!grid_barrier(c, gridDim.x, gen)) break;
-    const unsigned long long pk = *(volatile unsigned long long *)counter;
+    // with the two-level barrier of a large grid the level's counter comes
+    // with the release; after a one-level barrier every block reads it
+    unsigned long long pk = 0ull;
+    if (gridDim.x > kFlatBarrierBlocks) {
+      if (!grid_sync(&c->bar, &c->error, gen, counter, &pk)) break;
+    } else {
+      if (!grid_barrier(c, gridDim.x, gen)) break;
+      pk = *(volatile unsigned long long *)counter;
+    }
     seg_maxdeg = dir == kPull ? *(volatile int32_t *)&c->maxdeg3[L % 3] : 0;
     const int32_t qn = (int32_t)(pk & 0xFFFFFFFFull);
     const long long mfn = (long long)(pk >> 32);
