@@ -115,6 +115,22 @@ gr_status gr_graph_info(const gr_graph *g, int32_t *n, int64_t *m,
 gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                  const gr_opts *opts, void *stream);
 
+/* k breadth-first searches, one after another, each exactly as gr_bfs
+ * (Sec. 5.1) from srcs[i] into depth[i][n] and, when parent is not NULL and
+ * parent[i] is not NULL, parent[i][n]. srcs (k entries), depth and parent
+ * (k pointers each) are host arrays; each output pointer is host or device
+ * memory, as for gr_bfs. Results bound for host memory are copied out on a
+ * copy stream of the graph while the next search runs, through two device
+ * staging sets that alternate between searches (4n bytes per output each,
+ * allocated at first use and kept by the graph). With page-locked host
+ * outputs the copies overlap the searches; with pageable ones each copy
+ * completes before the next search is enqueued. When `stream` reaches the
+ * end of the call's work, every output, host or device, is complete.
+ * k = 0 does nothing. Every source and output pointer is checked before
+ * any work is enqueued (GR_EINVAL). */
+gr_status gr_bfs_multi(gr_graph *g, int32_t k, const int32_t *srcs, int32_t *const *depth,
+                       int32_t *const *parent, const gr_opts *opts, void *stream);
+
 /* Number of levels (including the source's) and of pull levels of the last
  * completed gr_bfs on this graph (host scalars; synchronises). */
 gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels);

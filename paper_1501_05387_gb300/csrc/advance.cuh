@@ -59,13 +59,17 @@ __device__ int32_t block_merge_search(const int32_t *S, int32_t q, int32_t s_q, 
 }
 
 // Both ends of a chunk [d0, d1) (d1 - d0 <= chunk): i0 over the whole
-// frontier, then i1 within i0 + chunk.
+// frontier, then i1 within i0 + chunk. The path starts at vertex 0 and ends
+// at vertex q, so the first and the last chunk skip that search (d0 and d1
+// are the same for the whole block).
 template <int THREADS>
 __device__ __forceinline__ void block_chunk_bounds(const int32_t *S, int32_t q, int32_t s_q,
                                                    long long d0, long long d1, int32_t chunk,
                                                    int32_t *s_red, int32_t *i0, int32_t *i1) {
-  *i0 = block_merge_search<THREADS>(S, q, s_q, d0, 0, q, s_red);
-  *i1 = block_merge_search<THREADS>(S, q, s_q, d1, *i0, min(q, *i0 + chunk), s_red);
+  *i0 = d0 <= 0 ? 0 : block_merge_search<THREADS>(S, q, s_q, d0, 0, q, s_red);
+  *i1 = d1 >= (long long)q + s_q
+            ? q
+            : block_merge_search<THREADS>(S, q, s_q, d1, *i0, min(q, *i0 + chunk), s_red);
 }
 
 // Append `v` to one of two block-local output buffers selected per thread

@@ -1244,6 +1244,80 @@ gr_status gr_bfs(gr_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   return GR_OK;
 }
 
+gr_status gr_bfs_multi(gr_graph *g, int32_t k, const int32_t *srcs, int32_t *const *depth,
+                       int32_t *const *parent, const gr_opts *opts, void *stream) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (k < 0) return fail(GR_EINVAL, "k must be >= 0");
+  if (k == 0) return GR_OK;
+  if (!srcs || !depth) return fail(GR_EINVAL, "srcs and depth must not be NULL");
+  const gr_opts &o = opts ? *opts : default_opts();
+  // every argument is checked before any work is enqueued
+  std::vector<uint8_t> host_d(k), host_p(k);
+  for (int32_t i = 0; i < k; ++i) {
+    if (!depth[i]) return fail(GR_EINVAL, "depth[i] must not be NULL");
+    GR_TRY(bfs_check(g, srcs[i], o));
+    bool hd = false, hp = false;
+    GR_TRY(output_on_host(g, depth[i], &hd));
+    if (parent) GR_TRY(output_on_host(g, parent[i], &hp));
+    host_d[i] = hd;
+    host_p[i] = hp;
+  }
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  GR_TRY(begin_call(g, s));
+  if (!g->bfs) GR_TRY(bfs_ws_create(g, s, &g->bfs));
+  if (!g->copy_stream) GR_CUDA(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b) {
+    if (!g->pipe_filled[b])
+      GR_CUDA(cudaEventCreateWithFlags(&g->pipe_filled[b], cudaEventDisableTiming));
+    if (!g->pipe_free[b])
+      GR_CUDA(cudaEventCreateWithFlags(&g->pipe_free[b], cudaEventDisableTiming));
+  }
+  const size_t bytes = sizeof(int32_t) * (size_t)g->n;
+  bool used[2] = {false, false};
+  int last = -1;
+  auto run = [&]() -> gr_status {
+    int b = 0;
+    for (int32_t i = 0; i < k; ++i) {
+      int32_t *par = parent ? parent[i] : nullptr;
+      if (!host_d[i] && !host_p[i]) {
+        GR_TRY(bfs_run(g, g->bfs, srcs[i], depth[i], par, o, s));
+        continue;
+      }
+      // staging set b is free once the copies of the search before last are done
+      if (used[b]) GR_CUDA(cudaStreamWaitEvent(s, g->pipe_free[b], 0));
+      DevMem &sd = g->pipe_stage[b][0], &sp = g->pipe_stage[b][1];
+      if (host_d[i] && sd.bytes < bytes) GR_TRY(sd.alloc(bytes, "BFS output staging"));
+      if (host_p[i] && sp.bytes < bytes) GR_TRY(sp.alloc(bytes, "BFS output staging"));
+      int32_t *dd = host_d[i] ? sd.as<int32_t>() : depth[i];
+      int32_t *dp = host_p[i] ? sp.as<int32_t>() : par;
+      GR_TRY(bfs_run(g, g->bfs, srcs[i], dd, dp, o, s));
+      GR_CUDA(cudaEventRecord(g->pipe_filled[b], s));
+      GR_CUDA(cudaStreamWaitEvent(g->copy_stream, g->pipe_filled[b], 0));
+      if (host_d[i])
+        GR_CUDA(cudaMemcpyAsync(depth[i], dd, bytes, cudaMemcpyDeviceToHost, g->copy_stream));
+      if (host_p[i])
+        GR_CUDA(cudaMemcpyAsync(par, dp, bytes, cudaMemcpyDeviceToHost, g->copy_stream));
+      GR_CUDA(cudaEventRecord(g->pipe_free[b], g->copy_stream));
+      used[b] = true;
+      last = b;
+      b ^= 1;
+    }
+    return GR_OK;
+  };
+  const gr_status st = run();
+  // the call's work on `stream` ends after its last copy (copies complete in
+  // order on the copy stream), also when an error stopped the loop early
+  if (last >= 0) {
+    const cudaError_t e = cudaStreamWaitEvent(s, g->pipe_free[last], 0);
+    if (st == GR_OK && e != cudaSuccess) return cuda_fail(e, "gr_bfs_multi");
+  }
+  if (st != GR_OK) return st;
+  GR_TRY(end_call(g, s));
+  return GR_OK;
+}
+
 gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels) {
   clear_error();
   if (!g) return fail(GR_EINVAL, "graph must not be NULL");

@@ -122,6 +122,14 @@ struct gr_graph {
 
   gr::DevMem stage[2];  // device staging for host output pointers
 
+  // gr_bfs_multi: a copy stream for host outputs, two staging sets (depth,
+  // parent) that alternate between searches, and per set the events "the
+  // search filled it" and "its copies finished"
+  cudaStream_t copy_stream = nullptr;
+  gr::DevMem pipe_stage[2][2];
+  cudaEvent_t pipe_filled[2] = {nullptr, nullptr};
+  cudaEvent_t pipe_free[2] = {nullptr, nullptr};
+
   ~gr_graph();
 };
 
@@ -131,6 +139,10 @@ namespace gr {
 // after the previous call on the graph when that ran on another stream.
 gr_status begin_call(gr_graph *g, cudaStream_t s);
 gr_status end_call(gr_graph *g, cudaStream_t s);
+
+// Whether an output pointer is host memory (NULL counts as device); fails
+// for device memory of another device.
+gr_status output_on_host(const gr_graph *g, const void *user, bool *host);
 
 // Output pointer handling: returns a device pointer to write to. If `user`
 // is host memory, a staging buffer of `bytes` is used and *needs_copy set.

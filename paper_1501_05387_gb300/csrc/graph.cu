@@ -82,10 +82,8 @@ gr_status end_call(gr_graph *g, cudaStream_t s) {
   return GR_OK;
 }
 
-gr_status resolve_output(gr_graph *g, int slot, void *user, size_t bytes,
-                         void **dev, bool *needs_copy) {
-  *needs_copy = false;
-  *dev = user;
+gr_status output_on_host(const gr_graph *g, const void *user, bool *host) {
+  *host = false;
   if (!user) return GR_OK;
   cudaPointerAttributes attr;
   cudaError_t e = cudaPointerGetAttributes(&attr, user);
@@ -98,7 +96,18 @@ gr_status resolve_output(gr_graph *g, int slot, void *user, size_t bytes,
       return fail(GR_EINVAL, "output pointer is on another device");
     return GR_OK;
   }
-  // host memory (page-locked or pageable): write to staging, copy at the end
+  *host = true;  // page-locked or pageable host memory
+  return GR_OK;
+}
+
+gr_status resolve_output(gr_graph *g, int slot, void *user, size_t bytes,
+                         void **dev, bool *needs_copy) {
+  *needs_copy = false;
+  *dev = user;
+  bool host = false;
+  GR_TRY(output_on_host(g, user, &host));
+  if (!host) return GR_OK;
+  // host memory: write to staging, copy at the end
   DevMem &st = g->stage[slot];
   if (st.bytes < bytes) GR_TRY(st.alloc(bytes, "output staging"));
   *dev = st.p;
@@ -232,6 +241,11 @@ gr_status validate_host_csr(int32_t n, int64_t m, const int32_t *R,
 
 gr_graph::~gr_graph() {
   if (last_done) cudaEventDestroy(last_done);
+  for (int i = 0; i < 2; ++i) {
+    if (pipe_filled[i]) cudaEventDestroy(pipe_filled[i]);
+    if (pipe_free[i]) cudaEventDestroy(pipe_free[i]);
+  }
+  if (copy_stream) cudaStreamDestroy(copy_stream);
 }
 
 using namespace gr;

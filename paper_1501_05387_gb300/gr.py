@@ -65,6 +65,7 @@ _sig("gr_graph_create", [_i32, _i64, _vp, _vp, _vp, ctypes.c_int, _vp, _P(_vp)])
 _sig("gr_graph_destroy", [_vp])
 _sig("gr_graph_info", [_vp, _P(_i32), _P(_i64), _P(_i32), _P(_i32), _P(_i32), _P(_i32)])
 _sig("gr_bfs", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
+_sig("gr_bfs_multi", [_vp, _i32, _vp, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_bfs_stats", [_vp, _P(_i32), _P(_i32)])
 _sig("gr_bfs_trace", [_vp, _i32, _vp, _vp, _vp, _vp, _P(_i32)])
 _sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
@@ -209,6 +210,22 @@ def gr_bfs(g: Graph, src: int, depth, parent=None, opts=None, stream=None):
     """BFS from src into depth[n] (and parent[n] if given), int32."""
     _check(_lib.gr_bfs(g.handle, int(src), _ptr(depth, np.int32), _ptr(parent, np.int32),
                        _opts(opts), _stream(stream)), "gr_bfs")
+
+
+def gr_bfs_multi(g: Graph, srcs, depths, parents=None, opts=None, stream=None):
+    """len(srcs) searches, each as gr_bfs, into depths[i] (and parents[i]
+    when parents is given; an entry may be None). Host outputs are copied
+    out while the next search runs."""
+    srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    k = int(srcs.size)
+    if len(depths) != k or (parents is not None and len(parents) != k):
+        raise ValueError("one depth (and parent) output per source")
+    dp = (ctypes.c_void_p * max(k, 1))(*[_ptr(d, np.int32) for d in depths])
+    pp = None
+    if parents is not None:
+        pp = (ctypes.c_void_p * max(k, 1))(*[_ptr(p, np.int32) for p in parents])
+    _check(_lib.gr_bfs_multi(g.handle, k, srcs.ctypes.data if k else None, dp, pp,
+                             _opts(opts), _stream(stream)), "gr_bfs_multi")
 
 
 def gr_bfs_stats(g: Graph):

@@ -164,6 +164,73 @@ def test_host_output_buffers(cuda_lib, s14):
     assert np.array_equal(d2, ref)
 
 
+@pytest.mark.parametrize("mode", ["auto", "graph", "persistent"])
+def test_multi_pinned_outputs_on_a_side_stream(cuda_lib, s14, mode):
+    """k searches with page-locked host outputs: more searches than staging
+    sets, so a set is reused only after its copies finished; synchronising
+    the call's own stream (not the device) must be enough to read them."""
+    import torch
+    r, c, g = s14
+    srcs = [int(s) for s in gg.sources(r, 7, seed=11)] + [gg.max_degree_vertex(r)]
+    d = [torch.full((g.n,), -7, dtype=torch.int32).pin_memory() for _ in srcs]
+    p = [torch.full((g.n,), -7, dtype=torch.int32).pin_memory() for _ in srcs]
+    st = torch.cuda.Stream()
+    cuda_lib.gr_bfs_multi(g, srcs, d, p, opts(cuda_lib, "auto", mode), st)
+    st.synchronize()
+    for s, di, pi in zip(srcs, d, p):
+        ref, _ = oracle.bfs(r, c, s)
+        assert np.array_equal(di.numpy(), ref)
+        validate_bfs(r, c, s, di.numpy(), pi.numpy())
+
+
+def test_multi_mixed_outputs(cuda_lib, s14):
+    """Host (pinned and pageable) and device outputs in one call, parents
+    missing for some sources, the same source twice."""
+    import torch
+    r, c, g = s14
+    srcs = [int(s) for s in gg.sources(r, 4, seed=12)]
+    srcs = srcs + [srcs[0]]
+    d = [np.empty(g.n, np.int32), torch.empty(g.n, dtype=torch.int32, device="cuda"),
+         torch.empty(g.n, dtype=torch.int32).pin_memory(), np.empty(g.n, np.int32),
+         torch.empty(g.n, dtype=torch.int32, device="cuda")]
+    p = [None, torch.empty(g.n, dtype=torch.int32).pin_memory(),
+         torch.empty(g.n, dtype=torch.int32, device="cuda"), np.empty(g.n, np.int32), None]
+    cuda_lib.gr_bfs_multi(g, srcs, d, p)
+    torch.cuda.synchronize()
+
+    def host(x):
+        return x.cpu().numpy() if hasattr(x, "cpu") else x
+
+    for s, di, pi in zip(srcs, d, p):
+        ref, _ = oracle.bfs(r, c, s)
+        assert np.array_equal(host(di), ref)
+        if pi is not None:
+            validate_bfs(r, c, s, host(di), host(pi))
+    # without any parent outputs; then k = 0 does nothing
+    d1 = [torch.empty(g.n, dtype=torch.int32).pin_memory() for _ in srcs[:3]]
+    cuda_lib.gr_bfs_multi(g, srcs[:3], d1)
+    torch.cuda.synchronize()
+    for s, di in zip(srcs[:3], d1):
+        assert np.array_equal(di.numpy(), oracle.bfs(r, c, s)[0])
+    cuda_lib.gr_bfs_multi(g, [], [])
+
+
+def test_multi_checks_everything_before_enqueueing(cuda_lib, s14):
+    import torch
+    r, c, g = s14
+    good = int(gg.sources(r, 1, seed=13)[0])
+    d = [torch.full((g.n,), -7, dtype=torch.int32).pin_memory() for _ in range(3)]
+    for bad in [-1, g.n]:
+        with pytest.raises(cuda_lib.GrError) as ei:
+            cuda_lib.gr_bfs_multi(g, [good, good, bad], d)
+        assert ei.value.status == cuda_lib.GR_EINVAL
+    torch.cuda.synchronize()
+    assert all(int(x[0]) == -7 for x in d)  # nothing ran, not even the good sources
+    with pytest.raises(cuda_lib.GrError) as ei:
+        cuda_lib.gr_bfs_multi(g, [good, good], [d[0], None])
+    assert ei.value.status == cuda_lib.GR_EINVAL
+
+
 def test_device_resident_inputs_and_streams(cuda_lib):
     import torch
     r, c = gg.rmat(12, 8, seed=3)
