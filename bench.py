@@ -374,8 +374,10 @@ def suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     srcs = gg.sources(r, 16, seed=2)
     n, m = r.size - 1, c.size
     g = gr.gr_graph_create(r, c, w)
-    # launch mode (host-enqueued iterations, untuned) only for profiling runs
-    o = gr.gr_opts(mode=gr.GR_MODE_LAUNCH) if args.mode == "launch" else None
+    # launch mode (host-enqueued iterations, one bucket as the tuner picks on
+    # R-MAT s22) only for profiling runs, where the kernels must be separate
+    # launches
+    o = gr.gr_opts(mode=gr.GR_MODE_LAUNCH, delta=0xFFFFFFFF) if args.mode == "launch" else None
     if o is None:
         gr.gr_autotune(g, [int(np.argmax(np.diff(r)))], gr.GR_TUNE_SSSP)
     dist = torch.empty(n, dtype=torch.int32, device=dev)

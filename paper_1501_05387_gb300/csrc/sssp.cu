@@ -163,7 +163,7 @@ __global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pr
 
 struct SsspSmem {
   int32_t off[kSsspChunk + 1];
-  int32_t u[kSsspChunk + 1];
+  uint32_t du[kSsspChunk + 1];
   int32_t row[kSsspChunk + 1];
   ScannedBuf<kSsspChunk> nearb;
   AppendBuf<kSsspChunk> farb;
@@ -207,19 +207,29 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
     block_chunk_bounds<kSsspThreads>(S, q, st.q_edges, d0, d1, kSsspChunk, sm.sred, &i0, &i1);
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    // per chunk vertex: its scan offset, its row start and its distance (read
+    // once here instead of once per edge)
     for (int32_t k = threadIdx.x; k < nv; k += kSsspThreads) {
       const int32_t i = i0 + k;
-      const int32_t u = GR_IN(i, a.n + 1, 301) ? Q[i] : 0;
+      const int32_t u0 = GR_IN(i, a.n + 1, 301) ? Q[i] : 0;
+      const int32_t u = GR_IN(u0, a.n, 303) ? u0 : 0;
       sm.off[k] = GR_IN(i, a.n + 2, 302) ? S[i] : 0;
-      sm.u[k] = GR_IN(u, a.n, 303) ? u : 0;
-      sm.row[k] = a.R[sm.u[k]];
+      sm.row[k] = a.R[u];
+      sm.du[k] = dist[u];
     }
     __syncthreads();
-    const int32_t ne = (int32_t)(j1 - j0);
-    for (int32_t kb = 0; kb < ne; kb += kSsspThreads) {
-      const int32_t k = kb + threadIdx.x;
-      int code = 0;
-      int32_t v = 0, dv = 0;
+    // each thread takes kSsspItems edges (ranks tid, tid + T, ...) and issues
+    // each step's loads (heads and weights, head distances, atomicMin, stamps,
+    // degrees) for all of them before using any, so the latency chains of the
+    // items overlap
+    const int32_t ne = (int32_t)(j1 - j0);  // <= kSsspChunk: one pass
+    int32_t e[kSsspItems], v[kSsspItems], code[kSsspItems], dv[kSsspItems];
+    uint32_t wt[kSsspItems], du[kSsspItems], nd[kSsspItems], cur[kSsspItems];
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j) {
+      const int32_t k = j * kSsspThreads + threadIdx.x;
+      e[j] = -1;
+      du[j] = 0xFFFFFFFFu;
       if (k < ne) {
         const int32_t er = (int32_t)(j0 + k);
         int32_t lo = 0, hi = nv - 1;
@@ -228,32 +238,55 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
           if (sm.off[mid] <= er) lo = mid;
           else hi = mid - 1;
         }
-        const int32_t e = sm.row[lo] + (er - sm.off[lo]);
-        const bool e_ok = GR_IN(e, a.m, 304);
-        v = e_ok ? a.C[e] : 0;
-        const bool v_ok = e_ok && GR_IN(v, a.n, 305);
-        const unsigned long long nd =
-            v_ok ? (unsigned long long)dist[sm.u[lo]] + a.W[e] : 0xFFFFFFFFull;
-        if (nd < 0xFFFFFFFFull) {  // else not representable: no improvement
-          const uint32_t nd32 = (uint32_t)nd;
-          if (nd32 < dist[v]) {  // plain-load cull
-            const uint32_t old = atomicMin(dist + v, nd32);
-            if (nd32 < old) {
-              if (nd < T) {
-                if (atomicExch(a.stamp + v, iter) != iter) {
-                  code = 1;
-                  dv = a.R[v + 1] - a.R[v];
-                }
-              } else {
-                atomicMin(st.fmin, nd32);
-                if (atomicExch(a.far_stamp + v, epoch) != epoch) code = 2;
-              }
-            }
-          }
+        const int32_t ee = sm.row[lo] + (er - sm.off[lo]);
+        if (GR_IN(ee, a.m, 304)) {
+          e[j] = ee;
+          du[j] = sm.du[lo];
         }
       }
-      emit_scanned(sm.nearb, code == 1, v, dv);
-      emit_plain(sm.farb, code == 2, v);
+    }
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j) {
+      v[j] = e[j] >= 0 ? a.C[e[j]] : -1;
+      wt[j] = e[j] >= 0 ? a.W[e[j]] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j) {
+      nd[j] = 0xFFFFFFFFu;  // not representable below 0xFFFFFFFF: no improvement
+      if (v[j] >= 0 && !GR_IN(v[j], a.n, 305)) v[j] = -1;
+      if (v[j] >= 0) {
+        const unsigned long long t = (unsigned long long)du[j] + wt[j];
+        if (t < 0xFFFFFFFFull) nd[j] = (uint32_t)t;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j)
+      cur[j] = nd[j] != 0xFFFFFFFFu ? dist[v[j]] : 0u;  // plain-load cull
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j) {
+      const bool try_it = nd[j] < cur[j];
+      cur[j] = try_it ? atomicMin(dist + v[j], nd[j]) : 0u;
+      if (!try_it) nd[j] = 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j) {
+      code[j] = 0;
+      if (nd[j] < cur[j]) {  // this thread lowered dist[v]
+        if (nd[j] < T) {
+          code[j] = atomicExch(a.stamp + v[j], iter) != iter ? 1 : 0;
+        } else {
+          atomicMin(st.fmin, nd[j]);
+          code[j] = atomicExch(a.far_stamp + v[j], epoch) != epoch ? 2 : 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j)
+      dv[j] = code[j] == 1 ? a.R[v[j] + 1] - a.R[v[j]] : 0;
+#pragma unroll
+    for (int j = 0; j < kSsspItems; ++j) {
+      emit_scanned(sm.nearb, code[j] == 1, v[j], dv[j]);
+      emit_plain(sm.farb, code[j] == 2, v[j]);
     }
     flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.n + 1);
     flush_plain<kSsspThreads>(sm.farb, st.far_ctr, st.far_dest, st.far_cap);
