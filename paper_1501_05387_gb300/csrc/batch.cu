@@ -25,11 +25,18 @@
 // This is the dependency recursion delta[v] += sigma[v]/sigma[w]*(1+delta[w])
 // regrouped so that each edge needs one gathered value per lane.
 //
+// Path counts are integers, and FP64 arithmetic is scarce on this GPU (a few
+// FP64 operations per clock per SM), so the forward pass counts them exactly
+// in uint64 with integer adds (exact where FP64 rounds, beyond 2^53). A batch
+// whose counts pass 2^64 - 1 (an add carries out) is counted again in FP64,
+// which holds counts up to about 1.8e308.
+//
 // The level loop is host-driven (one small read-back per level) because BC
 // keeps one mask array per level and allocates them as levels appear.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "advance.cuh"
@@ -45,6 +52,9 @@ constexpr int32_t kKeepLevels = 64;
 // edges, and pulls over every vertex otherwise.
 constexpr long long kPushDiv = 16;
 constexpr int kMbChunk = kMbThreads * kMbItems;
+// What the forward pass counts: nothing (batched BFS), path counts in uint64,
+// or path counts in FP64 (a batch whose uint64 counts overflowed).
+enum : int { kSigNone = 0, kSigU64 = 1, kSigF64 = 2 };
 
 struct BatchWorkspace {
   DevMem visit, sigma, q, counter, srcs, lmp;
@@ -70,7 +80,8 @@ struct MbArgs {
   unsigned long long *visit;
   const unsigned long long *cur;  // lm[L]
   unsigned long long *nxt;        // lm[L+1], zero on entry
-  double *sigma;                  // [n][64] or null (BFS only)
+  void *sigma;                    // [n][64] uint64 or FP64 path counts, or null (BFS)
+  int32_t *sig_overflow;          // set when a uint64 path count overflows
   int32_t *depth;                 // [k][n] or null (BC)
   int32_t k;
   int32_t level;
@@ -90,8 +101,31 @@ __device__ __forceinline__ unsigned long long shfl_down_u64(unsigned long long x
   return __shfl_down_sync(0xffffffffu, x, o);
 }
 
-__global__ void k_mb_init(unsigned long long *visit, unsigned long long *lm0, double *sigma,
-                          double *q, int32_t n) {
+// Path-count arithmetic in the forward pass's type: uint64 adds record a
+// carry out in `ovf`, FP64 adds cannot overflow short of infinity (caught
+// when the counts are used).
+template <int SK>
+using CountT = typename std::conditional<SK == kSigU64, unsigned long long, double>::type;
+
+__device__ __forceinline__ unsigned long long count_add(unsigned long long x,
+                                                        unsigned long long y, bool &ovf) {
+  const unsigned long long t = x + y;
+  ovf |= t < x;
+  return t;
+}
+__device__ __forceinline__ double count_add(double x, double y, bool &) { return x + y; }
+
+__device__ __forceinline__ void count_atomic_add(unsigned long long *p, unsigned long long y,
+                                                 bool &ovf) {
+  const unsigned long long old = atomicAdd(p, y);
+  ovf |= old + y < old;
+}
+__device__ __forceinline__ void count_atomic_add(double *p, double y, bool &) {
+  atomicAdd(p, y);
+}
+
+__global__ void k_mb_init(unsigned long long *visit, unsigned long long *lm0,
+                          unsigned long long *sigma, double *q, int32_t n) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     visit[v] = 0ull;
@@ -100,19 +134,20 @@ __global__ void k_mb_init(unsigned long long *visit, unsigned long long *lm0, do
   if (sigma) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * 64;
          i += (int64_t)gridDim.x * blockDim.x) {
-      sigma[i] = 0.0;
+      sigma[i] = 0ull;  // 0 as uint64 and as FP64
       q[i] = 0.0;
     }
   }
 }
 
 __global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long *lm0,
-                             double *sigma, int32_t n_vertices) {
+                             void *sigma, int32_t sk, int32_t n_vertices) {
   const int s = threadIdx.x;
   if (s < k && GR_IN(srcs[s], n_vertices, 205)) {
     const int32_t v = srcs[s];
     atomicOr(lm0 + v, 1ull << s);
-    if (sigma) sigma[(int64_t)v * 64 + s] = 1.0;
+    if (sk == kSigU64) ((unsigned long long *)sigma)[(int64_t)v * 64 + s] = 1ull;
+    if (sk == kSigF64) ((double *)sigma)[(int64_t)v * 64 + s] = 1.0;
   }
 }
 
@@ -121,8 +156,11 @@ __global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long 
 // newly reached lanes. The vertex loader of each chunk folds lm[L] into
 // visit (idempotent, so chunks sharing a vertex may both do it) and, for
 // batched BFS, writes depth L for the lanes of lm[L].
-template <bool SIGMA>
+template <int SK>
 __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
+  constexpr bool SIGMA = SK != kSigNone;
+  using T = CountT<SK>;
+  bool ovf = false;
   __shared__ int32_t s_off[kMbChunk + 1];
   __shared__ unsigned long long s_U[kMbChunk + 1];
   __shared__ int32_t s_red8[kMbThreads / 32];
@@ -190,11 +228,13 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
         }
       } else {
         // the warp serves the edges with bits one at a time: lane l handles
-        // BFS lanes l and l + 32 of the predecessor's 64 sigma values
+        // BFS lanes l and l + 32 of the predecessor's 64 path counts; a half
+        // with no bits set is skipped by the whole warp
+        T *const sigma = (T *)a.sigma;
         uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
         int32_t cur_owner = -1;
         unsigned long long orbits = 0ull;
-        double acc0 = 0.0, acc1 = 0.0;
+        T acc0 = T(0), acc1 = T(0);
         while (act) {
           const int j = __ffs(act) - 1;
           act &= act - 1u;
@@ -203,9 +243,9 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
           const unsigned long long bj = shfl_u64(bits, j);
           if (ov != cur_owner) {
             if (cur_owner >= 0) {
-              double *sg = a.sigma + (int64_t)cur_owner * 64;
-              if ((orbits >> lane) & 1ull) atomicAdd(sg + lane, acc0);
-              if ((orbits >> (lane + 32)) & 1ull) atomicAdd(sg + lane + 32, acc1);
+              T *sg = sigma + (int64_t)cur_owner * 64;
+              if ((orbits >> lane) & 1ull) count_atomic_add(sg + lane, acc0, ovf);
+              if ((orbits >> (lane + 32)) & 1ull) count_atomic_add(sg + lane + 32, acc1, ovf);
               if (lane == 0) {
                 const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
                 if (!old) new_vertices += joined(a, cur_owner);
@@ -213,17 +253,18 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
             }
             cur_owner = ov;
             orbits = 0ull;
-            acc0 = acc1 = 0.0;
+            acc0 = acc1 = T(0);
           }
           orbits |= bj;
-          const double *su = a.sigma + (int64_t)uj * 64;
-          if ((bj >> lane) & 1ull) acc0 += su[lane];
-          if ((bj >> (lane + 32)) & 1ull) acc1 += su[lane + 32];
+          const T *su = sigma + (int64_t)uj * 64;
+          if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 = count_add(acc0, su[lane], ovf);
+          if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull))
+            acc1 = count_add(acc1, su[lane + 32], ovf);
         }
         if (cur_owner >= 0) {
-          double *sg = a.sigma + (int64_t)cur_owner * 64;
-          if ((orbits >> lane) & 1ull) atomicAdd(sg + lane, acc0);
-          if ((orbits >> (lane + 32)) & 1ull) atomicAdd(sg + lane + 32, acc1);
+          T *sg = sigma + (int64_t)cur_owner * 64;
+          if ((orbits >> lane) & 1ull) count_atomic_add(sg + lane, acc0, ovf);
+          if ((orbits >> (lane + 32)) & 1ull) count_atomic_add(sg + lane + 32, acc1, ovf);
           if (lane == 0) {
             const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
             if (!old) new_vertices += joined(a, cur_owner);
@@ -237,6 +278,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
   // vertices that joined lm[L+1] (and their edges)
   for (int o = 16; o > 0; o >>= 1) new_vertices += __shfl_xor_sync(0xffffffffu, new_vertices, o);
   if (lane == 0 && new_vertices) atomicAdd(a.count, new_vertices);
+  if (SK == kSigU64 && __any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(a.sig_overflow, 1);
 }
 
 struct BcBackArgs {
@@ -328,8 +370,9 @@ __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const 
         }
         orbits |= bj;
         const double *qw = a.q + (int64_t)wj * 64;
-        if ((bj >> lane) & 1ull) acc0 += qw[lane];
-        if ((bj >> (lane + 32)) & 1ull) acc1 += qw[lane + 32];
+        // a half with no bits set costs the warp no FP64 add
+        if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 += qw[lane];
+        if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) acc1 += qw[lane + 32];
       }
       if (cur_owner >= 0) {
         double *qv = a.q + (int64_t)cur_owner * 64;
@@ -371,11 +414,13 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long
 // Finish level L: delta[v][s] = sigma[v][s] * q[v][s] (q holds the child
 // sum), bc[v] += delta over the lanes of lm[L][v], then q[v][s] becomes
 // 1/sigma + child sum for level L-1. One warp per vertex, lanes over s.
-__global__ void k_bc_finalize(const unsigned long long *lv, const double *sigma, double *q,
+template <int SK>
+__global__ void k_bc_finalize(const unsigned long long *lv, const void *sigma_p, double *q,
                               double *bc, int32_t n, int32_t *overflow) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
+  const CountT<SK> *sigma = (const CountT<SK> *)sigma_p;
   for (int64_t v = gw; v < n; v += nw) {
     const unsigned long long A = lv[v];
     if (!A) continue;
@@ -383,11 +428,19 @@ __global__ void k_bc_finalize(const unsigned long long *lv, const double *sigma,
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int s = lane + 32 * h;
+      if ((uint32_t)(A >> (32 * h)) == 0u) continue;  // warp-uniform
       if ((A >> s) & 1ull) {
-        const double sg = sigma[v * 64 + s];
         const double child = q[v * 64 + s];
-        if (!isfinite(sg) || sg <= 0.0) *overflow = 1;
-        part += sg * child;
+        double sg;
+        if (SK == kSigU64) {
+          const unsigned long long c = (unsigned long long)sigma[v * 64 + s];
+          if (c == 0ull) *overflow = 1;  // a reached lane has at least one path
+          sg = (double)c;
+        } else {
+          sg = (double)sigma[v * 64 + s];
+          if (!isfinite(sg) || sg <= 0.0) *overflow = 1;
+        }
+        part = fma(sg, child, part);
         q[v * 64 + s] = 1.0 / sg + child;
       }
     }
@@ -444,10 +497,13 @@ __global__ void k_mb_close(const unsigned long long *fpacked, int32_t *S) {
 // With SIGMA (BC's forward pass) the lanes newly sent to v also add u's path
 // counts to v's: the warp serves such edges one at a time, lane l adding
 // lanes l and l + 32.
-template <bool SIGMA>
+template <int SK>
 __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t *Q,
                                                          const int32_t *S,
                                                          const unsigned long long *fpacked) {
+  constexpr bool SIGMA = SK != kSigNone;
+  using T = CountT<SK>;
+  bool ovf = false;
   __shared__ int32_t s_off[kMbChunk + 1];
   __shared__ int32_t s_row[kMbChunk + 1];
   __shared__ unsigned long long s_cur[kMbChunk + 1];
@@ -502,6 +558,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t 
         }
       }
       if (SIGMA) {
+        T *const sigma = (T *)a.sigma;
         uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
         while (act) {
           const int j = __ffs(act) - 1;
@@ -509,10 +566,10 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t 
           const int32_t vj = __shfl_sync(0xffffffffu, v, j);
           const int32_t uj = __shfl_sync(0xffffffffu, u, j);
           const unsigned long long bj = shfl_u64(bits, j);
-          const double *su = a.sigma + (int64_t)uj * 64;
-          double *sv = a.sigma + (int64_t)vj * 64;
-          if ((bj >> lane) & 1ull) atomicAdd(sv + lane, su[lane]);
-          if ((bj >> (lane + 32)) & 1ull) atomicAdd(sv + lane + 32, su[lane + 32]);
+          const T *su = sigma + (int64_t)uj * 64;
+          T *sv = sigma + (int64_t)vj * 64;
+          if ((bj >> lane) & 1ull) count_atomic_add(sv + lane, su[lane], ovf);
+          if ((bj >> (lane + 32)) & 1ull) count_atomic_add(sv + lane + 32, su[lane + 32], ovf);
         }
       }
     }
@@ -520,6 +577,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t 
   }
   for (int o = 16; o > 0; o >>= 1) added += __shfl_xor_sync(0xffffffffu, added, o);
   if (lane == 0 && added) atomicAdd(a.count, added);
+  if (SK == kSigU64 && __any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(a.sig_overflow, 1);
 }
 
 // Depths of a batched BFS from its per-level lane masks, written once, in
@@ -604,20 +662,25 @@ static gr_status level_mask(gr_graph *g, BatchWorkspace *ws, size_t L, cudaStrea
   return GR_OK;
 }
 
-// Forward levels of one batch of k <= 64 sources. Returns the number of
-// levels holding vertices (the sources' level included).
+// Forward levels of one batch of k <= 64 sources, counting paths as `sk`
+// says. Returns the number of levels holding vertices (the sources' level
+// included); with kSigU64, *overflowed tells whether a count passed 2^64 - 1.
 static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
-                             int32_t *depth, bool with_sigma, cudaStream_t s,
-                             int32_t max_levels, int32_t *levels_out) {
+                             int32_t *depth, int sk, cudaStream_t s,
+                             int32_t max_levels, int32_t *levels_out,
+                             bool *overflowed = nullptr) {
+  const bool with_sigma = sk != kSigNone;
   const int grid = g->num_sms * 8;
   unsigned long long *lm0;
   GR_TRY(level_mask(g, ws, 0, s, &lm0));
+  int32_t *sig_overflow = (int32_t *)(ws->counter.as<unsigned long long>() + 3);
+  if (with_sigma) GR_CUDA(cudaMemsetAsync(sig_overflow, 0, sizeof(int32_t), s));
   k_mb_init<<<grid, 256, 0, s>>>(ws->visit.as<unsigned long long>(), lm0,
-                                 with_sigma ? ws->sigma.as<double>() : nullptr,
+                                 with_sigma ? ws->sigma.as<unsigned long long>() : nullptr,
                                  with_sigma ? ws->q.as<double>() : nullptr, g->n);
   GR_CUDA(cudaMemcpyAsync(ws->srcs.p, h_srcs, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
   k_mb_sources<<<1, 64, 0, s>>>(ws->srcs.as<int32_t>(), k, lm0,
-                                with_sigma ? ws->sigma.as<double>() : nullptr, g->n);
+                                with_sigma ? ws->sigma.p : nullptr, sk, g->n);
   GR_CUDA(cudaGetLastError());
   MbArgs a;
   a.R = g->row_off.as<int32_t>();
@@ -626,7 +689,8 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
   a.m = g->m;
   a.all = k == 64 ? ~0ull : ((1ull << k) - 1ull);
   a.visit = ws->visit.as<unsigned long long>();
-  a.sigma = with_sigma ? ws->sigma.as<double>() : nullptr;
+  a.sigma = with_sigma ? ws->sigma.p : nullptr;
+  a.sig_overflow = sig_overflow;
   a.depth = depth;
   a.k = k;
   a.count = ws->counter.as<unsigned long long>();
@@ -671,14 +735,18 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
       GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
       k_mb_compact<<<grid, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
       k_mb_close<<<1, 1, 0, s>>>(fpacked, fs);
-      if (with_sigma)
-        k_mb_push<true><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+      if (sk == kSigU64)
+        k_mb_push<kSigU64><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+      else if (sk == kSigF64)
+        k_mb_push<kSigF64><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
       else
-        k_mb_push<false><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
-    } else if (with_sigma) {
-      k_mb_forward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
+        k_mb_push<kSigNone><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
+    } else if (sk == kSigU64) {
+      k_mb_forward<kSigU64><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
+    } else if (sk == kSigF64) {
+      k_mb_forward<kSigF64><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
     } else {
-      k_mb_forward<false><<<g->num_sms * 8, kMbThreads, 0, s>>>(a);
+      k_mb_forward<kSigNone><<<g->num_sms * 8, kMbThreads, 0, s>>>(a);
     }
     GR_CUDA(cudaGetLastError());
     unsigned long long cnt = 0;
@@ -693,6 +761,15 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
   }
   if (depth && !depth_pass_done) GR_TRY(depth_pass(L));
   *levels_out = L;
+  if (overflowed) {
+    *overflowed = false;
+    if (sk == kSigU64) {
+      int32_t h = 0;
+      GR_CUDA(cudaMemcpyAsync(&h, sig_overflow, sizeof(h), cudaMemcpyDeviceToHost, s));
+      GR_CUDA(cudaStreamSynchronize(s));
+      *overflowed = h != 0;
+    }
+  }
   return GR_OK;
 }
 
@@ -700,7 +777,7 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
 gr_status bfs_batch_run(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
                         int32_t *depth, int32_t max_levels, cudaStream_t s) {
   int32_t levels = 0;  // every depth entry is written by run_forward
-  return run_forward(g, ws, h_srcs, k, depth, false, s, max_levels, &levels);
+  return run_forward(g, ws, h_srcs, k, depth, kSigNone, s, max_levels, &levels);
 }
 
 }  // namespace gr
@@ -758,7 +835,15 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
   for (int32_t b = 0; b < k; b += 64) {
     const int32_t kb = std::min<int32_t>(64, k - b);
     int32_t levels = 0;
-    GR_TRY(run_forward(g, ws, srcs + b, kb, nullptr, true, s, max_levels, &levels));
+    // exact uint64 path counts; a batch whose counts overflow them is
+    // counted again in FP64
+    int sk = kSigU64;
+    bool overflowed = false;
+    GR_TRY(run_forward(g, ws, srcs + b, kb, nullptr, sk, s, max_levels, &levels, &overflowed));
+    if (overflowed) {
+      sk = kSigF64;
+      GR_TRY(run_forward(g, ws, srcs + b, kb, nullptr, sk, s, max_levels, &levels));
+    }
     // backward over levels levels-2 .. 1 (level levels-1 has no children;
     // level 0 holds the sources, which take no credit)
     BcBackArgs ba;
@@ -777,9 +862,14 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
         k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
         k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
       }
-      k_bc_finalize<<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
-                                         ws->sigma.as<double>(), ws->q.as<double>(),
-                                         (double *)d_bc, g->n, overflow);
+      if (sk == kSigU64)
+        k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
+                                                    ws->sigma.p, ws->q.as<double>(),
+                                                    (double *)d_bc, g->n, overflow);
+      else
+        k_bc_finalize<kSigF64><<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
+                                                    ws->sigma.p, ws->q.as<double>(),
+                                                    (double *)d_bc, g->n, overflow);
       GR_CUDA(cudaGetLastError());
     }
   }

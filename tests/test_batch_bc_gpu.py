@@ -138,6 +138,23 @@ def test_bc_no_sources_and_overflow(cuda_lib):
         assert ei.value.status == cuda_lib.GR_EINVAL
 
 
+@pytest.mark.parametrize("diamonds", [60, 70])
+def test_bc_path_counts_past_2_to_the_64(cuda_lib, diamonds):
+    """A chain of diamonds doubles the number of shortest paths at each
+    diamond: 2^60 paths fit the exact uint64 counts, 2^70 do not and the
+    batch is counted again in FP64 (where powers of two are exact)."""
+    edges, c0 = [], 0
+    for i in range(diamonds):
+        a, b, c1 = 3 * i + 1, 3 * i + 2, 3 * i + 3
+        edges += [(c0, a), (c0, b), (a, c1), (b, c1)]
+        c0 = c1
+    n = c0 + 1
+    r, c = gg.from_edges(n, edges)
+    srcs = [0, n - 1, 1, 3 * (diamonds // 2)]
+    with cuda_lib.gr_graph_create(r, c) as g:
+        check_bc(run_bc(cuda_lib, g, srcs), oracle.bc(r, c, srcs))
+
+
 def _oracle_bc_part(args):
     scale, seed, srcs = args
     import graphgen
