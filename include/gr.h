@@ -185,7 +185,9 @@ gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
 /* Batched BFS from k in [1, 64] sources at once (one bit lane per source).
  * A level whose frontier (over all lanes) has fewer than m/16 edges pushes
  * the lanes of the frontier's vertices to their neighbours; the others pull
- * over every vertex, reading each column index once for all lanes. srcs[k]
+ * over every vertex, reading each column index once for all lanes. Pulls
+ * need in-neighbours = out-neighbours, so on a directed (non-symmetric) CSR
+ * every level pushes (along out-edges, as gr_bfs traverses). srcs[k]
  * is a host array of vertices (repeats allowed). depth[k*n] (int32) receives
  * source-major results: depth[i*n + v] is the hop count from srcs[i] to v,
  * -1 where unreached, equal to gr_bfs's depth for that source. Synchronises
@@ -196,10 +198,13 @@ gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k,
 /* Betweenness centrality (Brandes; Sec. 5.3): bc[n] (double) receives
  * bc[v] = sum over s in srcs, t != s of sigma_st(v) / sigma_st, v not in
  * {s, t}, where sigma_st counts shortest (unweighted) s-t paths: no halving
- * for undirected graphs, no normalisation. srcs[k] is a host array (k >= 0,
- * repeats counted). Sources run in batches of 64 bit lanes with FP64 path
- * counts and dependencies. Returns GR_EINVAL if a path count overflows FP64
- * (e.g. large grids). Synchronises once per BFS level. */
+ * for undirected graphs, no normalisation; on a directed CSR paths follow
+ * out-edges. srcs[k] is a host array (k >= 0, repeats counted). Sources run
+ * in batches of 64 bit lanes (the levels as gr_bfs_batch runs them); path
+ * counts are exact uint64 integers, and a batch whose counts pass 2^64 - 1
+ * is counted again in FP64; dependencies are FP64. Returns GR_EINVAL if a
+ * path count overflows FP64 (e.g. large grids). Synchronises once per BFS
+ * level. */
 gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const gr_opts *opts, void *stream);
 

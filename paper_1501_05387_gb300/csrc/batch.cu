@@ -384,8 +384,10 @@ __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const 
   }
 }
 
-// The vertices with lanes in `lv` and at least one edge, with their degree
-// scan (block-wise compaction, one packed atomic per block).
+// The vertices with lanes in `lv`, with their degree scan (block-wise
+// compaction, one packed atomic per block). Vertices without edges are
+// listed too (a directed graph reaches some): they have no children, but
+// their dependencies still have to be finished.
 __global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long *lv,
                                                          const int32_t *R, int32_t n,
                                                          int32_t *Q, int32_t *S,
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long
       bool take = false;
       if (v < n && lv[v]) {
         d = R[v + 1] - R[v];
-        take = d > 0;
+        take = true;
       }
       emit_scanned(buf, take, (int32_t)v, d);
     }
@@ -413,15 +415,22 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long
 
 // Finish level L: delta[v][s] = sigma[v][s] * q[v][s] (q holds the child
 // sum), bc[v] += delta over the lanes of lm[L][v], then q[v][s] becomes
-// 1/sigma + child sum for level L-1. One warp per vertex, lanes over s.
+// 1/sigma + child sum for level L-1. The vertices of level L come listed by
+// k_mb_list (Q[0..q), q in fpacked; a vertex of a level >= 1 has an edge).
+// One warp per vertex, lanes over s.
 template <int SK>
-__global__ void k_bc_finalize(const unsigned long long *lv, const void *sigma_p, double *q,
-                              double *bc, int32_t n, int32_t *overflow) {
+__global__ void k_bc_finalize(const unsigned long long *lv, const int32_t *Q,
+                              const unsigned long long *fpacked, const void *sigma_p,
+                              double *q, double *bc, int32_t n, int32_t *overflow) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   const CountT<SK> *sigma = (const CountT<SK> *)sigma_p;
-  for (int64_t v = gw; v < n; v += nw) {
+  const int32_t nq = (int32_t)(*fpacked & 0xFFFFFFFFull);
+  for (int64_t i = gw; i < nq; i += nw) {
+    const int32_t v0 = Q[i];
+    if (!GR_IN(v0, n, 230)) continue;
+    const int64_t v = v0;
     const unsigned long long A = lv[v];
     if (!A) continue;
     double part = 0.0;
@@ -757,7 +766,9 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     const long long joined_edges = (long long)(cnt >> 32);
     if (joined_vertices == 0) break;  // level L is empty; levels 0..L-1 hold vertices
     if (L >= max_levels) return fail(GR_ETIMEOUT, "level limit reached");
-    push = joined_edges * kPushDiv < g->m;
+    // a pull reads v's row as v's predecessors: only a symmetric CSR has them
+    // there, so a directed graph pushes on every level
+    push = !g->symmetric || joined_edges * kPushDiv < g->m;
   }
   if (depth && !depth_pass_done) GR_TRY(depth_pass(L));
   *levels_out = L;
@@ -855,21 +866,22 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
     int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
     for (int32_t L = levels - 1; L >= 1; --L) {
+      // the vertices of level L (in any lane) with their degree scan
+      ba.lv = ws->lm[L]->as<unsigned long long>();
+      GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
+      k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
       if (L + 1 < levels) {
-        ba.lv = ws->lm[L]->as<unsigned long long>();
         ba.lw = ws->lm[L + 1]->as<unsigned long long>();
-        GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
-        k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
         k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
       }
       if (sk == kSigU64)
-        k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
-                                                    ws->sigma.p, ws->q.as<double>(),
-                                                    (double *)d_bc, g->n, overflow);
+        k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
+                                                    ws->q.as<double>(), (double *)d_bc, g->n,
+                                                    overflow);
       else
-        k_bc_finalize<kSigF64><<<grid, 256, 0, s>>>(ws->lm[L]->as<unsigned long long>(),
-                                                    ws->sigma.p, ws->q.as<double>(),
-                                                    (double *)d_bc, g->n, overflow);
+        k_bc_finalize<kSigF64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
+                                                    ws->q.as<double>(), (double *)d_bc, g->n,
+                                                    overflow);
       GR_CUDA(cudaGetLastError());
     }
   }

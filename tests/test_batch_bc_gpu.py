@@ -138,6 +138,32 @@ def test_bc_no_sources_and_overflow(cuda_lib):
         assert ei.value.status == cuda_lib.GR_EINVAL
 
 
+def directed_rmat(scale, seed, keep=0.6):
+    """R-MAT with each directed entry kept with probability `keep`: a
+    non-symmetric CSR with dense levels and vertices without out-edges."""
+    r, c = gg.rmat(scale, 16, seed=seed)
+    rng = np.random.default_rng(seed)
+    keep_e = rng.random(c.size) < keep
+    rows = np.repeat(np.arange(r.size - 1), np.diff(r))
+    deg = np.bincount(rows[keep_e], minlength=r.size - 1)
+    r2 = np.zeros_like(r)
+    r2[1:] = np.cumsum(deg)
+    return r2.astype(np.int32), c[keep_e].astype(np.int32)
+
+
+def test_batch_bfs_and_bc_directed(cuda_lib):
+    """On a directed CSR every batched level pushes along out-edges; depths
+    equal the oracle's per source, BC equals directed Brandes."""
+    r, c = directed_rmat(12, 7)
+    srcs = gg.sources(r, 64, seed=7)
+    with cuda_lib.gr_graph_create(r, c) as g:
+        assert not cuda_lib.gr_graph_info(g)["symmetric"]
+        d = run_batch(cuda_lib, g, srcs)
+        for i in (0, 17, 40, 63):
+            assert np.array_equal(d[i], oracle.bfs(r, c, int(srcs[i]))[0]), f"lane {i}"
+        check_bc(run_bc(cuda_lib, g, srcs), oracle.bc(r, c, srcs))
+
+
 @pytest.mark.parametrize("diamonds", [60, 70])
 def test_bc_path_counts_past_2_to_the_64(cuda_lib, diamonds):
     """A chain of diamonds doubles the number of shortest paths at each
