@@ -151,14 +151,129 @@ __global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long 
   }
 }
 
-// One forward level: lm[L+1][v] = OR over edges (v,u) of lm[L][u] & ~seen(v),
-// seen(v) = visit[v] | lm[L][v]; with sigma, also the path counts of the
-// newly reached lanes. The vertex loader of each chunk folds lm[L] into
-// visit (idempotent, so chunks sharing a vertex may both do it) and, for
-// batched BFS, writes depth L for the lanes of lm[L].
+// One batched BFS pull level (no path counts): lm[L+1][v] = OR over edges
+// (v, u) of lm[L][u] & ~seen(v), seen(v) = visit[v] | lm[L][v]. Merge-based:
+// a chunk's vertex end markers and edges form one sequence of
+// kMbThreads * kMbPullItems items; each thread finds its first item's
+// vertex with one search, then walks its kMbPullItems consecutive items.
+// The column and lane-mask loads of all its items are issued before any is
+// used, edges of vertices that already hold every lane are skipped, and the
+// OR of a vertex accumulates in a register. A vertex whose edges and end
+// marker all fall in one thread's items is written with a plain store (no
+// other thread touches it); the others with atomicOr. The vertex loader
+// folds lm[L] into visit and, past the kept levels, writes depth L.
+constexpr int kMbPullItems = 8, kMbPullBlocksPerSm = 6;
+__global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbArgs a) {
+  constexpr int ITEMS = kMbPullItems;
+  constexpr int CHUNK = kMbThreads * ITEMS;
+  __shared__ int32_t s_end[CHUNK + 1];  // end marker of each vertex, chunk-local
+  __shared__ unsigned long long s_U[CHUNK + 1];  // lanes the vertex still misses
+  __shared__ int32_t s_red8[kMbThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)a.n + a.R[a.n];
+  const long long nchunks = (total + CHUNK - 1) / CHUNK;
+  unsigned long long new_vertices = 0;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * CHUNK;
+    const long long d1 = min(d0 + CHUNK, total);
+    int32_t i0, i1;
+    block_chunk_bounds<kMbThreads>(a.R, a.n, a.R[a.n], d0, d1, CHUNK, s_red8, &i0, &i1);
+    const long long j0 = d0 - i0;  // CSR position of the chunk's first edge
+    const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
+    const int32_t len = (int32_t)(d1 - d0);
+    for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
+      const int32_t v = i0 + kk;
+      const unsigned long long c = a.cur[v];
+      const unsigned long long seen = a.visit[v] | c;
+      if (c) {
+        a.visit[v] = seen;
+        if (a.depth) {
+          for (int s = 0; s < a.k; ++s)
+            if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 204))
+              a.depth[(int64_t)s * a.n + v] = a.level;
+        }
+      }
+      s_end[kk] = (int32_t)((long long)a.R[v + 1] + v - d0);
+      s_U[kk] = a.all & ~seen;
+    }
+    __syncthreads();
+    const int32_t k0 = min(len, (int32_t)threadIdx.x * ITEMS);
+    const int32_t k1 = min(len, k0 + ITEMS);
+    if (k0 < k1) {
+      // chunk vertices whose end marker lies before k0
+      int32_t lo = 0, hi = nv;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (s_end[mid] < k0) lo = mid + 1;
+        else hi = mid;
+      }
+      // classify the items: end markers (bit i of `ends`) and edges, loading
+      // the column of each edge whose vertex still misses lanes
+      uint32_t ends = 0u;
+      int32_t u[ITEMS];
+      int32_t r = lo, e = k0 - lo;  // e: chunk-local edge index
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = k0 + i;
+        u[i] = -1;
+        if (k < k1 && r < nv) {
+          if (s_end[r] == k) {
+            ends |= 1u << i;
+            ++r;
+          } else {
+            const long long pos = j0 + e;
+            if (s_U[r] && GR_IN(pos, a.m, 202)) u[i] = (int32_t)pos;
+            ++e;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) u[i] = u[i] >= 0 ? a.C[u[i]] : -1;
+      unsigned long long b[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) b[i] = (u[i] >= 0 && GR_IN(u[i], a.n, 203)) ? a.cur[u[i]] : 0ull;
+      // walk: OR per vertex, written at its end marker
+      r = lo;
+      unsigned long long acc = 0ull;
+      bool whole = false;  // the vertex's first edge lies in this thread's items
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = k0 + i;
+        if (k < k1 && r < nv) {
+          if ((ends >> i) & 1u) {
+            if (acc) {
+              const int32_t v = i0 + r;
+              if (whole) {
+                a.nxt[v] = acc;
+                new_vertices += joined(a, v);
+              } else if (!atomicOr(a.nxt + v, acc)) {
+                new_vertices += joined(a, v);
+              }
+            }
+            acc = 0ull;
+            whole = true;
+            ++r;
+          } else {
+            acc |= b[i] & s_U[r];
+          }
+        }
+      }
+      if (acc && r < nv && !atomicOr(a.nxt + (i0 + r), acc))  // continues past k1
+        new_vertices += joined(a, i0 + r);
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) new_vertices += __shfl_xor_sync(0xffffffffu, new_vertices, o);
+  if (lane == 0 && new_vertices) atomicAdd(a.count, new_vertices);
+}
+
+// One BC forward pull level: lm[L+1][v] = OR over edges (v,u) of
+// lm[L][u] & ~seen(v), seen(v) = visit[v] | lm[L][v], and the path counts of
+// the newly reached lanes. The vertex loader of each chunk folds lm[L] into
+// visit (idempotent, so chunks sharing a vertex may both do it).
 template <int SK>
 __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
-  constexpr bool SIGMA = SK != kSigNone;
+  static_assert(SK != kSigNone, "batched BFS pulls with k_mb_pull");
   using T = CountT<SK>;
   bool ovf = false;
   __shared__ int32_t s_off[kMbChunk + 1];
@@ -212,21 +327,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
           bits = GR_IN(u, a.n, 203) ? (a.cur[u] & U) : 0ull;
         }
       }
-      if (!SIGMA) {
-        // segmented OR over runs of equal owners, one atomicOr per run
-        unsigned long long acc = bits;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long x = shfl_down_u64(acc, o);
-          const int32_t oo = __shfl_down_sync(0xffffffffu, owner, o);
-          if (lane + o < 32 && oo == owner) acc |= x;
-        }
-        const int32_t prev = __shfl_up_sync(0xffffffffu, owner, 1);
-        if (owner >= 0 && (lane == 0 || prev != owner) && acc) {
-          const unsigned long long old = atomicOr(a.nxt + owner, acc);
-          if (!old) new_vertices += joined(a, owner);
-        }
-      } else {
+      {
         // the warp serves the edges with bits one at a time: lane l handles
         // BFS lanes l and l + 32 of the predecessor's 64 path counts; a half
         // with no bits set is skipped by the whole warp
@@ -755,7 +856,7 @@ static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_s
     } else if (sk == kSigF64) {
       k_mb_forward<kSigF64><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
     } else {
-      k_mb_forward<kSigNone><<<g->num_sms * 8, kMbThreads, 0, s>>>(a);
+      k_mb_pull<<<g->num_sms * kMbPullBlocksPerSm, kMbThreads, 0, s>>>(a);
     }
     GR_CUDA(cudaGetLastError());
     unsigned long long cnt = 0;
