@@ -275,9 +275,13 @@ gr_status gr_tuned_sssp(const gr_graph *g, int32_t *mode, int32_t *blocks_per_sm
  * holds back the ones behind it). A slot that takes a BFS request on a
  * batchable graph also takes up to max_batch - 1 further queued BFS
  * requests for that graph and runs them as lanes of one gr_bfs_batch
- * traversal. Results equal those of gr_bfs / gr_sssp / gr_cc alone. With
- * num_slots = 1 and max_batch = 1 the server is the plain path: one query
- * per launch sequence, in arrival order, on one stream. A request whose
+ * traversal (see gr_server_add_graph for when). Results equal those of
+ * gr_bfs / gr_sssp / gr_cc alone. With one slot, traversals use each
+ * graph's tuned driver (the persistent kernels included: the slot has the
+ * GPU to itself); with several slots, graph-mode level loops, since a
+ * cooperative launch needs the whole GPU. With num_slots = 1 and
+ * max_batch = 1 the server is the plain path: one query per launch
+ * sequence, in arrival order, on one stream. A request whose
  * traversal stops at a device-side level or iteration limit fails with
  * GR_ETIMEOUT; a slot waits at most 120 s for a batch's device work, after
  * which that batch fails with GR_ETIMEOUT and the slot fails its later
@@ -292,7 +296,12 @@ gr_status gr_server_create(size_t budget_bytes, int32_t num_slots, int32_t max_b
                            gr_server **out);
 
 /* Register a graph (it must outlive the server) before the first submit.
- * batchable = 0 keeps its BFS queries single (graphs with many levels). */
+ * batchable in [0, 64]: a BFS request on the graph runs as a lane of a
+ * batch when at least `batchable` BFS requests for the graph (itself
+ * included) are queued; 0 keeps them single. 1 batches whatever is queued
+ * (low-diameter graphs); a larger value suits graphs with many levels,
+ * whose batched traversal costs a host round trip per level and pays only
+ * when it carries enough queries. */
 gr_status gr_server_add_graph(gr_server *s, gr_graph *g, int32_t batchable,
                               int32_t *graph_id);
 

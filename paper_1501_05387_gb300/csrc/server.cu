@@ -71,7 +71,9 @@ struct SlotGraphState {
 
 struct GraphEntry {
   gr_graph *g = nullptr;
-  bool batchable = true;
+  // a BFS request is run as lanes of a batch when at least this many BFS
+  // requests for the graph are queued (0: never batched)
+  int32_t min_batch = 1;
 };
 
 }  // namespace
@@ -107,7 +109,8 @@ struct Server {
 namespace {
 
 // Pick the next batch for a slot (caller holds the lock): the oldest
-// request whose memory fits, plus same-graph BFS requests behind it.
+// request whose memory fits, plus same-graph BFS requests behind it when
+// enough of them are queued for the graph to batch.
 std::vector<uint64_t> take_batch(Server &S) {
   std::vector<uint64_t> out;
   for (auto it = S.queue.begin(); it != S.queue.end(); ++it) {
@@ -117,7 +120,17 @@ std::vector<uint64_t> take_batch(Server &S) {
     out.push_back(*it);
     S.in_use += need;
     S.queue.erase(it);
-    if (r.kind == GR_QUERY_BFS && S.max_batch > 1 && S.graphs[r.graph].batchable) {
+    bool batch = false;
+    const int32_t min_batch = S.graphs[r.graph].min_batch;
+    if (r.kind == GR_QUERY_BFS && S.max_batch > 1 && min_batch > 0) {
+      int32_t queued = 1;  // r and the same-graph BFS requests behind it
+      for (auto jt = S.queue.begin(); jt != S.queue.end() && queued < min_batch; ++jt) {
+        const Request &q = S.reqs[*jt];
+        if (q.kind == GR_QUERY_BFS && q.graph == r.graph) ++queued;
+      }
+      batch = queued >= min_batch;
+    }
+    if (batch) {
       for (auto jt = S.queue.begin(); jt != S.queue.end() && (int32_t)out.size() < S.max_batch;) {
         Request &q = S.reqs[*jt];
         if (q.kind == GR_QUERY_BFS && q.graph == r.graph) {
@@ -209,10 +222,12 @@ void Server::worker() {
     if (!stream_err.empty()) status = fail(GR_ECUDA, stream_err);
     if (status == GR_OK && !broken.empty()) status = fail(GR_ECUDA, broken);
     if (status == GR_OK && buf.bytes < need) status = buf.alloc(need, "server result buffer");
-    // graph-mode level loops: several slots may run traversals at once, so
-    // no launch may need the whole GPU to itself (cooperative launches do)
+    // with several slots, graph-mode level loops: slots may run traversals
+    // at once, so no launch may need the whole GPU to itself (cooperative
+    // launches do); a single slot has the GPU to itself and runs each
+    // graph's tuned driver
     gr_opts o = default_opts();
-    o.mode = GR_MODE_GRAPH;
+    if (nslots > 1) o.mode = GR_MODE_GRAPH;
     size_t ws_new = 0;
     // the first request of a kind on a graph creates this slot's workspace
     // and captures its level-loop graph; slots do that one at a time
@@ -337,12 +352,13 @@ gr_status gr_server_add_graph(gr_server *srv, gr_graph *g, int32_t batchable,
                               int32_t *graph_id) {
   clear_error();
   if (!srv || !g || !graph_id) return fail(GR_EINVAL, "server, graph and graph_id must not be NULL");
+  if (batchable < 0 || batchable > 64) return fail(GR_EINVAL, "batchable must be in [0, 64]");
   Server &S = srv->impl;
   std::lock_guard<std::mutex> lock(S.mu);
   if (!S.workers.empty()) return fail(GR_EBUSY, "add graphs before the first submit");
   GraphEntry e;
   e.g = g;
-  e.batchable = batchable != 0;
+  e.min_batch = batchable;
   S.graphs.push_back(e);
   *graph_id = (int32_t)S.graphs.size() - 1;
   return GR_OK;

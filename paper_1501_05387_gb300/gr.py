@@ -377,7 +377,9 @@ def gr_server_create(budget_bytes: int, num_slots: int = 4, max_batch: int = 64)
     return Server(out.value)
 
 
-def gr_server_add_graph(s: Server, g: Graph, batchable: bool = True) -> int:
+def gr_server_add_graph(s: Server, g: Graph, batchable: int = 1) -> int:
+    """Register g; batchable = the number of queued same-graph BFS requests
+    from which they run as lanes of one batch (0: never; True counts as 1)."""
     gid = _i32()
     _check(_lib.gr_server_add_graph(s.handle, g.handle, int(batchable), ctypes.byref(gid)),
            "gr_server_add_graph")

@@ -1,6 +1,6 @@
-"""Query server: every result served in the mix (batched, overlapped on
-several streams, admitted under a memory budget) equals the same query run
-alone, bit for bit."""
+"""Query server: every result served in the mix (batched, admitted under a
+memory budget, with several slots overlapped on several streams) equals the
+same query run alone, bit for bit."""
 import os
 
 import numpy as np
@@ -8,15 +8,17 @@ import pytest
 
 import graphgen as gg
 
-# The serving path raised a device fault under a serving benchmark whose
-# cause has not been found by reading the code; until it is, the server's
-# device tests run only when asked for explicitly.
-pytestmark = [
-    pytest.mark.gpu,
-    pytest.mark.skipif(os.environ.get("GR_SERVER_DEVICE_TESTS") != "1",
-                       reason="query-server device tests are opt-in (GR_SERVER_DEVICE_TESTS=1) "
-                              "while an unexplained device fault in the serving path is open"),
-]
+pytestmark = pytest.mark.gpu
+
+# Several slots overlap their device work on separate streams. Serving
+# benchmarks with 4 slots raised a device fault whose cause has not been
+# found by reading the code, while every one-slot phase ran cleanly; until
+# the cause is found, the tests with more than one slot run only when asked
+# for explicitly.
+multi_slot = pytest.mark.skipif(
+    os.environ.get("GR_SERVER_DEVICE_TESTS") != "1",
+    reason="multi-slot server device tests are opt-in (GR_SERVER_DEVICE_TESTS=1) while an "
+           "unexplained device fault with concurrent slots is open")
 
 
 def alone(gr, g, kind, src):
@@ -60,8 +62,10 @@ def make_requests(gr, graphs, count, seed):
     return reqs
 
 
-@pytest.mark.parametrize("slots,batch,budget", [(4, 64, 1 << 30), (1, 1, 1 << 30),
-                                                (3, 16, 200_000)])
+@pytest.mark.parametrize("slots,batch,budget", [
+    (1, 1, 1 << 30), (1, 64, 1 << 30), (1, 16, 200_000),
+    pytest.param(4, 64, 1 << 30, marks=multi_slot),
+    pytest.param(3, 16, 200_000, marks=multi_slot)])
 def test_mix_equals_alone(cuda_lib, pool, slots, batch, budget):
     gr = cuda_lib
     reqs = make_requests(gr, pool, 240, seed=slots * 7 + batch)
@@ -102,6 +106,27 @@ def test_batching_happens_and_device_outputs(cuda_lib, pool):
         assert np.array_equal(o.cpu().numpy(), alone(gr, g, gr.GR_QUERY_BFS, s))
 
 
+@pytest.mark.parametrize("depth,batched", [(8, True), (0, False)])
+def test_batching_depth(cuda_lib, pool, depth, batched):
+    """A graph registered with batchable = 8 batches its BFS requests once 8
+    are queued; with 0 it never batches. Results equal the queries alone."""
+    import torch
+    gr = cuda_lib
+    g = pool[3][0]  # the grid
+    srcs = list(range(0, 20 * 97, 97))
+    with gr.gr_server_create(1 << 30, 1, 64) as srv:
+        gid = gr.gr_server_add_graph(srv, g, depth)
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in srcs]
+        for s, o in zip(srcs, outs):
+            gr.gr_server_submit(srv, gid, gr.GR_QUERY_BFS, s, o)
+        gr.gr_server_drain(srv, 120000)
+        st = gr.gr_server_stats(srv)
+    assert st["completed"] == len(srcs) and st["failed"] == 0
+    assert (st["launches"] < len(srcs)) == batched
+    for s, o in zip(srcs, outs):
+        assert np.array_equal(o.cpu().numpy(), alone(gr, g, gr.GR_QUERY_BFS, s))
+
+
 def test_bad_requests(cuda_lib, pool):
     gr = cuda_lib
     g = pool[0][0]
@@ -113,6 +138,9 @@ def test_bad_requests(cuda_lib, pool):
             assert ei.value.status == gr.GR_EINVAL
         with pytest.raises(gr.GrError) as ei:
             gr.gr_server_wait(srv, 12345, 0)
+        assert ei.value.status == gr.GR_EINVAL
+        with pytest.raises(gr.GrError) as ei:
+            gr.gr_server_add_graph(srv, g, 65)
         assert ei.value.status == gr.GR_EINVAL
     with pytest.raises(gr.GrError):
         gr.gr_server_create(0, 1, 1)
