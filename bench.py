@@ -270,8 +270,8 @@ def run_serving(gr, graphs, batchable, reqs, unit_arrivals, rate, slots, batch, 
 
 def serving_bench(gr, full=False, count=2000, slots=1):
     """Plain path (one slot, no batching) vs served path (`slots` slots,
-    continuous batching of up to 64 BFS lanes per launch) on the same seeded
-    request stream. Every phase must complete all its requests."""
+    continuous batching of up to 64 BFS or SSSP lanes per launch) on the same
+    seeded request stream. Every phase must complete all its requests."""
     pool = serving_pool(full)
     graphs = [gr.gr_graph_create(r, c, w) for (_, _, _, _, r, c, w) in pool]
     try:
@@ -313,7 +313,8 @@ def serving_bench(gr, full=False, count=2000, slots=1):
             "served": {"saturated": pick(served), "at_0.7x_capacity": pick(served_lat),
                        "at_plain_0.7x_load": pick(served_eq),
                        "slots": slots, "max_batch": 64,
-                       "batching_depth": "R-MAT 1, grids 8 (queued same-graph BFS requests)"},
+                       "batching_depth": "BFS: R-MAT 1, grids 8 (queued same-graph BFS requests); "
+                                         "SSSP: whatever is queued, up to the graph's lane limit"},
             "speedup_qps": served["qps"] / max(plain["qps"], 1e-9)}
 
 

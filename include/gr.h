@@ -148,6 +148,27 @@ gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels);
 gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
                   const gr_opts *opts, void *stream);
 
+/* k single-source shortest-path searches in one run (Alg. 1; Sec. 4.5
+ * "Priority Queue"; Sec. 5.2), from the host array srcs[k] (repeats
+ * allowed) into dist[k*n] (uint32, device or host memory, source-major:
+ * dist[i*n + v] is the distance from srcs[i] to v), each equal to gr_sssp's
+ * dist for that source. The k searches run as one near/far search over k
+ * disjoint copies of the graph (vertex i*n + v is v in copy i, which holds
+ * source i only), so they share the device-side loop: on high-diameter
+ * graphs, where an iteration costs a grid barrier rather than bandwidth, k
+ * searches take about the time of one. No pred output. 1 <= k <= 64 with
+ * k*n + 2 and k*m at most INT32_MAX, else GR_EINVAL (the message states the
+ * graph's limit); requires weights. opts->mode GR_MODE_PERSISTENT runs the
+ * cooperative kernel; GR_MODE_GRAPH is taken as GR_MODE_LAUNCH (host-driven
+ * batches of iteration kernels). Scratch grows with k: about 32*k*n bytes,
+ * kept by the graph for the next call. */
+gr_status gr_sssp_batch(gr_graph *g, const int32_t *srcs, int32_t k, uint32_t *dist,
+                        const gr_opts *opts, void *stream);
+
+/* gr_sssp_stats for the last completed gr_sssp_batch on this graph. */
+gr_status gr_sssp_batch_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
+                              int64_t *relaxations);
+
 /* Statistics of the last completed gr_sssp on this graph (host scalars;
  * synchronises): device-loop iterations, near/far phases (splits) and
  * edges expanded. Returns GR_ETIMEOUT if that run hit its iteration cap
@@ -275,7 +296,10 @@ gr_status gr_tuned_sssp(const gr_graph *g, int32_t *mode, int32_t *blocks_per_sm
  * holds back the ones behind it). A slot that takes a BFS request on a
  * batchable graph also takes up to max_batch - 1 further queued BFS
  * requests for that graph and runs them as lanes of one gr_bfs_batch
- * traversal (see gr_server_add_graph for when). Results equal those of
+ * traversal (see gr_server_add_graph for when); likewise an SSSP request
+ * takes further queued SSSP requests for its graph as lanes of one
+ * gr_sssp_batch search (up to max_batch and the graph's lane limit, which
+ * keeps that search's scratch within 4 GiB). Results equal those of
  * gr_bfs / gr_sssp / gr_cc alone. With one slot, traversals use each
  * graph's tuned driver (the persistent kernels included: the slot has the
  * GPU to itself); with several slots, graph-mode level loops, since a
@@ -296,9 +320,11 @@ gr_status gr_server_create(size_t budget_bytes, int32_t num_slots, int32_t max_b
                            gr_server **out);
 
 /* Register a graph (it must outlive the server) before the first submit.
- * batchable in [0, 64]: a BFS request on the graph runs as a lane of a
- * batch when at least `batchable` BFS requests for the graph (itself
- * included) are queued; 0 keeps them single. 1 batches whatever is queued
+ * batchable in [0, 64]: 0 keeps the graph's BFS and SSSP requests single;
+ * otherwise SSSP requests batch whatever is queued, and a BFS request on
+ * the graph runs as a lane of a batch when at least `batchable` BFS
+ * requests for the graph (itself included) are queued. 1 batches whatever
+ * is queued
  * (low-diameter graphs); a larger value suits graphs with many levels,
  * whose batched traversal costs a host round trip per level and pays only
  * when it carries enough queries. */

@@ -116,6 +116,7 @@ struct gr_graph {
   // lazily created scratch, one per primitive (freed by destroy_workspaces)
   gr::BfsWorkspace *bfs = nullptr;
   gr::SsspWorkspace *sssp = nullptr;
+  gr::SsspWorkspace *sssp_batch = nullptr;  // gr_sssp_batch (lane-major copies)
   gr::CcWorkspace *cc = nullptr;
   gr::PrWorkspace *pr = nullptr;
   gr::BatchWorkspace *batch = nullptr;
@@ -159,8 +160,14 @@ gr_status bfs_check(const gr_graph *g, int32_t src, const gr_opts &o);
 gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, int32_t *parent,
                   const gr_opts &o, cudaStream_t s);
 gr_status bfs_read_ctl_error(BfsWorkspace *ws, cudaStream_t s);
-gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out);
-size_t sssp_ws_bytes(const gr_graph *g);
+// lanes > 1: buffers for that many lane-major copies (sssp_batch_run)
+gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out, int32_t lanes = 1);
+size_t sssp_ws_bytes(const gr_graph *g, int32_t lanes = 1);
+// most sources one batched SSSP run on this graph may take
+int32_t sssp_batch_max_lanes(const gr_graph *g);
+// k searches (k <= the workspace's lanes) into dist[k][n] on the device
+gr_status sssp_batch_run(gr_graph *g, SsspWorkspace *ws, const int32_t *h_srcs, int32_t k,
+                         uint32_t *dist, const gr_opts &o, cudaStream_t s);
 gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o);
 // GR_ETIMEOUT when the last SSSP on ws stopped at a device-side limit
 gr_status sssp_read_ctl_error(SsspWorkspace *ws, cudaStream_t s);

@@ -256,6 +256,8 @@ static void destroy_workspaces(gr_graph *g) {
   g->bfs = nullptr;
   free_sssp(g->sssp);
   g->sssp = nullptr;
+  free_sssp(g->sssp_batch);
+  g->sssp_batch = nullptr;
   free_cc(g->cc);
   g->cc = nullptr;
   free_pr(g->pr);

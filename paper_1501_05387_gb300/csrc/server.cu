@@ -13,7 +13,11 @@
 //   * same-graph BFS requests are batched: a worker that takes a BFS request
 //     also takes up to max_batch - 1 further queued BFS requests for that
 //     graph (in arrival order) and runs them as bit lanes of one batched
-//     traversal; high-diameter graphs (many levels) are not batched;
+//     traversal; on high-diameter graphs (many levels) only once enough of
+//     them are queued;
+//   * same-graph SSSP requests are batched the same way, as lanes of one
+//     near/far search over copies of the graph (sssp_batch_run), as many as
+//     the graph's lane limit allows;
 //   * a result is copied to the caller's buffer (device or host) given at
 //     submission, then its server buffer is released.
 //
@@ -61,9 +65,11 @@ struct SlotGraphState {
   SsspWorkspace *sssp = nullptr;
   CcWorkspace *cc = nullptr;
   BatchWorkspace *batch = nullptr;
+  SsspWorkspace *sssp_batch = nullptr;  // for GraphEntry::sssp_lanes lanes
   ~SlotGraphState() {
     free_bfs(bfs);
     free_sssp(sssp);
+    free_sssp(sssp_batch);
     free_cc(cc);
     free_batch(batch);
   }
@@ -74,7 +80,13 @@ struct GraphEntry {
   // a BFS request is run as lanes of a batch when at least this many BFS
   // requests for the graph are queued (0: never batched)
   int32_t min_batch = 1;
+  // most SSSP requests one batched search takes (1: never batched)
+  int32_t sssp_lanes = 1;
 };
+
+// Scratch one slot's batched SSSP workspace may take on a graph; the lane
+// limit of the graph follows from it.
+constexpr size_t kSsspBatchBytes = size_t(4) << 30;
 
 }  // namespace
 
@@ -120,20 +132,23 @@ std::vector<uint64_t> take_batch(Server &S) {
     out.push_back(*it);
     S.in_use += need;
     S.queue.erase(it);
-    bool batch = false;
-    const int32_t min_batch = S.graphs[r.graph].min_batch;
-    if (r.kind == GR_QUERY_BFS && S.max_batch > 1 && min_batch > 0) {
+    // lanes the batch of r may have
+    int32_t cap = 1;
+    const GraphEntry &ge = S.graphs[r.graph];
+    if (r.kind == GR_QUERY_BFS && S.max_batch > 1 && ge.min_batch > 0) {
       int32_t queued = 1;  // r and the same-graph BFS requests behind it
-      for (auto jt = S.queue.begin(); jt != S.queue.end() && queued < min_batch; ++jt) {
+      for (auto jt = S.queue.begin(); jt != S.queue.end() && queued < ge.min_batch; ++jt) {
         const Request &q = S.reqs[*jt];
         if (q.kind == GR_QUERY_BFS && q.graph == r.graph) ++queued;
       }
-      batch = queued >= min_batch;
+      if (queued >= ge.min_batch) cap = S.max_batch;
+    } else if (r.kind == GR_QUERY_SSSP && S.max_batch > 1 && ge.min_batch > 0) {
+      cap = std::min(S.max_batch, ge.sssp_lanes);
     }
-    if (batch) {
-      for (auto jt = S.queue.begin(); jt != S.queue.end() && (int32_t)out.size() < S.max_batch;) {
+    if (cap > 1) {
+      for (auto jt = S.queue.begin(); jt != S.queue.end() && (int32_t)out.size() < cap;) {
         Request &q = S.reqs[*jt];
-        if (q.kind == GR_QUERY_BFS && q.graph == r.graph) {
+        if (q.kind == r.kind && q.graph == r.graph) {
           const size_t nq = S.result_bytes(q);
           if (S.resident + S.in_use + nq > S.budget) break;
           S.in_use += nq;
@@ -232,10 +247,12 @@ void Server::worker() {
     // the first request of a kind on a graph creates this slot's workspace
     // and captures its level-loop graph; slots do that one at a time
     std::unique_lock<std::mutex> setup(setup_mu, std::defer_lock);
-    const bool fresh = (first.kind == GR_QUERY_BFS && rs.size() > 1) ? !st.batch
-                       : first.kind == GR_QUERY_BFS                 ? !st.bfs
-                       : first.kind == GR_QUERY_SSSP                ? !st.sssp
-                                                                    : !st.cc;
+    const bool many = rs.size() > 1;
+    const bool fresh = (first.kind == GR_QUERY_BFS && many)    ? !st.batch
+                       : first.kind == GR_QUERY_BFS            ? !st.bfs
+                       : (first.kind == GR_QUERY_SSSP && many) ? !st.sssp_batch
+                       : first.kind == GR_QUERY_SSSP           ? !st.sssp
+                                                               : !st.cc;
     if (fresh) setup.lock();
     if (status == GR_OK) {
       if (first.kind == GR_QUERY_BFS && rs.size() > 1) {
@@ -255,6 +272,19 @@ void Server::worker() {
           ws_new += bfs_ws_bytes(g);
         }
         if (status == GR_OK) status = bfs_run(g, st.bfs, first.src, buf.as<int32_t>(), nullptr, o, s);
+      } else if (first.kind == GR_QUERY_SSSP && many) {
+        if (!st.sssp_batch) {
+          status = sssp_ws_create(g, s, &st.sssp_batch, ge.sssp_lanes);
+          ws_new += sssp_ws_bytes(g, ge.sssp_lanes);
+        }
+        if (status == GR_OK) {
+          std::vector<int32_t> srcs;
+          for (auto &r : rs) srcs.push_back(r.src);
+          // the CUDA-graph driver holds one-lane arguments: host-driven
+          // batches stand in for it (sssp_batch_run)
+          status = sssp_batch_run(g, st.sssp_batch, srcs.data(), (int32_t)srcs.size(),
+                                  buf.as<uint32_t>(), o, s);
+        }
       } else if (first.kind == GR_QUERY_SSSP) {
         if (!st.sssp) {
           status = sssp_ws_create(g, s, &st.sssp);
@@ -281,7 +311,7 @@ void Server::worker() {
       if (status == GR_OK && first.kind == GR_QUERY_BFS && rs.size() == 1)
         status = bfs_read_ctl_error(st.bfs, s);
       if (status == GR_OK && first.kind == GR_QUERY_SSSP)
-        status = sssp_read_ctl_error(st.sssp, s);
+        status = sssp_read_ctl_error(many ? st.sssp_batch : st.sssp, s);
     }
     if (status != GR_OK)
       err = std::string(gr_last_error()) + " [batch: kind " + std::to_string(first.kind) +
@@ -359,6 +389,11 @@ gr_status gr_server_add_graph(gr_server *srv, gr_graph *g, int32_t batchable,
   GraphEntry e;
   e.g = g;
   e.min_batch = batchable;
+  if (g->has_weights) {
+    const size_t per_lane = sssp_ws_bytes(g, 1) + sizeof(uint32_t) * (size_t)g->n;
+    const size_t by_mem = std::max<size_t>(1, kSsspBatchBytes / per_lane);
+    e.sssp_lanes = (int32_t)std::min<size_t>(by_mem, (size_t)sssp_batch_max_lanes(g));
+  }
   S.graphs.push_back(e);
   *graph_id = (int32_t)S.graphs.size() - 1;
   return GR_OK;

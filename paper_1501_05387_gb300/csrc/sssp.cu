@@ -28,6 +28,15 @@
 // bucket, i.e. plain frontier relaxation). Distances do not depend on delta.
 // An optional last pass fills pred[v] with the smallest u that has an edge
 // (u, v) with dist[u] + w = dist[v].
+//
+// Batched form (gr_sssp_batch): k sources run as ONE search over k disjoint
+// copies of the graph. Vertex id l*n + v stands for vertex v in copy
+// (lane) l: its row is row v of the CSR, its neighbours are l*n + C[e], and
+// dist / stamps / queues are indexed by the lane-major id. Copy l holds
+// only source l, and no edge joins two copies, so each lane's distances are
+// exactly those of a search from its own source; the lanes share the
+// threshold T and the device-side loop, so k high-diameter searches cost
+// about as many iterations as one.
 #include <algorithm>
 #include <cstring>
 
@@ -77,6 +86,7 @@ struct SsspArgs {
   const int32_t *C;
   const uint32_t *W;
   int32_t n;
+  int32_t nv;  // vertex ids in use: lanes * n (lane-major copies of the graph)
   long long m;
   int32_t *nearq[2];
   int32_t *nearS[2];
@@ -94,8 +104,11 @@ constexpr int kSsspBlocksPerSm = 5;
 // thread (mesh-like graphs), and the neighbours a thread loads at once.
 constexpr int32_t kSsspLowDegreeMax = 16;
 constexpr int kSsspTpvItems = 4;
+// Most sources one batched run takes.
+constexpr int32_t kSsspMaxLanes = 64;
 
 struct SsspWorkspace {
+  int32_t lanes = 1;  // copies of the graph the buffers hold (batched form)
   DevMem nearq[2], nearS[2], farq[2], stamp, far_stamp, ctl;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -113,28 +126,46 @@ namespace {
 
 __device__ __forceinline__ int32_t *pick(int32_t *const *a, int p) { return p ? a[1] : a[0]; }
 
-__global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pred,
+// First id of the graph copy that lane-major id x lies in (0 for one lane).
+__device__ __forceinline__ int32_t lane_base(int32_t x, int32_t n) {
+  return x >= n ? x - x % n : 0;
+}
+
+// Sources of one run: lane l starts at vertex s[l] (id l*n + s[l]).
+struct SsspSources {
+  int32_t k;
+  int32_t s[kSsspMaxLanes];
+};
+
+__global__ void k_sssp_init(SsspArgs a, SsspSources src, uint32_t *dist, int32_t *pred,
                             unsigned long long delta, int32_t max_iters) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = tid; v < a.n; v += stride) {
-    dist[v] = v == src ? 0u : 0xFFFFFFFFu;
+  for (int64_t v = tid; v < a.nv; v += stride) {
+    const int32_t x = (int32_t)v;
+    const int32_t base = lane_base(x, a.n);
+    dist[v] = x - base == src.s[base ? base / a.n : 0] ? 0u : 0xFFFFFFFFu;
     a.stamp[v] = -1;
     a.far_stamp[v] = -1;
   }
   if (tid == 0) {
     SsspCtl *c = a.ctl;
-    const int32_t dsrc = a.R[src + 1] - a.R[src];
-    a.nearq[0][0] = src;
-    a.nearS[0][0] = 0;
-    a.nearS[0][1] = dsrc;
+    // the initial near frontier: every lane's source with its degree scan
+    int32_t edges = 0;
+    for (int32_t l = 0; l < src.k; ++l) {
+      const int32_t u = src.s[l];
+      a.nearq[0][l] = l * a.n + u;
+      a.nearS[0][l] = edges;
+      edges += a.R[u + 1] - a.R[u];
+    }
+    a.nearS[0][src.k] = edges;
     c->dist = dist;
     c->pred = pred;
-    c->src = src;
+    c->src = src.s[0];
     c->mode = kSsspRelax;
     c->near_parity = 0;
     c->far_parity = 0;
-    c->near_len = 1;
+    c->near_len = src.k;
     c->far_len = 0;
     c->far_next_len = 0;
     c->done = 0;
@@ -150,7 +181,7 @@ __global__ void k_sssp_init(SsspArgs a, int32_t src, uint32_t *dist, int32_t *pr
     c->delta = delta;
     c->T = delta;
     c->T_old = 0;
-    c->near_edges = dsrc;
+    c->near_edges = edges;
     c->relaxations = 0;
     for (int i = 0; i < 3; ++i) {
       c->ring_near[i] = 0ull;
@@ -165,6 +196,7 @@ struct SsspSmem {
   int32_t off[kSsspChunk + 1];
   uint32_t du[kSsspChunk + 1];
   int32_t row[kSsspChunk + 1];
+  int32_t base[kSsspChunk + 1];  // first id of the vertex's graph copy
   ScannedBuf<kSsspChunk> nearb;
   AppendBuf<kSsspChunk> farb;
   int32_t i[2];
@@ -211,10 +243,12 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
     // once here instead of once per edge)
     for (int32_t k = threadIdx.x; k < nv; k += kSsspThreads) {
       const int32_t i = i0 + k;
-      const int32_t u0 = GR_IN(i, a.n + 1, 301) ? Q[i] : 0;
-      const int32_t u = GR_IN(u0, a.n, 303) ? u0 : 0;
-      sm.off[k] = GR_IN(i, a.n + 2, 302) ? S[i] : 0;
-      sm.row[k] = a.R[u];
+      const int32_t u0 = GR_IN(i, a.nv + 1, 301) ? Q[i] : 0;
+      const int32_t u = GR_IN(u0, a.nv, 303) ? u0 : 0;
+      const int32_t ub = lane_base(u, a.n);
+      sm.off[k] = GR_IN(i, a.nv + 2, 302) ? S[i] : 0;
+      sm.row[k] = a.R[u - ub];
+      sm.base[k] = ub;
       sm.du[k] = dist[u];
     }
     __syncthreads();
@@ -223,12 +257,14 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
     // degrees) for all of them before using any, so the latency chains of the
     // items overlap
     const int32_t ne = (int32_t)(j1 - j0);  // <= kSsspChunk: one pass
-    int32_t e[kSsspItems], v[kSsspItems], code[kSsspItems], dv[kSsspItems];
+    int32_t e[kSsspItems], v[kSsspItems], vl[kSsspItems], vb[kSsspItems], code[kSsspItems],
+        dv[kSsspItems];
     uint32_t wt[kSsspItems], du[kSsspItems], nd[kSsspItems], cur[kSsspItems];
 #pragma unroll
     for (int j = 0; j < kSsspItems; ++j) {
       const int32_t k = j * kSsspThreads + threadIdx.x;
       e[j] = -1;
+      vb[j] = 0;
       du[j] = 0xFFFFFFFFu;
       if (k < ne) {
         const int32_t er = (int32_t)(j0 + k);
@@ -241,19 +277,21 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
         const int32_t ee = sm.row[lo] + (er - sm.off[lo]);
         if (GR_IN(ee, a.m, 304)) {
           e[j] = ee;
+          vb[j] = sm.base[lo];
           du[j] = sm.du[lo];
         }
       }
     }
 #pragma unroll
     for (int j = 0; j < kSsspItems; ++j) {
-      v[j] = e[j] >= 0 ? a.C[e[j]] : -1;
+      vl[j] = e[j] >= 0 ? a.C[e[j]] : -1;
       wt[j] = e[j] >= 0 ? a.W[e[j]] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < kSsspItems; ++j) {
       nd[j] = 0xFFFFFFFFu;  // not representable below 0xFFFFFFFF: no improvement
-      if (v[j] >= 0 && !GR_IN(v[j], a.n, 305)) v[j] = -1;
+      if (vl[j] >= 0 && !GR_IN(vl[j], a.n, 305)) vl[j] = -1;
+      v[j] = vl[j] >= 0 ? vb[j] + vl[j] : -1;  // the neighbour in the same copy
       if (v[j] >= 0) {
         const unsigned long long t = (unsigned long long)du[j] + wt[j];
         if (t < 0xFFFFFFFFull) nd[j] = (uint32_t)t;
@@ -282,13 +320,13 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
     }
 #pragma unroll
     for (int j = 0; j < kSsspItems; ++j)
-      dv[j] = code[j] == 1 ? a.R[v[j] + 1] - a.R[v[j]] : 0;
+      dv[j] = code[j] == 1 ? a.R[vl[j] + 1] - a.R[vl[j]] : 0;
 #pragma unroll
     for (int j = 0; j < kSsspItems; ++j) {
       emit_scanned(sm.nearb, code[j] == 1, v[j], dv[j]);
       emit_plain(sm.farb, code[j] == 2, v[j]);
     }
-    flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.n + 1);
+    flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.nv + 1);
     flush_plain<kSsspThreads>(sm.farb, st.far_ctr, st.far_dest, st.far_cap);
   }
 }
@@ -311,13 +349,14 @@ __device__ void relax_body_thread(const SsspArgs &a, uint32_t *dist, const SsspS
   const int64_t qr = ((int64_t)q + 31) & ~31ll;  // warp-uniform bound
   uint32_t local_min = 0xFFFFFFFFu;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < qr; i += stride) {
-    int32_t u = 0, r0 = 0, r1 = 0;
+    int32_t u = 0, ub = 0, r0 = 0, r1 = 0;
     uint32_t du = 0xFFFFFFFFu;
-    if (i < q && GR_IN(i, a.n + 1, 320)) {
+    if (i < q && GR_IN(i, a.nv + 1, 320)) {
       u = Q[i];
-      if (GR_IN(u, a.n, 321)) {
-        r0 = a.R[u];
-        r1 = a.R[u + 1];
+      if (GR_IN(u, a.nv, 321)) {
+        ub = lane_base(u, a.n);
+        r0 = a.R[u - ub];
+        r1 = a.R[u - ub + 1];
         du = dist[u];
       }
     }
@@ -341,9 +380,10 @@ __device__ void relax_body_thread(const SsspArgs &a, uint32_t *dist, const SsspS
         dv[j] = 0u;
         d0[j] = d1[j] = 0;
         if (v[j] >= 0) {
-          dv[j] = dist[v[j]];
           d0[j] = a.R[v[j]];
           d1[j] = a.R[v[j] + 1];
+          v[j] += ub;  // from here on: the neighbour's id in u's copy
+          dv[j] = dist[v[j]];
         }
       }
       uint32_t ncnt = 0, ndeg = 0, fcnt = 0;
@@ -399,7 +439,7 @@ __device__ void relax_body_thread(const SsspArgs &a, uint32_t *dist, const SsspS
 #pragma unroll
       for (int j = 0; j < kSsspTpvItems; ++j) {
         if (code[j] == 1) {
-          if (GR_IN(kn, a.n + 1, 324)) Qn[kn] = v[j];
+          if (GR_IN(kn, a.nv + 1, 324)) Qn[kn] = v[j];
           ++kn;
         } else if (code[j] == 2) {
           if (GR_IN(kf, st.far_cap, 325)) st.far_dest[kf] = v[j];
@@ -428,7 +468,7 @@ __device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm
     const long long i = (r * gridDim.x + blockIdx.x) * kSsspThreads + threadIdx.x;
     int code = 0;
     int32_t v = 0, dv = 0;
-    if (i < len && GR_IN(i, a.n + 1, 310) && GR_IN(F[i], a.n, 311)) {
+    if (i < len && GR_IN(i, a.nv + 1, 310) && GR_IN(F[i], a.nv, 311)) {
       v = F[i];
       const uint32_t d = dist[v];
       if ((unsigned long long)d < T_old) {
@@ -436,7 +476,8 @@ __device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm
       } else if ((unsigned long long)d < T) {
         if (atomicExch(a.stamp + v, iter) != iter) {
           code = 1;
-          dv = a.R[v + 1] - a.R[v];
+          const int32_t vl = v - lane_base(v, a.n);
+          dv = a.R[vl + 1] - a.R[vl];
         }
       } else {
         local_min = min(local_min, d);
@@ -446,7 +487,7 @@ __device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm
     emit_scanned(sm.nearb, code == 1, v, dv);
     emit_plain(sm.farb, code == 2, v);
     if ((r + 1) % (kSsspChunk / kSsspThreads) == 0 || r == rounds - 1) {
-      flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.n + 1);
+      flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.nv + 1);
       flush_plain<kSsspThreads>(sm.farb, st.far_ctr, st.far_dest, st.far_cap);
     }
   }
@@ -469,7 +510,7 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   st.near_ctr = &c->near_next_packed;
   st.far_ctr = &c->far_len;  // absolute positions in the current pile
   st.far_dest = pick(a.farq, c->far_parity);
-  st.far_cap = a.n + 1;
+  st.far_cap = (long long)a.nv + 1;
   st.fmin = &c->far_min;
   if (LOW) relax_body_thread(a, c->dist, st);
   else relax_body(a, c->dist, sm, st);
@@ -489,7 +530,7 @@ __device__ void split_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   st.near_ctr = &c->near_next_packed;
   st.far_ctr = &c->far_next_len;
   st.far_dest = pick(a.farq, c->far_parity ^ 1);
-  st.far_cap = a.n + 1;
+  st.far_cap = (long long)a.nv + 1;
   st.fmin = &c->far_min_next;
   split_body(a, c->dist, sm, st);
 }
@@ -596,7 +637,7 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
   uint32_t *dist = c->dist;
   const unsigned long long delta = c->delta;
   const int32_t max_iters = c->max_iters;
-  int32_t mode = kSsspRelax, near_parity = 0, far_parity = 0, near_len = 1, far_len = 0;
+  int32_t mode = kSsspRelax, near_parity = 0, far_parity = 0, near_len = c->near_len, far_len = 0;
   long long near_edges = c->near_edges, relaxations = 0;
   int32_t iter = 0, far_epoch = 0, phases = 0, gen = 0;
   uint32_t far_min = 0xFFFFFFFFu;
@@ -623,12 +664,12 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
     st.fmin = &c->ring_fmin[slot];
     if (mode == kSsspRelax) {
       st.far_dest = pick(a.farq, far_parity) + far_len;  // appended after the pile
-      st.far_cap = (long long)a.n + 1 - far_len;
+      st.far_cap = (long long)a.nv + 1 - far_len;
       if (LOW) relax_body_thread(a, dist, st);
       else relax_body(a, dist, sm, st);
     } else {
       st.far_dest = pick(a.farq, far_parity ^ 1);
-      st.far_cap = a.n + 1;
+      st.far_cap = (long long)a.nv + 1;
       split_body(a, dist, sm, st);
     }
     if (!grid_sync(&c->bar, &c->error, gen)) break;  // a wait gave up: error is set
@@ -709,15 +750,27 @@ __global__ void k_sssp_pred_fin(int32_t *pred, int32_t n, int32_t src) {
 
 }  // namespace
 
-size_t sssp_ws_bytes(const gr_graph *g) {
-  const size_t n = (size_t)g->n;
+size_t sssp_ws_bytes(const gr_graph *g, int32_t lanes) {
+  const size_t n = (size_t)g->n * (size_t)std::max(lanes, 1);
   return 4 * sizeof(int32_t) * (n + 1) + 2 * sizeof(int32_t) * (n + 2) +
          2 * sizeof(int32_t) * n + sizeof(SsspCtl);
 }
 
-gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out) {
+int32_t sssp_batch_max_lanes(const gr_graph *g) {
+  // lane-major ids and queue positions (up to lanes * n + 1), and a
+  // frontier's edge count (up to lanes * m), are int32
+  long long k = kSsspMaxLanes;
+  k = std::min<long long>(k, (INT32_MAX - 2) / std::max<int32_t>(g->n, 1));
+  if (g->m > 0) k = std::min<long long>(k, INT32_MAX / g->m);
+  return (int32_t)std::max<long long>(k, 1);
+}
+
+gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out, int32_t lanes) {
+  if (lanes < 1 || lanes > sssp_batch_max_lanes(g))
+    return fail(GR_EINVAL, "SSSP workspace: lane count out of range for this graph");
   std::unique_ptr<SsspWorkspace> ws(new SsspWorkspace());
-  const size_t n = (size_t)g->n;
+  ws->lanes = lanes;
+  const size_t n = (size_t)g->n * (size_t)lanes;
   for (int i = 0; i < 2; ++i) {
     GR_TRY(ws->nearq[i].alloc(sizeof(int32_t) * (n + 1), "SSSP near queue"));
     GR_TRY(ws->nearS[i].alloc(sizeof(int32_t) * (n + 2), "SSSP near degree scan"));
@@ -732,12 +785,13 @@ gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out) {
   return GR_OK;
 }
 
-static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws) {
+static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws, int32_t lanes = 1) {
   SsspArgs a;
   a.R = g->row_off.as<int32_t>();
   a.C = g->col.as<int32_t>();
   a.W = g->w.as<uint32_t>();
   a.n = g->n;
+  a.nv = g->n * lanes;
   a.m = g->m;
   for (int i = 0; i < 2; ++i) {
     a.nearq[i] = ws->nearq[i].as<int32_t>();
@@ -807,19 +861,9 @@ gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o) {
   return GR_OK;
 }
 
-// SSSP into device outputs with an explicit workspace (no locking, no
-// staging): the public gr_sssp and the query server both call this.
-gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, int32_t *pred,
-                   const gr_opts &o, cudaStream_t s) {
-  const unsigned long long delta =
-      o.delta == UINT32_MAX ? (1ull << 40) : (o.delta ? o.delta : g->sssp_delta);
-  const int32_t max_iters = o.max_iters > 0
-                                ? o.max_iters
-                                : (int32_t)std::min<long long>(INT32_MAX, 8ll * g->n + 1024);
-  SsspArgs a = sssp_args(g, ws);
-  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, src, dist, pred, delta, max_iters);
-  GR_CUDA(cudaGetLastError());
-  const int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
+// Runs the device-side loop of an initialised search with the given driver.
+static gr_status sssp_drive(gr_graph *g, SsspWorkspace *ws, SsspArgs a, int32_t mode,
+                            const gr_opts &o, int32_t max_iters, cudaStream_t s) {
   if (mode == GR_MODE_PERSISTENT) {
     int per_sm = 0;
     void *kern = a.low_degree ? (void *)k_sssp_do<true> : (void *)k_sssp_do<false>;
@@ -845,6 +889,32 @@ gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, 
     GR_TRY(build_sssp_graph(g, ws));
     GR_CUDA(cudaGraphLaunch(ws->exec, s));
   }
+  return GR_OK;
+}
+
+static unsigned long long sssp_delta_of(const gr_graph *g, const gr_opts &o) {
+  return o.delta == UINT32_MAX ? (1ull << 40) : (o.delta ? o.delta : g->sssp_delta);
+}
+
+static int32_t sssp_max_iters_of(const gr_graph *g, const gr_opts &o) {
+  return o.max_iters > 0 ? o.max_iters
+                         : (int32_t)std::min<long long>(INT32_MAX, 8ll * g->n + 1024);
+}
+
+// SSSP into device outputs with an explicit workspace (no locking, no
+// staging): the public gr_sssp and the query server both call this.
+gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, int32_t *pred,
+                   const gr_opts &o, cudaStream_t s) {
+  const unsigned long long delta = sssp_delta_of(g, o);
+  const int32_t max_iters = sssp_max_iters_of(g, o);
+  SsspArgs a = sssp_args(g, ws);
+  SsspSources one;
+  one.k = 1;
+  one.s[0] = src;
+  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, one, dist, pred, delta, max_iters);
+  GR_CUDA(cudaGetLastError());
+  const int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
+  GR_TRY(sssp_drive(g, ws, a, mode, o, max_iters, s));
   if (pred) {
     const int grid = g->num_sms * 8;
     k_sssp_pred_init<<<grid, 256, 0, s>>>(pred, g->n);
@@ -853,6 +923,25 @@ gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, 
     GR_CUDA(cudaGetLastError());
   }
   return GR_OK;
+}
+
+// k searches as one over k copies of the graph into dist[k][n] (device).
+// The CUDA-graph driver holds one-lane arguments, so every driver but the
+// persistent kernel becomes the host-driven loop here.
+gr_status sssp_batch_run(gr_graph *g, SsspWorkspace *ws, const int32_t *h_srcs, int32_t k,
+                         uint32_t *dist, const gr_opts &o, cudaStream_t s) {
+  if (k < 1 || k > ws->lanes) return fail(GR_EINVAL, "batched SSSP: k exceeds the workspace");
+  const unsigned long long delta = sssp_delta_of(g, o);
+  const int32_t max_iters = sssp_max_iters_of(g, o);
+  SsspArgs a = sssp_args(g, ws, k);
+  SsspSources srcs;
+  srcs.k = k;
+  for (int32_t l = 0; l < kSsspMaxLanes; ++l) srcs.s[l] = l < k ? h_srcs[l] : 0;
+  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, srcs, dist, nullptr, delta, max_iters);
+  GR_CUDA(cudaGetLastError());
+  int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
+  if (mode != GR_MODE_PERSISTENT) mode = GR_MODE_LAUNCH;
+  return sssp_drive(g, ws, a, mode, o, max_iters, s);
 }
 
 }  // namespace gr
@@ -884,6 +973,55 @@ gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
     GR_CUDA(cudaMemcpyAsync(pred, d_pred, sizeof(int32_t) * (size_t)g->n,
                             cudaMemcpyDeviceToHost, s));
   GR_TRY(end_call(g, s));
+  return GR_OK;
+}
+
+gr_status gr_sssp_batch(gr_graph *g, const int32_t *srcs, int32_t k, uint32_t *dist,
+                        const gr_opts *opts, void *stream) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (!srcs || !dist) return fail(GR_EINVAL, "srcs/dist must not be NULL");
+  const int32_t kmax = sssp_batch_max_lanes(g);
+  if (k < 1 || k > kmax)
+    return fail(GR_EINVAL, "k must be in [1, " + std::to_string(kmax) +
+                               "] (64, and k*n and k*m must fit in int32)");
+  const gr_opts &o = opts ? *opts : default_opts();
+  for (int32_t i = 0; i < k; ++i) GR_TRY(sssp_check(g, srcs[i], o));
+  std::lock_guard<std::mutex> lock(g->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  GR_TRY(begin_call(g, s));
+  if (g->sssp_batch && g->sssp_batch->lanes < k) {
+    // the old buffers may still be in use by enqueued work
+    GR_CUDA(cudaStreamSynchronize(s));
+    free_sssp(g->sssp_batch);
+    g->sssp_batch = nullptr;
+  }
+  if (!g->sssp_batch) GR_TRY(sssp_ws_create(g, s, &g->sssp_batch, k));
+  void *d_dist;
+  bool cp;
+  const size_t bytes = sizeof(uint32_t) * (size_t)k * (size_t)g->n;
+  GR_TRY(resolve_output(g, 0, dist, bytes, &d_dist, &cp));
+  GR_TRY(sssp_batch_run(g, g->sssp_batch, srcs, k, (uint32_t *)d_dist, o, s));
+  if (cp) GR_CUDA(cudaMemcpyAsync(dist, d_dist, bytes, cudaMemcpyDeviceToHost, s));
+  GR_TRY(end_call(g, s));
+  return GR_OK;
+}
+
+gr_status gr_sssp_batch_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
+                              int64_t *relaxations) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (!g->sssp_batch) return fail(GR_EINVAL, "no batched SSSP has run on this graph");
+  std::lock_guard<std::mutex> lock(g->mu);
+  GR_CUDA(cudaSetDevice(g->device));
+  if (g->has_last) GR_CUDA(cudaEventSynchronize(g->last_done));
+  SsspCtl h;
+  GR_CUDA(cudaMemcpy(&h, g->sssp_batch->ctl.p, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
+  if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "iteration limit reached");
+  if (iterations) *iterations = h.iter;
+  if (phases) *phases = h.phases;
+  if (relaxations) *relaxations = h.relaxations;
   return GR_OK;
 }
 

@@ -71,6 +71,8 @@ _sig("gr_bfs_trace", [_vp, _i32, _vp, _vp, _vp, _vp, _P(_i32)])
 _sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_sssp_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("gr_bfs_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
+_sig("gr_sssp_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
+_sig("gr_sssp_batch_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("gr_bc", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_autotune", [_vp, _vp, _i32, _i32, _vp])
 _sig("gr_tuned_opts", [_vp, _P(gr_opts), _P(ctypes.c_double), _P(ctypes.c_double)])
@@ -259,6 +261,23 @@ def gr_sssp_stats(g: Graph):
     rl = _i64()
     _check(_lib.gr_sssp_stats(g.handle, ctypes.byref(it), ctypes.byref(ph), ctypes.byref(rl)),
            "gr_sssp_stats")
+    return it.value, ph.value, rl.value
+
+
+def gr_sssp_batch(g: Graph, srcs, dist, opts=None, stream=None):
+    """k SSSP searches (k = len(srcs), up to 64) in one run into dist[k*n]
+    (uint32, source-major; torch.int32 tensors hold the same bits)."""
+    srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    _check(_lib.gr_sssp_batch(g.handle, srcs.ctypes.data if srcs.size else None,
+                              int(srcs.size), _ptr(dist, np.uint32), _opts(opts),
+                              _stream(stream)), "gr_sssp_batch")
+
+
+def gr_sssp_batch_stats(g: Graph):
+    it, ph = _i32(), _i32()
+    rl = _i64()
+    _check(_lib.gr_sssp_batch_stats(g.handle, ctypes.byref(it), ctypes.byref(ph),
+                                    ctypes.byref(rl)), "gr_sssp_batch_stats")
     return it.value, ph.value, rl.value
 
 

@@ -103,4 +103,5 @@ def test_batch_and_bc_reject_bad_arguments(gr):
     d = np.zeros(4, np.int32)
     assert gr._lib.gr_bfs_batch(None, srcs.ctypes.data, 1, d.ctypes.data, None, None) == gr.GR_EINVAL
     assert gr._lib.gr_bc(None, srcs.ctypes.data, 1, d.ctypes.data, None, None) == gr.GR_EINVAL
+    assert gr._lib.gr_sssp_batch(None, srcs.ctypes.data, 1, d.ctypes.data, None, None) == gr.GR_EINVAL
     assert gr._lib.gr_bfs_noalloc(0, 0, None, None, 0, None, None, None) == gr.GR_EINVAL

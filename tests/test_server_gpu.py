@@ -1,6 +1,6 @@
-"""Query server: every result served in the mix (batched, admitted under a
-memory budget, with several slots overlapped on several streams) equals the
-same query run alone, bit for bit."""
+"""Query server: every result served in the mix (BFS and SSSP batched,
+admitted under a memory budget, with several slots overlapped on several
+streams) equals the same query run alone, bit for bit."""
 import os
 
 import numpy as np
@@ -125,6 +125,26 @@ def test_batching_depth(cuda_lib, pool, depth, batched):
     assert (st["launches"] < len(srcs)) == batched
     for s, o in zip(srcs, outs):
         assert np.array_equal(o.cpu().numpy(), alone(gr, g, gr.GR_QUERY_BFS, s))
+
+
+@pytest.mark.parametrize("gi", [1, 3])
+def test_sssp_batching(cuda_lib, pool, gi):
+    """Queued same-graph SSSP requests run as lanes of one batched search
+    (an R-MAT graph and the grid); results equal the queries alone."""
+    gr = cuda_lib
+    g = pool[gi][0]
+    srcs = [(i * 53) % g.n for i in range(30)]
+    outs = [np.full(g.n, -7, np.int32) for _ in srcs]
+    with gr.gr_server_create(1 << 30, 1, 64) as srv:
+        gid = gr.gr_server_add_graph(srv, g, 8)
+        for s, o in zip(srcs, outs):
+            gr.gr_server_submit(srv, gid, gr.GR_QUERY_SSSP, s, o)
+        gr.gr_server_drain(srv, 120000)
+        st = gr.gr_server_stats(srv)
+    assert st["completed"] == len(srcs) and st["failed"] == 0
+    assert st["launches"] < len(srcs) and st["mean_batch"] > 1.0
+    for s, o in zip(srcs, outs):
+        assert np.array_equal(o, alone(gr, g, gr.GR_QUERY_SSSP, s))
 
 
 def test_bad_requests(cuda_lib, pool):

@@ -153,3 +153,127 @@ def test_rmat_s22_sampled_sources(cuda_lib):
             d, p = run_sssp(cuda_lib, g, int(s))
             assert np.array_equal(d, ref_d)
             assert np.array_equal(p, ref_p)
+
+
+# ------------------------------------------------------- batched searches
+# gr_sssp_batch runs k searches as one near/far search over k disjoint copies
+# of the graph; every lane must equal Dijkstra from its own source.
+
+def run_batch(gr, g, srcs, o=None):
+    import torch
+    k = len(srcs)
+    dist = torch.empty(k * g.n, dtype=torch.int32, device="cuda")
+    gr.gr_sssp_batch(g, srcs, dist, o)
+    torch.cuda.synchronize()
+    gr.gr_sssp_batch_stats(g)  # raises on a device-side cap or timeout
+    return dist.cpu().numpy().view(np.uint32).reshape(k, g.n)
+
+
+def check_batch(gr, r, c, w, g, srcs, o=None, cache=None, d=None):
+    if d is None:
+        d = run_batch(gr, g, srcs, o)
+    cache = {} if cache is None else cache
+    for lane, s in enumerate(srcs):
+        s = int(s)
+        if s not in cache:
+            cache[s] = oracle.sssp(r, c, w, s)[0]
+        bad = np.nonzero(d[lane] != cache[s])[0]
+        assert bad.size == 0, (f"lane {lane} (source {s}): dist mismatch at {bad[:10]}: "
+                               f"{d[lane][bad[:10]]} vs {cache[s][bad[:10]]}")
+
+
+@pytest.fixture(scope="module")
+def s14_sources(s14w):
+    r = s14w[0]
+    isolated = int(np.nonzero(np.diff(r) == 0)[0][0])
+    top = int(gg.max_degree_vertex(r))
+    # 64 lanes: a repeated source and an isolated one among them
+    return [top, isolated] + [int(x) for x in gg.sources(r, 61, seed=11)] + [top]
+
+
+@pytest.mark.parametrize("delta", [0, 1, 0xFFFFFFFF])
+@pytest.mark.parametrize("mode", ["launch", "graph", "persistent"])
+def test_batch_rmat_s14(cuda_lib, s14w, s14_sources, delta, mode):
+    r, c, w, g = s14w
+    cache = {}
+    for k in (1, 5, 64):
+        check_batch(cuda_lib, r, c, w, g, s14_sources[:k], opts(cuda_lib, delta, mode), cache)
+
+
+@pytest.mark.parametrize("mode", ["launch", "persistent"])
+def test_batch_grid_low_degree(cuda_lib, mode):
+    """A mesh (maximum degree 4: one thread per frontier vertex) with 5 %
+    of its edges deleted; corners, centre and random sources."""
+    side = 64
+    r, c = gg.grid(side, p_del=0.05, seed=4)
+    w = gg.weights(r, c, seed=5, wmin=1, wmax=16)
+    srcs = [0, side - 1, side * side - 1, side * side // 2 + side // 2]
+    srcs += [int(x) for x in gg.sources(r, 12, seed=8)]
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        cache = {}
+        for delta in (0, 1, 16):
+            check_batch(cuda_lib, r, c, w, g, srcs, opts(cuda_lib, delta, mode), cache)
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 257])
+def test_batch_ragged_paths(cuda_lib, n):
+    r, c = gg.from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    w = gg.weights(r, c, seed=n, wmin=1, wmax=64)
+    srcs = sorted({0, n // 2, n - 1}) + [0]
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for mode in ("launch", "persistent"):
+            check_batch(cuda_lib, r, c, w, g, srcs, opts(cuda_lib, 4, mode))
+
+
+def test_batch_directed_zero_weights_and_disconnected(cuda_lib):
+    # directed, with a zero-weight edge and an unreachable part (5, 6)
+    r = np.array([0, 2, 3, 4, 5, 5, 6, 6], np.int32)
+    c = np.array([1, 2, 3, 1, 0, 6], np.int32)
+    w = np.array([9, 0, 1, 3, 1, 7], np.uint32)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        check_batch(cuda_lib, r, c, w, g, list(range(7)))
+
+
+def test_batch_equals_single_rmat_s16(cuda_lib):
+    """24 lanes on a larger graph (merge-path relaxation over several chunks
+    per iteration) against gr_sssp one source at a time and Dijkstra."""
+    import torch
+    r, c = gg.rmat(16, 16, seed=9)
+    w = gg.weights(r, c, seed=10)
+    srcs = [int(x) for x in gg.sources(r, 24, seed=12)]
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        d = run_batch(cuda_lib, g, srcs)
+        for lane, s in enumerate(srcs[:6]):
+            one, _ = run_sssp(cuda_lib, g, s, with_pred=False)
+            assert np.array_equal(d[lane], one)
+        check_batch(cuda_lib, r, c, w, g, srcs, d=d)
+        torch.cuda.synchronize()
+
+
+def test_batch_host_output_and_regrow(cuda_lib, s14w, s14_sources):
+    """Host (pageable) output; the workspace grows from 4 to 16 lanes and is
+    reused for 2."""
+    import torch
+    r, c, w, g = s14w
+    cache = {}
+    h = np.full(4 * g.n, 7, np.uint32)
+    cuda_lib.gr_sssp_batch(g, s14_sources[:4], h)
+    torch.cuda.synchronize()
+    check_batch(cuda_lib, r, c, w, g, s14_sources[:4], cache=cache, d=h.reshape(4, g.n))
+    check_batch(cuda_lib, r, c, w, g, s14_sources[10:26], cache=cache)
+    check_batch(cuda_lib, r, c, w, g, s14_sources[30:32], cache=cache)
+
+
+def test_batch_bad_arguments(cuda_lib, s14w):
+    import torch
+    r, c, w, g = s14w
+    d = torch.empty(65 * g.n, dtype=torch.int32, device="cuda")
+    for srcs in ([], list(range(65)), [0, g.n], [-1]):
+        with pytest.raises(cuda_lib.GrError) as ei:
+            cuda_lib.gr_sssp_batch(g, srcs, d)
+        assert ei.value.status == cuda_lib.GR_EINVAL
+    r2, c2 = gg.from_edges(3, [(0, 1)])
+    with cuda_lib.gr_graph_create(r2, c2) as g2:
+        with pytest.raises(cuda_lib.GrError) as ei:
+            cuda_lib.gr_sssp_batch(g2, [0], d)
+        assert ei.value.status == cuda_lib.GR_EINVAL
