@@ -70,8 +70,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving", action="store_true",
-                    help="also run the query-server benchmark (plain vs continuous batching)")
-    ap.add_argument("--serving-requests", type=int, default=2000)
+                    help="run the query-server benchmark (plain vs continuous batching) also "
+                         "with more than one rank (at N=1 it runs unless --no-serving)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the query-server benchmark")
+    ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--serving-slots", type=int, default=1,
                     help="worker slots of the served path (device work of several slots "
                          "overlaps on separate streams)")
@@ -442,13 +445,14 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
                                   "row offset, 8 B depth+parent per reached vertex")})
     # SSSP bucket width and driver tuned once on two sample sources
     gr.gr_autotune(g, [int(srcs[0]), int(srcs[1])], gr.GR_TUNE_SSSP)
-    per, byts, iters = [], [], []
+    per, byts, iters, single = [], [], [], []
     dist_g = torch.empty(n, dtype=torch.int32, device=dev)
     for s in srcs[:2]:
         ms, _ = _timed_calls(lambda: gr.gr_sssp(g, int(s), dist_g), 1, flush)
         iters.append(gr.gr_sssp_stats(g)[0])
         per.append(ms)
-        byts.append(reach_bytes(r, dist_g.cpu().numpy().view(np.uint32) != INF, 8, 4))
+        single.append(dist_g.cpu().numpy().view(np.uint32).copy())
+        byts.append(reach_bytes(r, single[-1] != INF, 8, 4))
     mean = float(np.mean(per))
     out.append({"workload": "grid4096_sssp", "primitive": "sssp", "calls": 2,
                 "tuned_delta": gr.gr_tuned_opts(g)["delta"],
@@ -458,6 +462,22 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
                                   "8 B per column+weight entry of the reached vertices, "
                                   "4 B per row offset, 4 B per reached distance")})
+    # the same searches batched: 16 sources (the two above first) as one
+    # search over 16 copies of the graph
+    k = 16
+    srcs_k = [int(x) for x in srcs[:2]] + [int(x) for x in gg.sources(r, k + 2, seed=14)
+                                           if int(x) not in (int(srcs[0]), int(srcs[1]))][:k - 2]
+    dist_k = torch.empty(k * n, dtype=torch.int32, device=dev)
+    ms_k, _ = _timed_calls(lambda: gr.gr_sssp_batch(g, srcs_k, dist_k), 1, flush)
+    it_k = gr.gr_sssp_batch_stats(g)[0]
+    dk = dist_k.cpu().numpy().view(np.uint32).reshape(k, n)
+    out.append({"workload": f"grid4096_sssp_batch{k}", "primitive": "sssp (batched)",
+                "calls": 1, "sources": k, "ms_per_call": ms_k, "ms_per_source": ms_k / k,
+                "queries_per_s": k / (ms_k * 1e-3),
+                "speedup_vs_single": (k / ms_k) / (1.0 / mean), "iterations": it_k,
+                "lanes_equal_single": [bool(np.array_equal(dk[i], single[i])) for i in range(2)],
+                "throughput": k * m / (ms_k * 1e-3) / 1e9, "unit": "GTEPS (k*m per call)"})
+    del dist_k
     label = torch.empty(n, dtype=torch.int32, device=dev)
     ms, _ = _timed_calls(lambda: gr.gr_cc(g, label, count=False), 3, flush)
     out.append({"workload": "grid4096_cc", "primitive": "cc", "calls": 3, "ms_per_call": ms,
@@ -726,12 +746,15 @@ def run_gr(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(r, c, srcs, m, args.cpu_sample_sources)
     serving = None
-    if rank == 0 and args.serving:
+    if rank == 0 and not args.no_serving and (args.serving or world == 1):
         g.close()
         g = None
-        serving = serving_bench(gr, full=args.serving_full,
-                                count=20000 if args.serving_full else args.serving_requests,
-                                slots=args.serving_slots)
+        try:
+            serving = serving_bench(gr, full=args.serving_full,
+                                    count=20000 if args.serving_full else args.serving_requests,
+                                    slots=args.serving_slots)
+        except Exception as e:  # the BFS line is still reported
+            serving = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
