@@ -288,7 +288,12 @@ def serving_bench(gr, full=False, count=2000, slots=1):
             src = [int(np.argmax(np.diff(r)))]
             gr.gr_autotune(g, src, gr.GR_TUNE_BFS | gr.GR_TUNE_SSSP)
         reqs, unit = serving_requests(pool, count)
-        budget = 16 << 30
+        # the budget covers result buffers and the slots' kept workspaces;
+        # with batching those reach about 6 GB on the 6-graph subset and
+        # about 40 GB on the 24-graph pool (batched SSSP scratch on the
+        # 2048^2 and 4096^2 grids), past which admission could no longer
+        # batch
+        budget = (64 << 30) if full else (16 << 30)
         warm = [(gi, k, int(np.argmax(np.diff(pool[gi][4]))))
                 for gi in range(len(pool)) for k in range(3)]
         for sl, batch in [(1, 1), (slots, 64)]:
