@@ -7,9 +7,10 @@
 //   * a worker thread per slot owns a CUDA stream and, per graph, its own
 //     scratch workspaces, so queries on different slots overlap on the GPU;
 //   * admission is by a device-memory budget: a request is started only
-//     when its result buffer (plus any workspace its slot still has to
-//     create) fits in what the in-flight requests leave free; the memory
-//     footprint follows the paper's alpha*|E| + beta*|V| model (Sec. 6);
+//     when its result buffer fits in what the in-flight requests' buffers
+//     and the workspaces the slots keep leave free (the oldest request
+//     always starts when nothing is in flight); the memory footprint
+//     follows the paper's alpha*|E| + beta*|V| model (Sec. 6);
 //   * same-graph BFS requests are batched: a worker that takes a BFS request
 //     also takes up to max_batch - 1 further queued BFS requests for that
 //     graph (in arrival order) and runs them as bit lanes of one batched
