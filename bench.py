@@ -34,8 +34,8 @@ METRIC = "BFS GTEPS (R-MAT s22, 16 sources)"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic of one traversal (k_bfs_init + k_bfs_do), from one ncu capture
-# of the 16 timed traversals at R-MAT s21 (cold caches; the command and the
-# numbers are in profiles/k_bfs_do_rmat21_full.md), scaled to other scales by
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the 16 timed traversals
+# of this benchmark at R-MAT s21 with cold caches, scaled to other scales by
 # the edge count. It is reported only while the traversal's sources hash to
 # the value they had when it was measured (null after any change).
 TRAFFIC_S21 = {"bytes_per_traversal": 44861376, "m": 63540402,
@@ -75,9 +75,6 @@ def parse():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the query-server benchmark")
     ap.add_argument("--serving-requests", type=int, default=1000)
-    ap.add_argument("--serving-slots", type=int, default=1,
-                    help="worker slots of the served path (device work of several slots "
-                         "overlaps on separate streams)")
     ap.add_argument("--serving-full", action="store_true",
                     help="serve 20000 requests over the 24-graph pool (slow)")
     ap.add_argument("--suite", action="store_true",
@@ -271,10 +268,12 @@ def run_serving(gr, graphs, batchable, reqs, unit_arrivals, rate, slots, batch, 
         srv.close()
 
 
-def serving_bench(gr, full=False, count=2000, slots=1):
-    """Plain path (one slot, no batching) vs served path (`slots` slots,
-    continuous batching of up to 64 BFS or SSSP lanes per launch) on the same
-    seeded request stream. Every phase must complete all its requests."""
+def serving_bench(gr, full=False, count=2000):
+    """Plain path (no batching) vs served path (continuous batching of up to
+    64 BFS or SSSP lanes per launch) on the same seeded request stream, both
+    on the server's one worker slot. Every phase must complete all its
+    requests."""
+    slots = 1
     pool = serving_pool(full)
     graphs = [gr.gr_graph_create(r, c, w) for (_, _, _, _, r, c, w) in pool]
     try:
@@ -756,8 +755,7 @@ def run_gr(args):
         g = None
         try:
             serving = serving_bench(gr, full=args.serving_full,
-                                    count=20000 if args.serving_full else args.serving_requests,
-                                    slots=args.serving_slots)
+                                    count=20000 if args.serving_full else args.serving_requests)
         except Exception as e:  # the BFS line is still reported
             serving = {"error": f"{type(e).__name__}: {e}"}
 

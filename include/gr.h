@@ -233,21 +233,28 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc,
  * code running while a CUDA stream is being captured into a graph (an
  * allocation there breaks the capture), hosts whose device memory is owned
  * by their own allocator or pool, and real-time loops that forbid
- * allocation after start-up. The paper has no counterpart; it is a variant
- * of the push-only persistent BFS kernel (GR_MODE_PERSISTENT of gr_bfs).
+ * allocation after start-up. The paper has no counterpart; it runs a
+ * push-only cooperative BFS kernel (one launch, a bounded grid barrier per
+ * level) and gives the same depths as gr_bfs.
  *
  * row_off[n+1] and col[m] are device pointers to a CSR as described above,
- * read but not validated; depth[n] and parent[n] (parent may be NULL) are
- * device pointers receiving the same results as gr_bfs. n must not exceed
+ * read but not validated (a column index outside [0, n) is skipped);
+ * depth[n] and parent[n] (parent may be NULL) are device pointers receiving
+ * the same results as gr_bfs. A traversal cut short on the device (a grid
+ * barrier wait that ran out) leaves depth[src] = GR_NOALLOC_INCOMPLETE
+ * instead of 0: check depth[src] after synchronising `stream` where that
+ * matters, since the call itself returns before the work runs. n must not exceed
  * 1048576 (1 << 20): the scratch is one fixed device array of about 8.5 MB
  * (control block, two frontier queues, visited bitmap) that every GPU which
  * loads this library holds until the process exits; larger n returns
  * GR_EINVAL. The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. All calls on a device share the array and
+ * address (cudaGetSymbolAddress) with that device current, and looks it up
+ * again after the device's context changed (cudaDeviceReset); make that
+ * first call before any stream capture. All calls on a device share the array and
  * each call reinitialises what it reads, so calls that overlap on the GPU
  * (other streams, other threads) race and must be ordered by the caller.
  * Work is enqueued on `stream`; nothing is synchronised. */
+#define GR_NOALLOC_INCOMPLETE (-2)
 gr_status gr_bfs_noalloc(int32_t n, int64_t m, const int32_t *row_off,
                          const int32_t *col, int32_t src, int32_t *depth,
                          int32_t *parent, void *stream);
@@ -288,34 +295,37 @@ gr_status gr_tuned_sssp(const gr_graph *g, int32_t *mode, int32_t *blocks_per_sm
 
 /* ------------------------------------------------------------------------
  * Query server (not in the paper): BFS / SSSP / CC queries on resident
- * graphs with continuous batching. Worker slots each own a CUDA stream and
- * per-graph workspaces, so queries on different slots overlap on the GPU.
- * A queued request starts when its result buffer (4n bytes) fits in the
- * device-memory budget left by the requests in flight and the slots'
- * workspaces (requests are admitted in arrival order; one that does not fit
- * holds back the ones behind it). A slot that takes a BFS request on a
- * batchable graph also takes up to max_batch - 1 further queued BFS
- * requests for that graph and runs them as lanes of one gr_bfs_batch
- * traversal (see gr_server_add_graph for when); likewise an SSSP request
- * takes further queued SSSP requests for its graph as lanes of one
- * gr_sssp_batch search (up to max_batch and the graph's lane limit, which
- * keeps that search's scratch within 4 GiB). Results equal those of
- * gr_bfs / gr_sssp / gr_cc alone. With one slot, traversals use each
- * graph's tuned driver (the persistent kernels included: the slot has the
- * GPU to itself); with several slots, graph-mode level loops, since a
- * cooperative launch needs the whole GPU. With num_slots = 1 and
- * max_batch = 1 the server is the plain path: one query per launch
- * sequence, in arrival order, on one stream. A request whose
- * traversal stops at a device-side level or iteration limit fails with
- * GR_ETIMEOUT; a slot waits at most 120 s for a batch's device work, after
- * which that batch fails with GR_ETIMEOUT and the slot fails its later
- * requests (its stream may still hold work).
+ * graphs with continuous batching. One worker slot owns a CUDA stream and
+ * per-graph workspaces and runs one batch at a time. Admission: a batch is
+ * started when its result buffers (4n bytes per request) and any workspace
+ * it must create fit in the device-memory budget next to the workspaces
+ * the slot already keeps (workspaces stay until the server is destroyed);
+ * requests are taken in arrival order, and the oldest one starts alone
+ * even when it does not fit while nothing is in flight, so the budget
+ * bounds batching, not single requests. A BFS request on a batchable graph
+ * takes up to max_batch - 1 further queued BFS requests for that graph and
+ * runs them as lanes of one gr_bfs_batch traversal (see
+ * gr_server_add_graph for when); likewise an SSSP request takes further
+ * queued SSSP requests for its graph as lanes of one gr_sssp_batch search
+ * (up to max_batch and the graph's lane limit, which keeps that search's
+ * scratch within 4 GiB). Results equal those of gr_bfs / gr_sssp / gr_cc
+ * alone. Traversals use each graph's tuned driver. With max_batch = 1 the
+ * server is the plain path: one query per launch sequence, in arrival
+ * order, on one stream. A request whose traversal stops at a device-side
+ * level or iteration limit fails with GR_ETIMEOUT. Whatever a batch's
+ * outcome, the slot waits for the device work it enqueued before it
+ * reuses or frees any buffer; it waits at most 120 s, after which that
+ * batch fails with GR_ETIMEOUT and the slot fails its later requests
+ * (its stream may still hold work, so its buffers are then left alone).
+ * The server takes each graph's lock while it enqueues work on the graph.
  * ---------------------------------------------------------------------- */
 typedef struct gr_server gr_server;
 
 enum { GR_QUERY_BFS = 0, GR_QUERY_SSSP = 1, GR_QUERY_CC = 2 };
 
-/* budget_bytes > 0; num_slots and max_batch in [1, 64]. */
+/* budget_bytes > 0; num_slots must be 1 (several slots running traversals
+ * at once are disabled: a device fault seen with them is not explained);
+ * max_batch in [1, 64]. */
 gr_status gr_server_create(size_t budget_bytes, int32_t num_slots, int32_t max_batch,
                            gr_server **out);
 

@@ -940,6 +940,9 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
 // of the visited-bitmap claim are appended with one atomic per warp. Levels
 // are separated by a sense-reversing grid barrier whose spin is bounded.
 constexpr int kPersThreads = 256;
+// depth[src] after an allocation-free BFS that stopped at a device-side
+// limit (GR_NOALLOC_INCOMPLETE in gr.h)
+constexpr int32_t kNoAllocIncomplete = -2;
 
 __device__ __forceinline__ bool grid_barrier(BfsCtl *c, int32_t nblocks, int32_t &gen) {
   (void)nblocks;
@@ -988,8 +991,9 @@ __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
         const int32_t e = eb + lane;
         bool won = false;
         int32_t v = 0;
-        if (e < r1) {
-          v = a.C[e];
+        // the CSR is not validated by the allocation-free entry point: a
+        // column outside [0, n) is skipped rather than followed
+        if (e < r1 && (uint32_t)(v = a.C[e]) < (uint32_t)a.n) {
           const uint32_t mask = 1u << (v & 31);
           uint32_t *vw = a.visited + (v >> 5);
           if (!(*(volatile uint32_t *)vw & mask)) won = !(atomicOr(vw, mask) & mask);
@@ -1014,6 +1018,10 @@ __global__ void __launch_bounds__(kPersThreads) k_bfs_persistent(BfsArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) persistent_level_end(c);
     if (!grid_barrier(c, nblocks, gen)) break;
   }
+  // a traversal cut short by a device-side limit (a barrier wait that ran
+  // out, the level cap) marks its source, whose depth is otherwise 0
+  if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int32_t *)&c->error != kDevOk)
+    depth[c->src] = kNoAllocIncomplete;
 }
 
 }  // namespace
@@ -1377,16 +1385,49 @@ static_assert(sizeof(BfsCtl) <= kNoAllocCtlBytes, "control block does not fit it
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// device address of g_noalloc_scratch, looked up once per device
+// device address of g_noalloc_scratch, looked up once per device context:
+// a process that resets a device (cudaDeviceReset) gets a new context in
+// which the array may sit elsewhere, so the cached address is keyed by the
+// driver's unique id of the context it was looked up in
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
 int g_noalloc_sms[kMaxDevices] = {};
 int g_noalloc_blocks_per_sm[kMaxDevices] = {};
 
+// Id of the calling thread's current context (0 if the driver cannot tell;
+// the cached address is then kept for the life of the process).
+unsigned long long current_context_id() {
+  using get_current_t = int (*)(void **);
+  using get_id_t = int (*)(void *, unsigned long long *);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (get_current_t)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (get_id_t)f;
+    cudaGetLastError();
+  });
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
 gr_status noalloc_setup(int dev, void **addr, int *sms, int *per_sm) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  // makes the device's primary context current (no allocation)
+  GR_CUDA(cudaSetDevice(dev));
+  const unsigned long long ctx = current_context_id();
+  if (!g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
     void *p = nullptr;
     GR_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     int nsm = 0, occ = 0;
@@ -1396,6 +1437,7 @@ gr_status noalloc_setup(int dev, void **addr, int *sms, int *per_sm) {
     g_noalloc_sms[dev] = nsm;
     g_noalloc_blocks_per_sm[dev] = std::max(1, std::min(occ, 4));
     g_noalloc_addr[dev] = p;
+    g_noalloc_ctx[dev] = ctx;
   }
   *addr = g_noalloc_addr[dev];
   *sms = g_noalloc_sms[dev];

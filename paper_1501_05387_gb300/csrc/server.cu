@@ -4,26 +4,23 @@
 // BFS / SSSP / CC queries on graphs kept resident on the device:
 //
 //   * requests enter a FIFO queue (gr_server_submit);
-//   * a worker thread per slot owns a CUDA stream and, per graph, its own
-//     scratch workspaces, so queries on different slots overlap on the GPU;
-//   * admission is by a device-memory budget: a request is started only
-//     when its result buffer fits in what the in-flight requests' buffers
-//     and the workspaces the slots keep leave free (the oldest request
-//     always starts when nothing is in flight); the memory footprint
-//     follows the paper's alpha*|E| + beta*|V| model (Sec. 6);
-//   * same-graph BFS requests are batched: a worker that takes a BFS request
-//     also takes up to max_batch - 1 further queued BFS requests for that
-//     graph (in arrival order) and runs them as bit lanes of one batched
-//     traversal; on high-diameter graphs (many levels) only once enough of
-//     them are queued;
+//   * a worker thread (the slot) owns a CUDA stream and, per graph, its own
+//     scratch workspaces, and runs one batch at a time;
+//   * admission and batching (server_core.hpp): a batch is admitted while
+//     its result buffers and any workspace it must create fit in the
+//     device-memory budget next to the workspaces already kept;
+//   * same-graph BFS requests are batched: the slot takes up to max_batch
+//     queued BFS requests for the graph (in arrival order) and runs them as
+//     bit lanes of one batched traversal; on high-diameter graphs only once
+//     enough of them are queued;
 //   * same-graph SSSP requests are batched the same way, as lanes of one
 //     near/far search over copies of the graph (sssp_batch_run), as many as
 //     the graph's lane limit allows;
 //   * a result is copied to the caller's buffer (device or host) given at
 //     submission, then its server buffer is released.
 //
-// With one slot and max_batch = 1 the same code is the plain path: one query
-// per launch sequence, in arrival order, on one stream, no overlap.
+// With max_batch = 1 the same code is the plain path: one query per launch
+// sequence, in arrival order, on one stream.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -35,6 +32,7 @@
 #include <vector>
 
 #include "gr_internal.cuh"
+#include "server_core.hpp"
 
 namespace gr {
 
@@ -66,7 +64,7 @@ struct SlotGraphState {
   SsspWorkspace *sssp = nullptr;
   CcWorkspace *cc = nullptr;
   BatchWorkspace *batch = nullptr;
-  SsspWorkspace *sssp_batch = nullptr;  // for GraphEntry::sssp_lanes lanes
+  SsspWorkspace *sssp_batch = nullptr;  // for the graph's sssp_lanes lanes
   ~SlotGraphState() {
     free_bfs(bfs);
     free_sssp(sssp);
@@ -76,94 +74,9 @@ struct SlotGraphState {
   }
 };
 
-struct GraphEntry {
-  gr_graph *g = nullptr;
-  // a BFS request is run as lanes of a batch when at least this many BFS
-  // requests for the graph are queued (0: never batched)
-  int32_t min_batch = 1;
-  // most SSSP requests one batched search takes (1: never batched)
-  int32_t sssp_lanes = 1;
-};
-
 // Scratch one slot's batched SSSP workspace may take on a graph; the lane
 // limit of the graph follows from it.
 constexpr size_t kSsspBatchBytes = size_t(4) << 30;
-
-}  // namespace
-
-struct Server {
-  size_t budget = 0;
-  size_t in_use = 0;    // result buffers of admitted, unfinished requests
-  size_t resident = 0;  // workspaces created by the slots (kept)
-  int32_t nslots = 1;
-  int32_t max_batch = 64;
-  int device = 0;
-  std::vector<GraphEntry> graphs;
-  std::mutex mu;
-  std::mutex setup_mu;  // one slot at a time builds workspaces and level-loop graphs
-  std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;                      // tickets waiting
-  std::unordered_map<uint64_t, Request> reqs;      // all known requests
-  uint64_t next_ticket = 1;
-  bool stopping = false;
-  std::vector<std::thread> workers;
-  std::vector<double> latencies;  // completed requests (ms, submit -> done)
-  uint64_t completed = 0, failed = 0, launches = 0, batched_lanes = 0;
-  double t_first_submit = -1.0, t_last_done = 0.0;
-  std::string last_error;
-
-  size_t result_bytes(const Request &r) const {
-    const gr_graph *g = graphs[r.graph].g;
-    return sizeof(int32_t) * (size_t)g->n;
-  }
-  void worker();
-};
-
-namespace {
-
-// Pick the next batch for a slot (caller holds the lock): the oldest
-// request whose memory fits, plus same-graph BFS requests behind it when
-// enough of them are queued for the graph to batch.
-std::vector<uint64_t> take_batch(Server &S) {
-  std::vector<uint64_t> out;
-  for (auto it = S.queue.begin(); it != S.queue.end(); ++it) {
-    Request &r = S.reqs[*it];
-    const size_t need = S.result_bytes(r);
-    if (S.resident + S.in_use + need > S.budget && S.in_use > 0) break;  // wait for memory
-    out.push_back(*it);
-    S.in_use += need;
-    S.queue.erase(it);
-    // lanes the batch of r may have
-    int32_t cap = 1;
-    const GraphEntry &ge = S.graphs[r.graph];
-    if (r.kind == GR_QUERY_BFS && S.max_batch > 1 && ge.min_batch > 0) {
-      int32_t queued = 1;  // r and the same-graph BFS requests behind it
-      for (auto jt = S.queue.begin(); jt != S.queue.end() && queued < ge.min_batch; ++jt) {
-        const Request &q = S.reqs[*jt];
-        if (q.kind == GR_QUERY_BFS && q.graph == r.graph) ++queued;
-      }
-      if (queued >= ge.min_batch) cap = S.max_batch;
-    } else if (r.kind == GR_QUERY_SSSP && S.max_batch > 1 && ge.min_batch > 0) {
-      cap = std::min(S.max_batch, ge.sssp_lanes);
-    }
-    if (cap > 1) {
-      for (auto jt = S.queue.begin(); jt != S.queue.end() && (int32_t)out.size() < cap;) {
-        Request &q = S.reqs[*jt];
-        if (q.kind == r.kind && q.graph == r.graph) {
-          const size_t nq = S.result_bytes(q);
-          if (S.resident + S.in_use + nq > S.budget) break;
-          S.in_use += nq;
-          out.push_back(*jt);
-          jt = S.queue.erase(jt);
-        } else {
-          ++jt;
-        }
-      }
-    }
-    break;
-  }
-  return out;
-}
 
 // Longest a batch's device work may take before its slot gives up on it.
 constexpr double kBatchLimitMs = 120000.0;
@@ -193,127 +106,142 @@ gr_status copy_out(const Request &r, const void *dev, size_t bytes, cudaStream_t
 
 }  // namespace
 
+struct Server {
+  serve::Admission adm;  // under mu
+  int device = 0;
+  std::vector<gr_graph *> graphs;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::unordered_map<uint64_t, Request> reqs;  // all known requests
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+  std::vector<std::thread> workers;
+  std::vector<double> latencies;  // completed requests (ms, submit -> done)
+  uint64_t completed = 0, failed = 0, launches = 0, batched_lanes = 0;
+  double t_first_submit = -1.0, t_last_done = 0.0;
+  std::string last_error;
+
+  void worker();
+};
+
+namespace {
+
+// The device side of one batch on the slot (serve::run_batch's Dev).
+struct SlotDev {
+  gr_graph *g;
+  SlotGraphState &st;
+  const std::vector<Request> &rs;
+  int32_t sssp_lanes;
+  cudaStream_t s;
+  DevMem &buf;
+  std::string &broken;  // set once the slot's stream stopped draining
+
+  bool many() const { return rs.size() > 1; }
+
+  gr_status prepare(size_t need) {
+    if (!s) return fail(GR_ECUDA, "server slot has no stream");
+    if (!broken.empty()) return fail(GR_ECUDA, broken);
+    // every earlier batch of this slot has been waited for (run_batch), so
+    // the buffer is free to reallocate
+    if (buf.bytes < need) GR_TRY(buf.alloc(need, "server result buffer"));
+    return GR_OK;
+  }
+
+  gr_status enqueue() {
+    const Request &first = rs[0];
+    const size_t nbytes = sizeof(int32_t) * (size_t)g->n;
+    // the graph's tuned settings are read under its lock, which also orders
+    // this batch against public calls on the graph from other threads
+    std::lock_guard<std::mutex> lock(g->mu);
+    const gr_opts &o = default_opts();
+    if (first.kind == GR_QUERY_BFS && many()) {
+      if (!st.batch) GR_TRY(batch_ws_create(g, &st.batch));
+      std::vector<int32_t> srcs;
+      for (auto &r : rs) srcs.push_back(r.src);
+      GR_TRY(bfs_batch_run(g, st.batch, srcs.data(), (int32_t)srcs.size(), buf.as<int32_t>(),
+                           g->n + 1, s));
+    } else if (first.kind == GR_QUERY_BFS) {
+      if (!st.bfs) GR_TRY(bfs_ws_create(g, s, &st.bfs));
+      GR_TRY(bfs_run(g, st.bfs, first.src, buf.as<int32_t>(), nullptr, o, s));
+    } else if (first.kind == GR_QUERY_SSSP && many()) {
+      if (!st.sssp_batch) GR_TRY(sssp_ws_create(g, s, &st.sssp_batch, sssp_lanes));
+      std::vector<int32_t> srcs;
+      for (auto &r : rs) srcs.push_back(r.src);
+      GR_TRY(sssp_batch_run(g, st.sssp_batch, srcs.data(), (int32_t)srcs.size(),
+                            buf.as<uint32_t>(), o, s));
+    } else if (first.kind == GR_QUERY_SSSP) {
+      if (!st.sssp) GR_TRY(sssp_ws_create(g, s, &st.sssp));
+      GR_TRY(sssp_run(g, st.sssp, first.src, buf.as<uint32_t>(), nullptr, o, s));
+    } else {
+      if (!st.cc) GR_TRY(cc_ws_create(g, &st.cc));
+      GR_TRY(cc_run(g, st.cc, buf.as<int32_t>(), s));
+    }
+    for (size_t i = 0; i < rs.size(); ++i)
+      GR_TRY(copy_out(rs[i], buf.as<char>() + i * nbytes, nbytes, s));
+    return GR_OK;
+  }
+
+  gr_status wait_idle() {
+    const gr_status w = wait_stream(s, kBatchLimitMs);
+    if (w == GR_ETIMEOUT) broken = std::string("server slot unusable: ") + gr_last_error();
+    return w;
+  }
+
+  // a traversal that stopped at a device-side limit (level or iteration
+  // cap, a timed-out wait) fails its request
+  gr_status check_device_errors() {
+    const int32_t kind = rs[0].kind;
+    if (kind == GR_QUERY_BFS && !many()) return bfs_read_ctl_error(st.bfs, s);
+    if (kind == GR_QUERY_SSSP) return sssp_read_ctl_error(many() ? st.sssp_batch : st.sssp, s);
+    return GR_OK;
+  }
+};
+
+}  // namespace
+
 void Server::worker() {
   cudaSetDevice(device);
   cudaStream_t s = nullptr;
   // a slot without a stream still drains its requests, failing them, so
   // that waiters never hang
-  const cudaError_t se = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-  const std::string stream_err =
-      se == cudaSuccess ? std::string() : std::string("server slot stream: ") + cudaGetErrorString(se);
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    s = nullptr;
+    cudaGetLastError();
+  }
   // per-graph workspaces and the result staging of this slot; held by
   // pointer so that a slot whose stream stopped draining can leave them
   // (freeing memory that queued work may still use would wait on it)
   auto *state = new std::map<int32_t, SlotGraphState>();
-  auto *buf_p = new DevMem();
-  DevMem &buf = *buf_p;
-  std::string broken;  // set when the slot's stream stopped draining
+  auto *buf = new DevMem();
+  std::string broken;
   for (;;) {
-    std::vector<uint64_t> batch;
+    std::vector<Request> rs;
     {
       std::unique_lock<std::mutex> lock(mu);
+      std::vector<uint64_t> batch;
       cv_work.wait(lock, [&] {
         if (stopping) return true;
-        batch = take_batch(*this);
+        batch = adm.take_batch();
         return !batch.empty();
       });
       if (batch.empty()) break;  // stopping
-      for (uint64_t t : batch) reqs[t].t_start = now_ms();
+      const double t = now_ms();
+      for (uint64_t tk : batch) {
+        reqs[tk].t_start = t;
+        rs.push_back(reqs[tk]);
+      }
     }
     // requests of a batch share kind and graph
-    Request first;
-    std::vector<Request> rs;
+    const Request &first = rs[0];
+    gr_graph *g = graphs[first.graph];
+    int32_t sssp_lanes;
     {
       std::lock_guard<std::mutex> lock(mu);
-      for (uint64_t t : batch) rs.push_back(reqs[t]);
+      sssp_lanes = adm.graphs[first.graph].sssp_lanes;
     }
-    first = rs[0];
-    GraphEntry &ge = graphs[first.graph];
-    gr_graph *g = ge.g;
-    SlotGraphState &st = (*state)[first.graph];
-    const size_t nbytes = sizeof(int32_t) * (size_t)g->n;
-    const size_t need = nbytes * rs.size();
-    gr_status status = GR_OK;
+    SlotDev dev{g, (*state)[first.graph], rs, sssp_lanes, s, *buf, broken};
+    const gr_status status = serve::run_batch(dev, sizeof(int32_t) * (size_t)g->n * rs.size());
     std::string err;
-    if (!stream_err.empty()) status = fail(GR_ECUDA, stream_err);
-    if (status == GR_OK && !broken.empty()) status = fail(GR_ECUDA, broken);
-    if (status == GR_OK && buf.bytes < need) status = buf.alloc(need, "server result buffer");
-    // with several slots, graph-mode level loops: slots may run traversals
-    // at once, so no launch may need the whole GPU to itself (cooperative
-    // launches do); a single slot has the GPU to itself and runs each
-    // graph's tuned driver
-    gr_opts o = default_opts();
-    if (nslots > 1) o.mode = GR_MODE_GRAPH;
-    size_t ws_new = 0;
-    // the first request of a kind on a graph creates this slot's workspace
-    // and captures its level-loop graph; slots do that one at a time
-    std::unique_lock<std::mutex> setup(setup_mu, std::defer_lock);
-    const bool many = rs.size() > 1;
-    const bool fresh = (first.kind == GR_QUERY_BFS && many)    ? !st.batch
-                       : first.kind == GR_QUERY_BFS            ? !st.bfs
-                       : (first.kind == GR_QUERY_SSSP && many) ? !st.sssp_batch
-                       : first.kind == GR_QUERY_SSSP           ? !st.sssp
-                                                               : !st.cc;
-    if (fresh) setup.lock();
-    if (status == GR_OK) {
-      if (first.kind == GR_QUERY_BFS && rs.size() > 1) {
-        if (!st.batch) {
-          status = batch_ws_create(g, &st.batch);
-          ws_new += batch_ws_bytes(g);
-        }
-        if (status == GR_OK) {
-          std::vector<int32_t> srcs;
-          for (auto &r : rs) srcs.push_back(r.src);
-          status = bfs_batch_run(g, st.batch, srcs.data(), (int32_t)srcs.size(),
-                                 buf.as<int32_t>(), g->n + 1, s);
-        }
-      } else if (first.kind == GR_QUERY_BFS) {
-        if (!st.bfs) {
-          status = bfs_ws_create(g, s, &st.bfs);
-          ws_new += bfs_ws_bytes(g);
-        }
-        if (status == GR_OK) status = bfs_run(g, st.bfs, first.src, buf.as<int32_t>(), nullptr, o, s);
-      } else if (first.kind == GR_QUERY_SSSP && many) {
-        if (!st.sssp_batch) {
-          status = sssp_ws_create(g, s, &st.sssp_batch, ge.sssp_lanes);
-          ws_new += sssp_ws_bytes(g, ge.sssp_lanes);
-        }
-        if (status == GR_OK) {
-          std::vector<int32_t> srcs;
-          for (auto &r : rs) srcs.push_back(r.src);
-          // the CUDA-graph driver holds one-lane arguments: host-driven
-          // batches stand in for it (sssp_batch_run)
-          status = sssp_batch_run(g, st.sssp_batch, srcs.data(), (int32_t)srcs.size(),
-                                  buf.as<uint32_t>(), o, s);
-        }
-      } else if (first.kind == GR_QUERY_SSSP) {
-        if (!st.sssp) {
-          status = sssp_ws_create(g, s, &st.sssp);
-          ws_new += sssp_ws_bytes(g);
-        }
-        if (status == GR_OK)
-          status = sssp_run(g, st.sssp, first.src, buf.as<uint32_t>(), nullptr, o, s);
-      } else {
-        if (!st.cc) {
-          status = cc_ws_create(g, &st.cc);
-          ws_new += cc_ws_bytes(g);
-        }
-        if (status == GR_OK) status = cc_run(g, st.cc, buf.as<int32_t>(), s);
-      }
-      for (size_t i = 0; status == GR_OK && i < rs.size(); ++i)
-        status = copy_out(rs[i], buf.as<char>() + i * nbytes, nbytes, s);
-      if (setup.owns_lock()) setup.unlock();
-      if (status == GR_OK) {
-        status = wait_stream(s, kBatchLimitMs);
-        if (status == GR_ETIMEOUT) broken = std::string("server slot unusable: ") + gr_last_error();
-      }
-      // a traversal that stopped at a device-side limit (level or iteration
-      // cap, a timed-out wait) fails its request
-      if (status == GR_OK && first.kind == GR_QUERY_BFS && rs.size() == 1)
-        status = bfs_read_ctl_error(st.bfs, s);
-      if (status == GR_OK && first.kind == GR_QUERY_SSSP)
-        status = sssp_read_ctl_error(many ? st.sssp_batch : st.sssp, s);
-    }
     if (status != GR_OK)
       err = std::string(gr_last_error()) + " [batch: kind " + std::to_string(first.kind) +
             ", graph " + std::to_string(first.graph) + ", lanes " + std::to_string(rs.size()) +
@@ -327,7 +255,6 @@ void Server::worker() {
         q.status = status;
         q.t_done = t;
         q.batch = (int32_t)rs.size();
-        in_use -= result_bytes(q);
         if (status == GR_OK) {
           ++completed;
           latencies.push_back(t - q.t_submit);
@@ -336,9 +263,17 @@ void Server::worker() {
           last_error = err;
         }
       }
+      adm.release(first.graph, rs.size());
+      const serve::WsKind w = serve::ws_kind(first.kind, rs.size() > 1);
+      const SlotGraphState &st = (*state)[first.graph];
+      const void *ws = w == serve::kWsBfs ? (const void *)st.bfs
+                       : w == serve::kWsBfsBatch ? (const void *)st.batch
+                       : w == serve::kWsSssp ? (const void *)st.sssp
+                       : w == serve::kWsSsspBatch ? (const void *)st.sssp_batch
+                                                  : (const void *)st.cc;
+      if (!ws) adm.ws_not_created(first.graph, w);
       ++launches;
       batched_lanes += rs.size();
-      resident += ws_new;  // workspaces stay with the slot
       t_last_done = std::max(t_last_done, t);
     }
     cv_done.notify_all();
@@ -346,7 +281,7 @@ void Server::worker() {
   }
   if (broken.empty()) {
     delete state;
-    delete buf_p;
+    delete buf;
     if (s) cudaStreamDestroy(s);
   }
 }
@@ -366,15 +301,18 @@ gr_status gr_server_create(size_t budget_bytes, int32_t num_slots, int32_t max_b
   clear_error();
   if (!out) return fail(GR_EINVAL, "out must not be NULL");
   *out = nullptr;
-  if (num_slots < 1 || num_slots > 64) return fail(GR_EINVAL, "num_slots must be in [1, 64]");
+  if (num_slots != 1)
+    return fail(GR_EINVAL,
+                "num_slots must be 1: the server runs one worker slot (several slots running "
+                "traversals at once are disabled until a device fault seen with them is "
+                "explained)");
   if (max_batch < 1 || max_batch > 64) return fail(GR_EINVAL, "max_batch must be in [1, 64]");
   if (budget_bytes == 0) return fail(GR_EINVAL, "budget_bytes must be > 0");
   std::unique_ptr<gr_server> srv(new gr_server());
   Server &S = srv->impl;
   GR_CUDA(cudaGetDevice(&S.device));
-  S.budget = budget_bytes;
-  S.nslots = num_slots;
-  S.max_batch = max_batch;
+  S.adm.budget = budget_bytes;
+  S.adm.max_batch = max_batch;
   *out = srv.release();
   return GR_OK;
 }
@@ -387,15 +325,21 @@ gr_status gr_server_add_graph(gr_server *srv, gr_graph *g, int32_t batchable,
   Server &S = srv->impl;
   std::lock_guard<std::mutex> lock(S.mu);
   if (!S.workers.empty()) return fail(GR_EBUSY, "add graphs before the first submit");
-  GraphEntry e;
-  e.g = g;
+  serve::GraphInfo e;
+  e.n = g->n;
   e.min_batch = batchable;
   if (g->has_weights) {
     const size_t per_lane = sssp_ws_bytes(g, 1) + sizeof(uint32_t) * (size_t)g->n;
     const size_t by_mem = std::max<size_t>(1, kSsspBatchBytes / per_lane);
     e.sssp_lanes = (int32_t)std::min<size_t>(by_mem, (size_t)sssp_batch_max_lanes(g));
   }
-  S.graphs.push_back(e);
+  e.ws_bytes[serve::kWsBfs] = bfs_ws_bytes(g);
+  e.ws_bytes[serve::kWsBfsBatch] = batch_ws_bytes(g);
+  e.ws_bytes[serve::kWsSssp] = g->has_weights ? sssp_ws_bytes(g) : 0;
+  e.ws_bytes[serve::kWsSsspBatch] = g->has_weights ? sssp_ws_bytes(g, e.sssp_lanes) : 0;
+  e.ws_bytes[serve::kWsCc] = cc_ws_bytes(g);
+  S.adm.graphs.push_back(e);
+  S.graphs.push_back(g);
   *graph_id = (int32_t)S.graphs.size() - 1;
   return GR_OK;
 }
@@ -408,12 +352,12 @@ gr_status gr_server_submit(gr_server *srv, int32_t graph_id, int32_t kind, int32
   std::unique_lock<std::mutex> lock(S.mu);
   if (graph_id < 0 || graph_id >= (int32_t)S.graphs.size())
     return fail(GR_EINVAL, "unknown graph id");
-  gr_graph *g = S.graphs[graph_id].g;
+  gr_graph *g = S.graphs[graph_id];
   if (kind != GR_QUERY_BFS && kind != GR_QUERY_SSSP && kind != GR_QUERY_CC)
     return fail(GR_EINVAL, "unknown query kind");
   if (kind != GR_QUERY_CC && (src < 0 || src >= g->n)) return fail(GR_EINVAL, "source out of range");
   if (kind == GR_QUERY_SSSP && !g->has_weights) return fail(GR_EINVAL, "SSSP needs weights");
-  if (sizeof(int32_t) * (size_t)g->n > S.budget)
+  if (sizeof(int32_t) * (size_t)g->n > S.adm.budget)
     return fail(GR_EINVAL, "a single result does not fit the memory budget");
   if (S.stopping) return fail(GR_EBUSY, "server is shutting down");
   Request r;
@@ -432,10 +376,10 @@ gr_status gr_server_submit(gr_server *srv, int32_t graph_id, int32_t kind, int32
   r.t_submit = now_ms();
   if (S.t_first_submit < 0) S.t_first_submit = r.t_submit;
   S.reqs[r.ticket] = r;
-  S.queue.push_back(r.ticket);
+  S.adm.pending[r.ticket] = serve::Pending{graph_id, kind};
+  S.adm.queue.push_back(r.ticket);
   *ticket = r.ticket;
-  if (S.workers.empty())
-    for (int i = 0; i < S.nslots; ++i) S.workers.emplace_back([&S] { S.worker(); });
+  if (S.workers.empty()) S.workers.emplace_back([&S] { S.worker(); });
   lock.unlock();
   S.cv_work.notify_one();
   return GR_OK;
@@ -469,7 +413,7 @@ gr_status gr_server_drain(gr_server *srv, int32_t timeout_ms) {
   Server &S = srv->impl;
   std::unique_lock<std::mutex> lock(S.mu);
   auto pred = [&] {
-    if (!S.queue.empty()) return false;
+    if (!S.adm.queue.empty()) return false;
     for (auto &kv : S.reqs)
       if (!kv.second.done) return false;
     return true;

@@ -32,6 +32,7 @@ STATUS_NAMES = {0: "GR_OK", 1: "GR_EINVAL", 2: "GR_ENOMEM", 3: "GR_ECUDA",
 GR_DIR_AUTO, GR_DIR_PUSH, GR_DIR_PULL = 0, 1, 2
 GR_MODE_AUTO, GR_MODE_LAUNCH, GR_MODE_GRAPH, GR_MODE_PERSISTENT = 0, 1, 2, 3
 GR_QUERY_BFS, GR_QUERY_SSSP, GR_QUERY_CC = 0, 1, 2
+GR_NOALLOC_INCOMPLETE = -2
 GR_TUNE_BFS, GR_TUNE_SSSP = 1, 2
 
 
@@ -299,10 +300,26 @@ def gr_bc(g: Graph, srcs, bc, opts=None, stream=None):
 
 def gr_bfs_noalloc(row_off, col, src: int, depth, parent=None, stream=None):
     """BFS without any device allocation (see include/gr.h): row_off, col,
-    depth and parent are CUDA tensors owned by the caller."""
-    _check(_lib.gr_bfs_noalloc(int(row_off.shape[0]) - 1, int(col.shape[0]), _ptr(row_off),
-                               _ptr(col), int(src), _ptr(depth), _ptr(parent),
-                               _stream(stream)), "gr_bfs_noalloc")
+    depth and parent are contiguous int32 CUDA tensors on the current device,
+    owned by the caller; depth and parent hold at least n entries. The C
+    entry point does not validate the CSR and reads these pointers on the
+    device, so their types, device and sizes are checked here."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("row_off", row_off), ("col", col), ("depth", depth), ("parent", parent)):
+        if t is None and name == "parent":
+            continue
+        if not _is_torch(t) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != torch.int32 or not t.is_contiguous() or t.dim() != 1:
+            raise ValueError(f"{name} must be a contiguous 1-D int32 tensor")
+    n = int(row_off.shape[0]) - 1
+    if n < 1:
+        raise ValueError("row_off must hold n + 1 >= 2 entries")
+    if depth.numel() < n or (parent is not None and parent.numel() < n):
+        raise ValueError(f"depth and parent must hold at least n = {n} entries")
+    _check(_lib.gr_bfs_noalloc(n, int(col.shape[0]), _ptr(row_off), _ptr(col), int(src),
+                               _ptr(depth), _ptr(parent), _stream(stream)), "gr_bfs_noalloc")
 
 
 def gr_cc(g: Graph, label, opts=None, stream=None, count=True):
@@ -389,7 +406,7 @@ class Server:
         self.close()
 
 
-def gr_server_create(budget_bytes: int, num_slots: int = 4, max_batch: int = 64) -> Server:
+def gr_server_create(budget_bytes: int, num_slots: int = 1, max_batch: int = 64) -> Server:
     out = _vp()
     _check(_lib.gr_server_create(int(budget_bytes), int(num_slots), int(max_batch),
                                  ctypes.byref(out)), "gr_server_create")

@@ -93,8 +93,11 @@ def test_null_graph_rejected(gr):
 def test_server_rejects_bad_arguments(gr):
     out = ctypes.c_void_p()
     for budget, slots, batch in [(0, 1, 1), (1 << 20, 0, 1), (1 << 20, 65, 1),
+                                 (1 << 20, 2, 1), (1 << 20, 4, 64),
                                  (1 << 20, 1, 0), (1 << 20, 1, 65)]:
         assert gr._lib.gr_server_create(budget, slots, batch, ctypes.byref(out)) == gr.GR_EINVAL
+        if slots in (2, 4):
+            assert "num_slots must be 1" in gr.gr_last_error()
     assert gr._lib.gr_server_destroy(None) == gr.GR_OK
 
 

@@ -1,24 +1,12 @@
 """Query server: every result served in the mix (BFS and SSSP batched,
-admitted under a memory budget, with several slots overlapped on several
-streams) equals the same query run alone, bit for bit."""
-import os
-
+admitted under a memory budget) equals the same query run alone, bit for
+bit. The server runs one worker slot (gr_server_create refuses more)."""
 import numpy as np
 import pytest
 
 import graphgen as gg
 
 pytestmark = pytest.mark.gpu
-
-# Several slots overlap their device work on separate streams. Serving
-# benchmarks with 4 slots raised a device fault whose cause has not been
-# found by reading the code, while every one-slot phase ran cleanly; until
-# the cause is found, the tests with more than one slot run only when asked
-# for explicitly.
-multi_slot = pytest.mark.skipif(
-    os.environ.get("GR_SERVER_DEVICE_TESTS") != "1",
-    reason="multi-slot server device tests are opt-in (GR_SERVER_DEVICE_TESTS=1) while an "
-           "unexplained device fault with concurrent slots is open")
 
 
 def alone(gr, g, kind, src):
@@ -63,9 +51,7 @@ def make_requests(gr, graphs, count, seed):
 
 
 @pytest.mark.parametrize("slots,batch,budget", [
-    (1, 1, 1 << 30), (1, 64, 1 << 30), (1, 16, 200_000),
-    pytest.param(4, 64, 1 << 30, marks=multi_slot),
-    pytest.param(3, 16, 200_000, marks=multi_slot)])
+    (1, 1, 1 << 30), (1, 64, 1 << 30), (1, 16, 200_000)])
 def test_mix_equals_alone(cuda_lib, pool, slots, batch, budget):
     gr = cuda_lib
     reqs = make_requests(gr, pool, 240, seed=slots * 7 + batch)
@@ -150,7 +136,7 @@ def test_sssp_batching(cuda_lib, pool, gi):
 def test_bad_requests(cuda_lib, pool):
     gr = cuda_lib
     g = pool[0][0]
-    with gr.gr_server_create(1 << 20, 2, 8) as srv:
+    with gr.gr_server_create(1 << 20, 1, 8) as srv:
         gid = gr.gr_server_add_graph(srv, g, True)
         for args in [(gid + 5, gr.GR_QUERY_BFS, 0), (gid, 9, 0), (gid, gr.GR_QUERY_BFS, g.n)]:
             with pytest.raises(gr.GrError) as ei:

@@ -2,6 +2,7 @@
 has the specified mix, valid non-isolated sources and Poisson arrivals, and
 is reproducible."""
 import numpy as np
+import pytest
 
 import graphgen as gg
 
@@ -37,3 +38,26 @@ def test_request_stream_mix_sources_and_arrivals():
     assert reqs2 == reqs and np.array_equal(unit2, unit)
     reqs3, _ = bench.serving_requests(pool, 200, seed=7)
     assert reqs3 != reqs[:200]
+
+
+def test_server_core_lifecycle_and_admission(tmp_path):
+    """The query server's host-only core, built with g++ and a fake device:
+    a batch that fails after enqueueing work is waited for before the slot
+    reallocates or reuses any buffer (a fake of the earlier order, which
+    skipped that wait on error, is caught), and admission counts result
+    buffers and the workspaces a batch must create against the budget."""
+    import os
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path / "server_core_check")
+    subprocess.check_call([gxx, "-std=c++17", "-O1", "-Wall",
+                           "-I", os.path.join(root, "include"),
+                           "-I", os.path.join(root, "paper_1501_05387_gb300", "csrc"),
+                           os.path.join(root, "tests", "server_core_check.cpp"), "-o", exe])
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout + res.stderr
+    assert res.stdout.strip().endswith("ok")

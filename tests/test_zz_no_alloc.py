@@ -44,19 +44,43 @@ def test_noalloc_bfs_matches_gr_bfs_twice(cuda_lib):
 
 
 def test_noalloc_bfs_depth_only_on_a_grid(cuda_lib):
+    """Depth only (parent NULL) on a mesh with deleted edges, two sources in
+    a row, checked against the CPU queue BFS itself."""
+    import oracle
     import torch
     gr = cuda_lib
     r, c = gg.grid(48, p_del=0.05, seed=4)
     rt = torch.from_numpy(r).cuda()
     ct = torch.from_numpy(c).cuda()
-    with gr.gr_graph_create(r, c) as g:
-        for src in (0, 1000):
-            ref = torch.empty(g.n, dtype=torch.int32, device="cuda")
-            gr.gr_bfs(g, src, ref, None)
-            d = torch.empty(g.n, dtype=torch.int32, device="cuda")
-            gr.gr_bfs_noalloc(rt, ct, src, d, None)
-            torch.cuda.synchronize()
-            assert torch.equal(d, ref)
+    n = r.size - 1
+    for src in (0, 1000):
+        want, _ = oracle.bfs(r, c, src)
+        d = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+        gr.gr_bfs_noalloc(rt, ct, src, d, None)
+        torch.cuda.synchronize()
+        got = d.cpu().numpy()
+        assert got[src] == 0  # not GR_NOALLOC_INCOMPLETE
+        assert np.array_equal(got, want)
+
+
+def test_noalloc_wrapper_rejects_bad_tensors(cuda_lib):
+    """The Python wrapper checks what the C entry point cannot (types,
+    device, sizes) before any pointer reaches the GPU."""
+    import torch
+    gr = cuda_lib
+    r, c = gg.grid(8, p_del=0.0, seed=1)
+    rt = torch.from_numpy(r).cuda()
+    ct = torch.from_numpy(c).cuda()
+    n = r.size - 1
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        gr.gr_bfs_noalloc(rt.long(), ct, 0, d)                        # int64 offsets
+    with pytest.raises(ValueError):
+        gr.gr_bfs_noalloc(rt, ct, 0, d[: n - 1])                      # short depth
+    with pytest.raises(ValueError):
+        gr.gr_bfs_noalloc(rt, ct, 0, d, torch.empty(3, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        gr.gr_bfs_noalloc(rt.cpu(), ct, 0, d)                         # host tensor
 
 
 def test_noalloc_bfs_rejects_oversized_graph(cuda_lib):
