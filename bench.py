@@ -433,12 +433,14 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     srcs = gg.sources(r, 4, seed=4)
     depth = torch.empty(n, dtype=torch.int32, device=dev)
     parent = torch.empty(n, dtype=torch.int32, device=dev)
-    per, byts, levels = [], [], []
+    per, byts, levels, single_depth = [], [], [], []
     for s in srcs:
         ms, _ = _timed_calls(lambda: gr.gr_bfs(g, int(s), depth, parent), 1, flush)
         levels.append(gr.gr_bfs_stats(g)[0])
         per.append(ms)
-        byts.append(reach_bytes(r, depth.cpu().numpy() >= 0, 4, 8))
+        d = depth.cpu().numpy()
+        single_depth.append(d.copy())
+        byts.append(reach_bytes(r, d >= 0, 4, 8))
     mean = float(np.mean(per))
     out.append({"workload": "grid4096_bfs", "primitive": "bfs", "calls": len(srcs),
                 "ms_per_call": mean, "throughput": m / (mean * 1e-3) / 1e9, "unit": "GTEPS",
@@ -447,6 +449,25 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
                 "roofline": _roof(float(np.mean(byts)), mean, peak,
                                   "4 B per column entry of the reached vertices, 4 B per "
                                   "row offset, 8 B depth+parent per reached vertex")})
+    # the same traversals batched: 64 sources (the four above first) as bit
+    # lanes of one persistent traversal, against one at a time
+    del parent
+    kb = 64
+    srcs_b = [int(x) for x in srcs] + [int(x) for x in gg.sources(r, kb + 8, seed=24)
+                                        if int(x) not in set(int(y) for y in srcs)][:kb - len(srcs)]
+    depth_b = torch.empty(kb * n, dtype=torch.int32, device=dev)
+    ms_b, _ = _timed_calls(lambda: gr.gr_bfs_batch(g, srcs_b, depth_b), 1, flush)
+    lv_b = gr.gr_bfs_batch_stats(g)
+    db = depth_b.view(kb, n)
+    equal = [bool(np.array_equal(db[i].cpu().numpy(), single_depth[i])) for i in range(len(srcs))]
+    out.append({"workload": f"grid4096_bfs_batch{kb}", "primitive": "batched bfs", "calls": 1,
+                "sources": kb, "ms_per_call": ms_b, "ms_per_source": ms_b / kb,
+                "queries_per_s": kb / (ms_b * 1e-3),
+                "speedup_vs_single": (kb / ms_b) / (1.0 / mean), "levels": lv_b,
+                "us_per_level": 1e3 * ms_b / lv_b,
+                "lanes_equal_single": equal,
+                "throughput": kb * m / (ms_b * 1e-3) / 1e9, "unit": "GTEPS (k*m per call)"})
+    del depth_b, db
     # SSSP bucket width and driver tuned once on two sample sources
     gr.gr_autotune(g, [int(srcs[0]), int(srcs[1])], gr.GR_TUNE_SSSP)
     per, byts, iters, single = [], [], [], []

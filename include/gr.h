@@ -144,7 +144,14 @@ gr_status gr_bfs_stats(gr_graph *g, int32_t *levels, int32_t *pull_levels);
  * pred[src] = src; -1 where unreachable (with zero-weight edges pred may
  * contain cycles among equal-distance vertices). opts->delta sets the
  * near/far bucket width (0: tuned, UINT32_MAX: a single bucket); the
- * distances do not depend on it. */
+ * distances do not depend on it. Direction (the pull form of Sec. 4.5
+ * applied to the relaxation, which the paper leaves to future work): on a
+ * symmetric CSR a relaxation whose near frontier holds at least m /
+ * opts->alpha edges (opts->alpha 0: the tuned threshold, by default never)
+ * runs as a pull, every vertex taking the minimum over its in-edges;
+ * opts->direction GR_DIR_PUSH never pulls, GR_DIR_PULL (symmetric CSR
+ * only, else GR_EINVAL) pulls every relaxation. Distances do not depend on
+ * the direction. */
 gr_status gr_sssp(gr_graph *g, int32_t src, uint32_t *dist, int32_t *pred,
                   const gr_opts *opts, void *stream);
 
@@ -175,6 +182,10 @@ gr_status gr_sssp_batch_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
  * (opts->max_iters) or a device-side wait limit. */
 gr_status gr_sssp_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
                         int64_t *relaxations);
+
+/* Relaxations of the last completed gr_sssp on this graph that ran in pull
+ * form (host scalar; synchronises). */
+gr_status gr_sssp_pull_stats(gr_graph *g, int32_t *pulls);
 
 /* Connected components (Sec. 5.4): label[n] (int32) receives, for every
  * vertex, the smallest vertex id of its component (weakly connected
@@ -211,10 +222,20 @@ gr_status gr_pagerank(gr_graph *g, float damping, int32_t max_iter, double tol,
  * every level pushes (along out-edges, as gr_bfs traverses). srcs[k]
  * is a host array of vertices (repeats allowed). depth[k*n] (int32) receives
  * source-major results: depth[i*n + v] is the hop count from srcs[i] to v,
- * -1 where unreached, equal to gr_bfs's depth for that source. Synchronises
- * once per level (the level loop is host-driven). */
+ * -1 where unreached, equal to gr_bfs's depth for that source. The whole
+ * level loop is one cooperative kernel (a bounded grid barrier per level,
+ * directions decided on the device): the call enqueues its work and returns
+ * without synchronising. opts->max_iters > 0 caps the levels; a traversal
+ * stopped by that cap or by a barrier wait that ran out is reported by
+ * gr_bfs_batch_stats. */
 gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k,
                        int32_t *depth, const gr_opts *opts, void *stream);
+
+/* Levels of the last gr_bfs_batch on g (host output; synchronises):
+ * *levels = 1 + the largest depth reached over all lanes. GR_ETIMEOUT if
+ * that traversal stopped at a device-side limit (its depths are then
+ * incomplete). */
+gr_status gr_bfs_batch_stats(gr_graph *g, int32_t *levels);
 
 /* Betweenness centrality (Brandes; Sec. 5.3): bc[n] (double) receives
  * bc[v] = sum over s in srcs, t != s of sigma_st(v) / sigma_st, v not in
@@ -224,8 +245,11 @@ gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k,
  * in batches of 64 bit lanes (the levels as gr_bfs_batch runs them); path
  * counts are exact uint64 integers, and a batch whose counts pass 2^64 - 1
  * is counted again in FP64; dependencies are FP64. Returns GR_EINVAL if a
- * path count overflows FP64 (e.g. large grids). Synchronises once per BFS
- * level. */
+ * path count overflows FP64 (e.g. large grids). The forward levels of a
+ * batch run in one cooperative kernel that keeps every level's lane masks;
+ * it stops when it needs more mask arrays than are allocated, and the call
+ * allocates more and resumes it. The call synchronises after each batch's
+ * forward pass (for its level count) and at the end. */
 gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const gr_opts *opts, void *stream);
 

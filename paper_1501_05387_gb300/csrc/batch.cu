@@ -31,8 +31,14 @@
 // whose counts pass 2^64 - 1 (an add carries out) is counted again in FP64,
 // which holds counts up to about 1.8e308.
 //
-// The level loop is host-driven (one small read-back per level) because BC
-// keeps one mask array per level and allocates them as levels appear.
+// The forward level loop runs in one cooperative persistent kernel
+// (k_mb_do), levels separated by the bounded grid barrier, the direction of
+// every level decided on the device. Each level also emits the list of the
+// vertices that joined the next level (with its degree scan), so a push
+// level expands exactly its frontier and nothing scans all n vertices to
+// find it. A batched BFS needs no host round trip at all; BC, which keeps
+// one mask array per level, stops the kernel when the next level needs an
+// array not yet allocated, and the host allocates more and resumes it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,22 +50,29 @@
 namespace gr {
 
 constexpr int kMbThreads = 256, kMbItems = 4;
-// Batched BFS keeps the lane masks of its first kKeepLevels levels and
-// writes their depths in one pass (k_mb_depth); deeper levels write depths
-// as they are reached.
-constexpr int32_t kKeepLevels = 64;
+// Batched BFS keeps the lane masks of its first kKeepLevels levels, each in
+// its own array, and writes their depths in one pass at the end (full
+// coalesced rows); deeper levels rotate through three arrays and write their
+// depths as they are reached. On graphs of small maximum degree (meshes:
+// thousands of levels, small frontiers) no level is kept.
+constexpr int32_t kKeepLevels = 16;
 // A batched BFS level pushes when its frontier has fewer than m / kPushDiv
 // edges, and pulls over every vertex otherwise.
 constexpr long long kPushDiv = 16;
+// Graphs of at most this maximum degree (meshes) keep no level's masks.
+constexpr int32_t kLowDegreeMaxBatch = 16;
 constexpr int kMbChunk = kMbThreads * kMbItems;
 // What the forward pass counts: nothing (batched BFS), path counts in uint64,
 // or path counts in FP64 (a batch whose uint64 counts overflowed).
 enum : int { kSigNone = 0, kSigU64 = 1, kSigF64 = 2 };
 
+
 struct BatchWorkspace {
-  DevMem visit, sigma, q, counter, srcs, lmp;
-  DevMem fq, fs;  // frontier list and degree scan of the push levels
-  std::vector<DevMem *> lm;  // lm[L]: lane masks of level L
+  DevMem visit, sigma, q, counter, lmp, ctl;
+  DevMem fq, fs;    // BC backward: one level's vertex list and degree scan
+  DevMem lq[3], ls[3];  // forward: level lists (ring by level) and degree scans
+  std::vector<DevMem *> lm;  // level mask arrays ("slots")
+  int32_t uploaded = 0;      // slots whose pointers are in lmp
   ~BatchWorkspace() {
     for (DevMem *p : lm) delete p;
   }
@@ -71,6 +84,25 @@ GR_GUARD_REPORTER(guard_report_batch)
 
 namespace {
 
+// Forward state in device memory: where the level loop stands (so a
+// stopped kernel can resume), the level lists' counters and the barrier.
+struct MbCtl {
+  GridBarrier bar;
+  unsigned long long cnt3[3];  // level L+1's vertices: [31:0] count, [63:32] edges
+  unsigned long long cnt_list;  // compaction of a pulled level's list
+  int32_t level;   // next level to run
+  int32_t push;    // its direction
+  int32_t q, qe;   // its list's size and edge count
+  int32_t q_prev;  // size of the list before it
+  int32_t listed;       // the list of `level` exists (a push emitted it)
+  int32_t prev_listed;  // the list of `level` - 1 exists
+  int32_t done;
+  int32_t paused;  // stopped before `level`: it needs a slot beyond cap
+  int32_t error;   // kDevTimeout / kDevOverflow
+  int32_t levels;  // levels holding vertices (when done)
+  int32_t sig_overflow;  // a uint64 path count overflowed
+};
+
 struct MbArgs {
   const int32_t *R;
   const int32_t *C;
@@ -78,27 +110,25 @@ struct MbArgs {
   long long m;
   unsigned long long all;  // mask of the lanes in use
   unsigned long long *visit;
-  const unsigned long long *cur;  // lm[L]
-  unsigned long long *nxt;        // lm[L+1], zero on entry
-  void *sigma;                    // [n][64] uint64 or FP64 path counts, or null (BFS)
-  int32_t *sig_overflow;          // set when a uint64 path count overflows
-  int32_t *depth;                 // [k][n] or null (BC)
+  unsigned long long *const *lmp;  // level mask arrays
+  int32_t cap;        // arrays in lmp
+  int32_t keep;       // levels < keep have their own array; later ones rotate through 3
+  int32_t *lq[3];     // level lists, ring by level: lq[L % 3] lists level L
+  int32_t *ls[3];     // their exclusive degree scans
+  void *sigma;        // [n][64] uint64 or FP64 path counts, or null (BFS)
+  int32_t *depth;     // [k][n] or null (BC)
   int32_t k;
-  int32_t level;
-  unsigned long long *count;      // [31:0] vertices that joined lm[L+1], [63:32] their edges
+  int32_t symmetric;
+  int32_t max_levels;
+  MbCtl *ctl;
 };
 
-// Packed (vertices, edges) increment for a vertex that joined the next level.
-__device__ __forceinline__ unsigned long long joined(const MbArgs &a, int32_t v) {
-  return 1ull | ((unsigned long long)(uint32_t)(a.R[v + 1] - a.R[v]) << 32);
+__device__ __forceinline__ int32_t mb_slot(const MbArgs &a, int32_t L) {
+  return L < a.keep ? L : a.keep + (L - a.keep) % 3;
 }
 
 __device__ __forceinline__ unsigned long long shfl_u64(unsigned long long x, int src) {
   return __shfl_sync(0xffffffffu, x, src);
-}
-
-__device__ __forceinline__ unsigned long long shfl_down_u64(unsigned long long x, int o) {
-  return __shfl_down_sync(0xffffffffu, x, o);
 }
 
 // Path-count arithmetic in the forward pass's type: uint64 adds record a
@@ -124,36 +154,130 @@ __device__ __forceinline__ void count_atomic_add(double *p, double y, bool &) {
   atomicAdd(p, y);
 }
 
-__global__ void k_mb_init(unsigned long long *visit, unsigned long long *lm0,
-                          unsigned long long *sigma, double *q, int32_t n) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    visit[v] = 0ull;
-    lm0[v] = 0ull;
+// Zeroes what the forward reads first: visit, the arrays of levels 0 and 1,
+// the path counts and dependencies (BC) and, when no level is kept, the
+// depth output (-1: unreached; kept levels' depths are all written by the
+// end-of-run pass).
+__global__ void k_mb_init(MbArgs a, unsigned long long *sigma, double *q) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long *l0 = a.lmp[mb_slot(a, 0)], *l1 = a.lmp[mb_slot(a, 1)];
+  for (int64_t v = tid; v < a.n; v += stride) {
+    a.visit[v] = 0ull;
+    l0[v] = 0ull;
+    l1[v] = 0ull;
   }
   if (sigma) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * 64;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = tid; i < (int64_t)a.n * 64; i += stride) {
       sigma[i] = 0ull;  // 0 as uint64 and as FP64
       q[i] = 0.0;
     }
   }
+  if (a.depth && a.keep == 0)
+    for (int64_t i = tid; i < (int64_t)a.k * a.n; i += stride) a.depth[i] = -1;
 }
 
-__global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long *lm0,
-                             void *sigma, int32_t sk, int32_t n_vertices) {
+// Level 0: the sources' lanes, their path counts (1) and the level list
+// (each distinct source vertex once, with its degree scan). One block of 64
+// threads, after k_mb_init.
+struct MbSources {
+  int32_t s[64];
+};
+
+__global__ void k_mb_sources(MbArgs a, MbSources srcs, int32_t sk) {
+  __shared__ int32_t s_v[64], s_d[64];
+  __shared__ int32_t s_cnt;
   const int s = threadIdx.x;
-  if (s < k && GR_IN(srcs[s], n_vertices, 205)) {
-    const int32_t v = srcs[s];
-    atomicOr(lm0 + v, 1ull << s);
-    if (sk == kSigU64) ((unsigned long long *)sigma)[(int64_t)v * 64 + s] = 1ull;
-    if (sk == kSigF64) ((double *)sigma)[(int64_t)v * 64 + s] = 1.0;
+  if (s == 0) s_cnt = 0;
+  __syncthreads();
+  unsigned long long *l0 = a.lmp[mb_slot(a, 0)];
+  if (s < a.k && GR_IN(srcs.s[s], a.n, 205)) {
+    const int32_t v = srcs.s[s];
+    if (atomicOr(l0 + v, 1ull << s) == 0ull) {
+      const int32_t k = atomicAdd(&s_cnt, 1);
+      s_v[k] = v;
+      s_d[k] = a.R[v + 1] - a.R[v];
+    }
+    if (sk == kSigU64) ((unsigned long long *)a.sigma)[(int64_t)v * 64 + s] = 1ull;
+    if (sk == kSigF64) ((double *)a.sigma)[(int64_t)v * 64 + s] = 1.0;
+  }
+  __syncthreads();
+  if (s == 0) {
+    const int32_t cnt = s_cnt;
+    int32_t run = 0;
+    for (int32_t i = 0; i < cnt; ++i) {
+      a.lq[0][i] = s_v[i];
+      a.ls[0][i] = run;
+      run += s_d[i];
+    }
+    MbCtl *c = a.ctl;
+    grid_barrier_reset(&c->bar);
+    for (int i = 0; i < 3; ++i) c->cnt3[i] = 0ull;
+    c->cnt_list = 0ull;
+    c->listed = 1;
+    c->prev_listed = 0;
+    c->level = 0;
+    c->push = 1;
+    c->q = cnt;
+    c->qe = run;
+    c->q_prev = 0;
+    c->done = cnt == 0;
+    c->paused = 0;
+    c->error = kDevOk;
+    c->levels = cnt ? 0 : 1;
+    c->sig_overflow = 0;
   }
 }
 
-// One batched BFS pull level (no path counts): lm[L+1][v] = OR over edges
-// (v, u) of lm[L][u] & ~seen(v), seen(v) = visit[v] | lm[L][v]. Merge-based:
-// a chunk's vertex end markers and edges form one sequence of
+// Block-local list of the vertices a push level adds to the next level,
+// flushed per chunk with flush_scanned (one packed atomic per block and
+// chunk); a chunk of kMbChunk items adds at most kMbChunk vertices.
+constexpr int kMbPullItems = 8;
+constexpr int kMbPullChunk = kMbThreads * kMbPullItems;
+using MbEmitBuf = ScannedBuf<kMbChunk>;
+
+__device__ __forceinline__ void mb_emit(MbEmitBuf &em, const MbArgs &a, int32_t v) {
+  const int32_t k = atomicAdd(&em.cnt, 1);
+  em.out[k] = v;
+  em.deg[k] = a.R[v + 1] - a.R[v];
+}
+
+// Packed (vertices, edges) increment for a vertex that joined the next level.
+__device__ __forceinline__ unsigned long long joined(const MbArgs &a, int32_t v) {
+  return 1ull | ((unsigned long long)(uint32_t)(a.R[v + 1] - a.R[v]) << 32);
+}
+
+// Shared memory of the level forms (one at a time).
+union MbSmem {
+  struct {
+    int32_t end[kMbPullChunk + 1];  // end marker of each vertex, chunk-local
+    unsigned long long U[kMbPullChunk + 1];  // lanes the vertex still misses
+  } pull;
+  struct {
+    int32_t off[kMbChunk + 1];
+    unsigned long long U[kMbChunk + 1];
+  } fwd;
+  struct {
+    int32_t off[kMbChunk + 1];
+    int32_t row[kMbChunk + 1];
+    unsigned long long cur[kMbChunk + 1];
+    int32_t u[kMbChunk + 1];
+    MbEmitBuf em;
+  } push;
+  MbEmitBuf list;  // compaction of a pulled level into its list
+};
+
+// Lanes of `c` at vertex v reach their depth at level L.
+__device__ __forceinline__ void mb_write_depth(const MbArgs &a, int32_t v, unsigned long long c,
+                                               int32_t L) {
+  for (int s = 0; s < a.k; ++s)
+    if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 204))
+      a.depth[(int64_t)s * a.n + v] = L;
+}
+
+// A batched BFS pull level (no path counts): nxt[v] = OR over edges (v, u)
+// of cur[u] & ~seen(v), seen(v) = visit[v] | cur[v], for every vertex v.
+// Merge-based: a chunk's vertex end markers and edges form one sequence of
 // kMbThreads * kMbPullItems items; each thread finds its first item's
 // vertex with one search, then walks its kMbPullItems consecutive items.
 // The column and lane-mask loads of all its items are issued before any is
@@ -161,15 +285,15 @@ __global__ void k_mb_sources(const int32_t *srcs, int32_t k, unsigned long long 
 // OR of a vertex accumulates in a register. A vertex whose edges and end
 // marker all fall in one thread's items is written with a plain store (no
 // other thread touches it); the others with atomicOr. The vertex loader
-// folds lm[L] into visit and, past the kept levels, writes depth L.
-constexpr int kMbPullItems = 8, kMbPullBlocksPerSm = 6;
-__global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbArgs a) {
+// folds cur into visit and, past the kept levels, writes depth L. The level
+// counts the vertices whose mask goes from empty to non-empty (and their
+// edges); it writes no list (a push level after it compacts one).
+__device__ void mb_pull_level(const MbArgs &a, MbSmem &sm, int32_t *s_red8, int32_t L,
+                              const unsigned long long *cur, unsigned long long *nxt,
+                              unsigned long long *counter) {
   constexpr int ITEMS = kMbPullItems;
-  constexpr int CHUNK = kMbThreads * ITEMS;
-  __shared__ int32_t s_end[CHUNK + 1];  // end marker of each vertex, chunk-local
-  __shared__ unsigned long long s_U[CHUNK + 1];  // lanes the vertex still misses
-  __shared__ int32_t s_red8[kMbThreads / 32];
-  const int lane = threadIdx.x & 31;
+  constexpr int CHUNK = kMbPullChunk;
+  const bool write_depth = a.depth && L >= a.keep;
   const long long total = (long long)a.n + a.R[a.n];
   const long long nchunks = (total + CHUNK - 1) / CHUNK;
   unsigned long long new_vertices = 0;
@@ -183,18 +307,14 @@ __global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbAr
     const int32_t len = (int32_t)(d1 - d0);
     for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
       const int32_t v = i0 + kk;
-      const unsigned long long c = a.cur[v];
+      const unsigned long long c = cur[v];
       const unsigned long long seen = a.visit[v] | c;
       if (c) {
         a.visit[v] = seen;
-        if (a.depth) {
-          for (int s = 0; s < a.k; ++s)
-            if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 204))
-              a.depth[(int64_t)s * a.n + v] = a.level;
-        }
+        if (write_depth) mb_write_depth(a, v, c, L);
       }
-      s_end[kk] = (int32_t)((long long)a.R[v + 1] + v - d0);
-      s_U[kk] = a.all & ~seen;
+      sm.pull.end[kk] = (int32_t)((long long)a.R[v + 1] + v - d0);
+      sm.pull.U[kk] = a.all & ~seen;
     }
     __syncthreads();
     const int32_t k0 = min(len, (int32_t)threadIdx.x * ITEMS);
@@ -204,7 +324,7 @@ __global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbAr
       int32_t lo = 0, hi = nv;
       while (lo < hi) {
         const int32_t mid = (lo + hi) >> 1;
-        if (s_end[mid] < k0) lo = mid + 1;
+        if (sm.pull.end[mid] < k0) lo = mid + 1;
         else hi = mid;
       }
       // classify the items: end markers (bit i of `ends`) and edges, loading
@@ -217,12 +337,12 @@ __global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbAr
         const int32_t k = k0 + i;
         u[i] = -1;
         if (k < k1 && r < nv) {
-          if (s_end[r] == k) {
+          if (sm.pull.end[r] == k) {
             ends |= 1u << i;
             ++r;
           } else {
             const long long pos = j0 + e;
-            if (s_U[r] && GR_IN(pos, a.m, 202)) u[i] = (int32_t)pos;
+            if (sm.pull.U[r] && GR_IN(pos, a.m, 202)) u[i] = (int32_t)pos;
             ++e;
           }
         }
@@ -231,7 +351,7 @@ __global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbAr
       for (int i = 0; i < ITEMS; ++i) u[i] = u[i] >= 0 ? a.C[u[i]] : -1;
       unsigned long long b[ITEMS];
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i) b[i] = (u[i] >= 0 && GR_IN(u[i], a.n, 203)) ? a.cur[u[i]] : 0ull;
+      for (int i = 0; i < ITEMS; ++i) b[i] = (u[i] >= 0 && GR_IN(u[i], a.n, 203)) ? cur[u[i]] : 0ull;
       // walk: OR per vertex, written at its end marker
       r = lo;
       unsigned long long acc = 0ull;
@@ -244,9 +364,9 @@ __global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbAr
             if (acc) {
               const int32_t v = i0 + r;
               if (whole) {
-                a.nxt[v] = acc;
+                nxt[v] = acc;
                 new_vertices += joined(a, v);
-              } else if (!atomicOr(a.nxt + v, acc)) {
+              } else if (!atomicOr(nxt + v, acc)) {
                 new_vertices += joined(a, v);
               }
             }
@@ -254,31 +374,28 @@ __global__ void __launch_bounds__(kMbThreads, kMbPullBlocksPerSm) k_mb_pull(MbAr
             whole = true;
             ++r;
           } else {
-            acc |= b[i] & s_U[r];
+            acc |= b[i] & sm.pull.U[r];
           }
         }
       }
-      if (acc && r < nv && !atomicOr(a.nxt + (i0 + r), acc))  // continues past k1
+      if (acc && r < nv && !atomicOr(nxt + (i0 + r), acc))  // continues past k1
         new_vertices += joined(a, i0 + r);
     }
     __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) new_vertices += __shfl_xor_sync(0xffffffffu, new_vertices, o);
-  if (lane == 0 && new_vertices) atomicAdd(a.count, new_vertices);
+  if ((threadIdx.x & 31) == 0 && new_vertices) atomicAdd(counter, new_vertices);
 }
 
-// One BC forward pull level: lm[L+1][v] = OR over edges (v,u) of
-// lm[L][u] & ~seen(v), seen(v) = visit[v] | lm[L][v], and the path counts of
-// the newly reached lanes. The vertex loader of each chunk folds lm[L] into
-// visit (idempotent, so chunks sharing a vertex may both do it).
+// A BC forward pull level: nxt[v] = OR over edges (v,u) of cur[u] &
+// ~seen(v), seen(v) = visit[v] | cur[v], and the path counts of the newly
+// reached lanes. The vertex loader of each chunk folds cur into visit
+// (idempotent, so chunks sharing a vertex may both do it).
 template <int SK>
-__global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
-  static_assert(SK != kSigNone, "batched BFS pulls with k_mb_pull");
+__device__ void mb_forward_level(const MbArgs &a, MbSmem &sm, int32_t *s_red8,
+                                 const unsigned long long *cur, unsigned long long *nxt,
+                                 unsigned long long *counter, bool &ovf) {
   using T = CountT<SK>;
-  bool ovf = false;
-  __shared__ int32_t s_off[kMbChunk + 1];
-  __shared__ unsigned long long s_U[kMbChunk + 1];
-  __shared__ int32_t s_red8[kMbThreads / 32];
   const int lane = threadIdx.x & 31;
   const long long total = (long long)a.n + a.R[a.n];
   const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
@@ -292,18 +409,11 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
     const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
     for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
       const int32_t v = i0 + kk;
-      const unsigned long long c = a.cur[v];
+      const unsigned long long c = cur[v];
       const unsigned long long seen = a.visit[v] | c;
-      if (c) {
-        a.visit[v] = seen;
-        if (a.depth) {
-          for (int s = 0; s < a.k; ++s)
-            if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 204))
-            a.depth[(int64_t)s * a.n + v] = a.level;
-        }
-      }
-      s_off[kk] = a.R[v];
-      s_U[kk] = a.all & ~seen;
+      if (c) a.visit[v] = seen;
+      sm.fwd.off[kk] = a.R[v];
+      sm.fwd.U[kk] = a.all & ~seen;
     }
     __syncthreads();
     const int32_t ne = (int32_t)(j1 - j0);
@@ -316,70 +426,341 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_forward(MbArgs a) {
         int32_t lo = 0, hi = nv - 1;
         while (lo < hi) {
           const int32_t mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= e) lo = mid;
+          if (sm.fwd.off[mid] <= e) lo = mid;
           else hi = mid - 1;
         }
         owner = i0 + lo;
         if (!GR_IN(owner, a.n, 201)) owner = -1;
-        const unsigned long long U = owner >= 0 ? s_U[lo] : 0ull;
+        const unsigned long long U = owner >= 0 ? sm.fwd.U[lo] : 0ull;
         if (U && GR_IN(e, a.m, 202)) {
           u = a.C[e];
-          bits = GR_IN(u, a.n, 203) ? (a.cur[u] & U) : 0ull;
+          bits = GR_IN(u, a.n, 203) ? (cur[u] & U) : 0ull;
         }
       }
-      {
-        // the warp serves the edges with bits one at a time: lane l handles
-        // BFS lanes l and l + 32 of the predecessor's 64 path counts; a half
-        // with no bits set is skipped by the whole warp
-        T *const sigma = (T *)a.sigma;
-        uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
-        int32_t cur_owner = -1;
-        unsigned long long orbits = 0ull;
-        T acc0 = T(0), acc1 = T(0);
-        while (act) {
-          const int j = __ffs(act) - 1;
-          act &= act - 1u;
-          const int32_t ov = __shfl_sync(0xffffffffu, owner, j);
-          const int32_t uj = __shfl_sync(0xffffffffu, u, j);
-          const unsigned long long bj = shfl_u64(bits, j);
-          if (ov != cur_owner) {
-            if (cur_owner >= 0) {
-              T *sg = sigma + (int64_t)cur_owner * 64;
-              if ((orbits >> lane) & 1ull) count_atomic_add(sg + lane, acc0, ovf);
-              if ((orbits >> (lane + 32)) & 1ull) count_atomic_add(sg + lane + 32, acc1, ovf);
-              if (lane == 0) {
-                const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
-                if (!old) new_vertices += joined(a, cur_owner);
-              }
-            }
-            cur_owner = ov;
-            orbits = 0ull;
-            acc0 = acc1 = T(0);
+      // the warp serves the edges with bits one at a time: lane l handles
+      // BFS lanes l and l + 32 of the predecessor's 64 path counts; a half
+      // with no bits set is skipped by the whole warp
+      T *const sigma = (T *)a.sigma;
+      uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
+      int32_t cur_owner = -1;
+      unsigned long long orbits = 0ull;
+      T acc0 = T(0), acc1 = T(0);
+      while (act) {
+        const int j = __ffs(act) - 1;
+        act &= act - 1u;
+        const int32_t ov = __shfl_sync(0xffffffffu, owner, j);
+        const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+        const unsigned long long bj = shfl_u64(bits, j);
+        if (ov != cur_owner) {
+          if (cur_owner >= 0) {
+            T *sg = sigma + (int64_t)cur_owner * 64;
+            if ((orbits >> lane) & 1ull) count_atomic_add(sg + lane, acc0, ovf);
+            if ((orbits >> (lane + 32)) & 1ull) count_atomic_add(sg + lane + 32, acc1, ovf);
+            if (lane == 0 && !atomicOr(nxt + cur_owner, orbits))
+              new_vertices += joined(a, cur_owner);
           }
-          orbits |= bj;
-          const T *su = sigma + (int64_t)uj * 64;
-          if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 = count_add(acc0, su[lane], ovf);
-          if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull))
-            acc1 = count_add(acc1, su[lane + 32], ovf);
+          cur_owner = ov;
+          orbits = 0ull;
+          acc0 = acc1 = T(0);
         }
-        if (cur_owner >= 0) {
-          T *sg = sigma + (int64_t)cur_owner * 64;
-          if ((orbits >> lane) & 1ull) count_atomic_add(sg + lane, acc0, ovf);
-          if ((orbits >> (lane + 32)) & 1ull) count_atomic_add(sg + lane + 32, acc1, ovf);
-          if (lane == 0) {
-            const unsigned long long old = atomicOr(a.nxt + cur_owner, orbits);
-            if (!old) new_vertices += joined(a, cur_owner);
-          }
-        }
+        orbits |= bj;
+        const T *su = sigma + (int64_t)uj * 64;
+        if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 = count_add(acc0, su[lane], ovf);
+        if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull))
+          acc1 = count_add(acc1, su[lane + 32], ovf);
+      }
+      if (cur_owner >= 0) {
+        T *sg = sigma + (int64_t)cur_owner * 64;
+        if ((orbits >> lane) & 1ull) count_atomic_add(sg + lane, acc0, ovf);
+        if ((orbits >> (lane + 32)) & 1ull) count_atomic_add(sg + lane + 32, acc1, ovf);
+        if (lane == 0 && !atomicOr(nxt + cur_owner, orbits)) new_vertices += joined(a, cur_owner);
       }
     }
     __syncthreads();
   }
-  // new_vertices counts runs whose atomicOr found an empty mask: exactly the
-  // vertices that joined lm[L+1] (and their edges)
   for (int o = 16; o > 0; o >>= 1) new_vertices += __shfl_xor_sync(0xffffffffu, new_vertices, o);
-  if (lane == 0 && new_vertices) atomicAdd(a.count, new_vertices);
-  if (SK == kSigU64 && __any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(a.sig_overflow, 1);
+  if (lane == 0 && new_vertices) atomicAdd(counter, new_vertices);
+}
+
+// A push level, for levels whose list has few edges (the sources' level,
+// the last levels, every level of a mesh): the listed vertices send their
+// lanes over their edges (merge-path chunks over the list's degree scan).
+// For an edge (u, v): bits = cur[u] & ~seen(v), seen(v) = visit[v] | cur[v]
+// (v may be on the list itself, its cur not yet folded into visit), and
+// nxt[v] |= bits; with SIGMA (BC's forward pass) those lanes also add u's
+// path counts to v's, the warp serving such edges one at a time. The
+// loader folds each listed vertex's cur into visit and, past the kept
+// levels, writes its depths.
+template <int SK>
+__device__ void mb_push_level(const MbArgs &a, MbSmem &sm, int32_t *s_red8, int32_t L,
+                              const unsigned long long *cur,
+                              unsigned long long *nxt, const int32_t *Q, const int32_t *S,
+                              int32_t q, int32_t qe, int32_t *Qn, int32_t *Sn,
+                              unsigned long long *counter, bool &ovf) {
+  constexpr bool SIGMA = SK != kSigNone;
+  using T = CountT<SK == kSigNone ? kSigU64 : SK>;
+  const bool write_depth = a.depth && L >= a.keep;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)q + qe;
+  const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
+  // the emission buffer shares its storage with the other level forms: its
+  // count starts at zero here
+  if (threadIdx.x == 0) sm.push.em.cnt = 0;
+  __syncthreads();
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * kMbChunk;
+    const long long d1 = min(d0 + kMbChunk, total);
+    int32_t i0, i1;
+    block_chunk_bounds<kMbThreads>(S, q, qe, d0, d1, kMbChunk, s_red8, &i0, &i1);
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
+    for (int32_t k = threadIdx.x; k < nv; k += kMbThreads) {
+      const int32_t i = i0 + k;
+      const int32_t u = GR_IN(i, a.n + 1, 207) ? Q[i] : 0;
+      const bool ok = GR_IN(u, a.n, 208);
+      const unsigned long long c = ok ? cur[u] : 0ull;
+      if (c) {
+        a.visit[u] |= c;
+        if (write_depth) mb_write_depth(a, u, c, L);
+      }
+      sm.push.off[k] = S[i];
+      sm.push.row[k] = ok ? a.R[u] : 0;
+      sm.push.cur[k] = c;
+      if (SIGMA) sm.push.u[k] = ok ? u : 0;
+    }
+    __syncthreads();
+    const int32_t ne = (int32_t)(j1 - j0);
+    for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
+      const int32_t k = kb + threadIdx.x;
+      unsigned long long bits = 0ull;
+      int32_t v = -1, u = 0;
+      if (k < ne) {
+        const int32_t er = (int32_t)(j0 + k);
+        int32_t lo = 0, hi = nv - 1;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi + 1) >> 1;
+          if (sm.push.off[mid] <= er) lo = mid;
+          else hi = mid - 1;
+        }
+        const long long e = (long long)sm.push.row[lo] + (er - sm.push.off[lo]);
+        v = GR_IN(e, a.m, 209) ? a.C[e] : -1;
+        if (v >= 0 && GR_IN(v, a.n, 210)) {
+          bits = sm.push.cur[lo] & ~(a.visit[v] | cur[v]);
+          if (bits && !atomicOr(nxt + v, bits)) mb_emit(sm.push.em, a, v);
+          if (SIGMA) u = sm.push.u[lo];
+        }
+      }
+      if (SIGMA) {
+        T *const sigma = (T *)a.sigma;
+        uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
+        while (act) {
+          const int j = __ffs(act) - 1;
+          act &= act - 1u;
+          const int32_t vj = __shfl_sync(0xffffffffu, v, j);
+          const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+          const unsigned long long bj = shfl_u64(bits, j);
+          const T *su = sigma + (int64_t)uj * 64;
+          T *sv = sigma + (int64_t)vj * 64;
+          if ((bj >> lane) & 1ull) count_atomic_add(sv + lane, su[lane], ovf);
+          if ((bj >> (lane + 32)) & 1ull) count_atomic_add(sv + lane + 32, su[lane + 32], ovf);
+        }
+      }
+    }
+    flush_scanned<kMbThreads>(sm.push.em, counter, Qn, Sn, (long long)a.n + 1);
+  }
+}
+
+// The list of a level reached by a pull (the vertices with lanes in cur,
+// with their degree scan), for the push level that expands it.
+__device__ void mb_compact_list(const MbArgs &a, MbSmem &sm, const unsigned long long *cur,
+                                int32_t *Q, int32_t *S, unsigned long long *counter) {
+  constexpr int PER = kMbChunk / kMbThreads;
+  // the list buffer shares its storage with the level forms: its count
+  // starts at zero here
+  if (threadIdx.x == 0) sm.list.cnt = 0;
+  __syncthreads();
+  for (int64_t base = (int64_t)blockIdx.x * kMbChunk; base < a.n;
+       base += (int64_t)gridDim.x * kMbChunk) {  // block-uniform
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int64_t v = base + j * kMbThreads + threadIdx.x;
+      const bool take = v < a.n && cur[v] != 0ull;
+      emit_scanned(sm.list, take, (int32_t)v, take ? a.R[v + 1] - a.R[v] : 0);
+    }
+    flush_scanned<kMbThreads>(sm.list, counter, Q, S, (long long)a.n + 1);
+  }
+}
+
+// Depths of the kept levels [0, levels) from their lane masks, written once
+// for every (lane, vertex), in full coalesced rows: for each lane s,
+// depth[s][v] = the level L whose mask holds bit s (-1 if none). The masks
+// of one vertex are disjoint, so the level of every lane follows from bit
+// slices: slice j is the OR of the masks of the levels whose index has bit j
+// set.
+__device__ void mb_depth_pass(const MbArgs &a, int32_t levels) {
+  constexpr int kSlices = 6;  // levels < 64
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nr = ((int64_t)a.n + 31) & ~31ll;  // warp-uniform bound
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nr; v += stride) {
+    unsigned long long b[kSlices] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull}, reached = 0ull;
+    if (v < a.n) {
+      for (int32_t L = 0; L < levels; ++L) {
+        const unsigned long long m = a.lmp[L][v];
+        reached |= m;
+#pragma unroll
+        for (int j = 0; j < kSlices; ++j)
+          if ((L >> j) & 1) b[j] |= m;
+      }
+    }
+    for (int32_t s = 0; s < a.k; ++s) {
+      int32_t d = -1;
+      if ((reached >> s) & 1ull) {
+        d = 0;
+#pragma unroll
+        for (int j = 0; j < kSlices; ++j) d |= (int32_t)((b[j] >> s) & 1ull) << j;
+      }
+      if (v < a.n) a.depth[(int64_t)s * a.n + v] = d;
+    }
+  }
+}
+
+// Blocks per SM of k_mb_do: the batched BFS at 5 (48 registers; 7.48 ms
+// for 64 sources on R-MAT s23 against 8.25 ms at 6), BC at 6 (116 ms
+// against 118 ms at 5).
+template <int SK>
+constexpr int mb_do_blocks_per_sm() { return SK == kSigNone ? 5 : 6; }
+
+// The forward levels in one cooperative kernel. Every block runs every
+// level; levels are separated by one bounded grid barrier, after which each
+// block reads the level's packed counter (published with the release on
+// large grids) and takes the same decisions: stop when no vertex joined,
+// push when the next level's vertices have fewer than m / kPushDiv edges
+// (or the graph is directed), else pull. A push level expands the list of
+// its level (emitted by the push before it, or compacted from the masks
+// after a pull, which writes no list). Lane-mask arrays: the one of level
+// L + 2 is cleared while level L runs (all of it for a kept level, an
+// array's first use in this run or when level L - 1, its last user, has no
+// list; otherwise only the entries on that list). The kernel stops before a
+// level whose arrays are not allocated (BC only) and records where;
+// launched again, it resumes.
+// Loop state of k_mb_do, the same in every block; kept in shared memory so
+// that the level bodies have the registers to themselves.
+struct MbLoop {
+  int32_t L, push, q, qe, q_prev, listed, prev_listed;
+};
+
+template <int SK>
+__global__ void __launch_bounds__(kMbThreads, mb_do_blocks_per_sm<SK>()) k_mb_do(MbArgs a) {
+  MbCtl *c = a.ctl;
+  __shared__ MbSmem sm;
+  __shared__ int32_t s_red8[kMbThreads / 32];
+  __shared__ MbLoop st;
+  if (threadIdx.x == 0) {
+    st.L = c->level;
+    st.push = c->push;
+    st.q = c->q;
+    st.qe = c->qe;
+    st.q_prev = c->q_prev;
+    st.listed = c->listed;
+    st.prev_listed = c->prev_listed;
+  }
+  __syncthreads();
+  if (c->done) return;
+  int32_t gen = 0;
+  bool ovf = false;
+  for (;;) {
+    const int32_t L = st.L;
+    if (mb_slot(a, L + 1) >= a.cap || (L + 2 < a.keep && L + 2 >= a.cap)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->level = L;
+        c->push = st.push;
+        c->q = st.q;
+        c->qe = st.qe;
+        c->q_prev = st.q_prev;
+        c->listed = st.listed;
+        c->prev_listed = st.prev_listed;
+        c->paused = 1;
+      }
+      break;
+    }
+    if (a.depth && a.keep > 0 && L == a.keep) {
+      // every kept level is complete: their depths first, then the later
+      // levels' writes
+      mb_depth_pass(a, a.keep);
+      if (!grid_sync(&c->bar, &c->error, gen)) break;
+    }
+    const unsigned long long *cur = a.lmp[mb_slot(a, L)];
+    unsigned long long *nxt = a.lmp[mb_slot(a, L + 1)];
+    if (st.push && !st.listed) {
+      mb_compact_list(a, sm, cur, a.lq[L % 3], a.ls[L % 3], &c->cnt_list);
+      if (!grid_sync(&c->bar, &c->error, gen)) break;
+      if (threadIdx.x == 0) st.listed = 1;
+      if (blockIdx.x == 0 && threadIdx.x == 0) c->cnt_list = 0ull;  // next use: a barrier later
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->cnt3[(L + 2) % 3] = 0ull;
+    {
+      const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+      const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+      const int32_t s2 = mb_slot(a, L + 2);
+      if (s2 < a.cap) {
+        unsigned long long *clr = a.lmp[s2];
+        if (L - 1 < a.keep || !st.prev_listed) {
+          for (int64_t v = tid; v < a.n; v += stride) clr[v] = 0ull;
+        } else {
+          const int32_t *Qp = a.lq[(L + 2) % 3];  // level L - 1's list
+          for (int64_t i = tid; i < st.q_prev; i += stride) {
+            const int32_t v = Qp[i];
+            if (GR_IN(v, a.n, 211)) clr[v] = 0ull;
+          }
+        }
+      }
+    }
+    unsigned long long *counter = &c->cnt3[(L + 1) % 3];
+    if (st.push) {
+      mb_push_level<SK>(a, sm, s_red8, L, cur, nxt, a.lq[L % 3], a.ls[L % 3], st.q, st.qe,
+                        a.lq[(L + 1) % 3], a.ls[(L + 1) % 3], counter, ovf);
+    } else if (SK == kSigNone) {
+      mb_pull_level(a, sm, s_red8, L, cur, nxt, counter);
+    } else {
+      mb_forward_level<SK == kSigNone ? kSigU64 : SK>(a, sm, s_red8, cur, nxt, counter, ovf);
+    }
+    unsigned long long pk = 0ull;
+    if (gridDim.x > kFlatBarrierBlocks) {
+      if (!grid_sync(&c->bar, &c->error, gen, counter, &pk)) break;
+    } else {
+      if (!grid_sync(&c->bar, &c->error, gen)) break;
+      pk = *(volatile unsigned long long *)counter;
+    }
+    // grid_sync ends with a block barrier: every thread has read st
+    const int32_t qn = (int32_t)(pk & 0xFFFFFFFFull);
+    const long long en = (long long)(pk >> 32);
+    const int32_t levels = L + 1;  // levels 0 .. L hold vertices
+    const bool done = qn == 0;
+    const bool overflow = !done && levels >= a.max_levels;
+    if (done || overflow) {
+      if (done && a.depth && a.keep > 0 && levels <= a.keep) mb_depth_pass(a, levels);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->level = levels;
+        c->levels = levels;
+        c->q = 0;
+        if (overflow) c->error = kDevOverflow;
+        c->done = 1;
+      }
+      break;
+    }
+    if (threadIdx.x == 0) {
+      st.prev_listed = st.listed;
+      st.listed = st.push;  // a push emitted the next level's list
+      st.L = levels;
+      st.q_prev = st.q;
+      st.q = qn;
+      st.qe = (int32_t)en;
+      st.push = (!a.symmetric || en * kPushDiv < a.m) ? 1 : 0;
+    }
+    __syncthreads();
+  }
+  if (SK == kSigU64 && __any_sync(0xffffffffu, ovf) && (threadIdx.x & 31) == 0)
+    atomicOr(&c->sig_overflow, 1);
 }
 
 struct BcBackArgs {
@@ -559,188 +940,42 @@ __global__ void k_bc_finalize(const unsigned long long *lv, const int32_t *Q,
   }
 }
 
-// Push form of a batched BFS level, for frontiers with few edges (the
-// sources' level and the last levels): instead of every vertex pulling from
-// all its neighbours, the frontier's vertices push their lanes.
-// k_mb_compact lists the frontier (vertices with lanes in lm[L]) with its
-// degree scan, folds lm[L] into visit (the pull's vertex loader does that)
-// and, past the kept levels, writes the level's depths; k_mb_push sends, over
-// every edge (u, v) of the frontier, u's lanes that v has not seen to v's
-// mask in lm[L+1] (merge-path chunks over the listed vertices' edges).
-__global__ void __launch_bounds__(kMbThreads) k_mb_compact(MbArgs a, int32_t *Q, int32_t *S,
-                                                            unsigned long long *fpacked) {
-  __shared__ ScannedBuf<kMbChunk> buf;
-  if (threadIdx.x == 0) buf.cnt = 0;
-  __syncthreads();
-  constexpr int PER = kMbChunk / kMbThreads;
-  for (int64_t base = (int64_t)blockIdx.x * kMbChunk; base < a.n;
-       base += (int64_t)gridDim.x * kMbChunk) {  // block-uniform
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int64_t v = base + j * kMbThreads + threadIdx.x;
-      int32_t d = 0;
-      bool take = false;
-      if (v < a.n) {
-        const unsigned long long c = a.cur[v];
-        if (c) {
-          a.visit[v] |= c;
-          if (a.depth) {
-            for (int s = 0; s < a.k; ++s)
-              if (((c >> s) & 1ull) && GR_IN((int64_t)s * a.n + v, (int64_t)a.k * a.n, 206))
-                a.depth[(int64_t)s * a.n + v] = a.level;
-          }
-          d = a.R[v + 1] - a.R[v];
-          take = d > 0;
-        }
-      }
-      emit_scanned(buf, take, (int32_t)v, d);
-    }
-    flush_scanned<kMbThreads>(buf, fpacked, Q, S, (long long)a.n + 1);
-  }
-}
-
-__global__ void k_mb_close(const unsigned long long *fpacked, int32_t *S) {
-  const unsigned long long p = *fpacked;
-  S[(int32_t)(p & 0xFFFFFFFFull)] = (int32_t)(p >> 32);
-}
-
-// With SIGMA (BC's forward pass) the lanes newly sent to v also add u's path
-// counts to v's: the warp serves such edges one at a time, lane l adding
-// lanes l and l + 32.
-template <int SK>
-__global__ void __launch_bounds__(kMbThreads) k_mb_push(MbArgs a, const int32_t *Q,
-                                                         const int32_t *S,
-                                                         const unsigned long long *fpacked) {
-  constexpr bool SIGMA = SK != kSigNone;
-  using T = CountT<SK>;
-  bool ovf = false;
-  __shared__ int32_t s_off[kMbChunk + 1];
-  __shared__ int32_t s_row[kMbChunk + 1];
-  __shared__ unsigned long long s_cur[kMbChunk + 1];
-  __shared__ int32_t s_u[SIGMA ? kMbChunk + 1 : 1];
-  __shared__ int32_t s_red8[kMbThreads / 32];
-  const int lane = threadIdx.x & 31;
-  const unsigned long long fp = *fpacked;
-  const int32_t q = (int32_t)(fp & 0xFFFFFFFFull);
-  const int32_t qe = (int32_t)(fp >> 32);
-  const long long total = (long long)q + qe;
-  const long long nchunks = (total + kMbChunk - 1) / kMbChunk;
-  unsigned long long added = 0;
-  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-    const long long d0 = chunk * kMbChunk;
-    const long long d1 = min(d0 + kMbChunk, total);
-    int32_t i0, i1;
-    block_chunk_bounds<kMbThreads>(S, q, qe, d0, d1, kMbChunk, s_red8, &i0, &i1);
-    const long long j0 = d0 - i0, j1 = d1 - i1;
-    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
-    for (int32_t k = threadIdx.x; k < nv; k += kMbThreads) {
-      const int32_t i = i0 + k;
-      const int32_t u = GR_IN(i, a.n + 1, 207) ? Q[i] : 0;
-      const bool ok = GR_IN(u, a.n, 208);
-      s_off[k] = (i == q) ? qe : S[i];
-      s_row[k] = ok ? a.R[u] : 0;
-      s_cur[k] = ok ? a.cur[u] : 0ull;
-      if (SIGMA) s_u[k] = ok ? u : 0;
-    }
-    __syncthreads();
-    const int32_t ne = (int32_t)(j1 - j0);
-    for (int32_t kb = 0; kb < ne; kb += kMbThreads) {
-      const int32_t k = kb + threadIdx.x;
-      unsigned long long bits = 0ull;
-      int32_t v = -1, u = 0;
-      if (k < ne) {
-        const int32_t er = (int32_t)(j0 + k);
-        int32_t lo = 0, hi = nv - 1;
-        while (lo < hi) {
-          const int32_t mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= er) lo = mid;
-          else hi = mid - 1;
-        }
-        const long long e = (long long)s_row[lo] + (er - s_off[lo]);
-        v = GR_IN(e, a.m, 209) ? a.C[e] : -1;
-        if (v >= 0 && GR_IN(v, a.n, 210)) {
-          bits = s_cur[lo] & ~a.visit[v];
-          if (bits) {
-            const unsigned long long old = atomicOr(a.nxt + v, bits);
-            if (!old) added += joined(a, v);
-          }
-          if (SIGMA) u = s_u[lo];
-        }
-      }
-      if (SIGMA) {
-        T *const sigma = (T *)a.sigma;
-        uint32_t act = __ballot_sync(0xffffffffu, bits != 0ull);
-        while (act) {
-          const int j = __ffs(act) - 1;
-          act &= act - 1u;
-          const int32_t vj = __shfl_sync(0xffffffffu, v, j);
-          const int32_t uj = __shfl_sync(0xffffffffu, u, j);
-          const unsigned long long bj = shfl_u64(bits, j);
-          const T *su = sigma + (int64_t)uj * 64;
-          T *sv = sigma + (int64_t)vj * 64;
-          if ((bj >> lane) & 1ull) count_atomic_add(sv + lane, su[lane], ovf);
-          if ((bj >> (lane + 32)) & 1ull) count_atomic_add(sv + lane + 32, su[lane + 32], ovf);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  for (int o = 16; o > 0; o >>= 1) added += __shfl_xor_sync(0xffffffffu, added, o);
-  if (lane == 0 && added) atomicAdd(a.count, added);
-  if (SK == kSigU64 && __any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(a.sig_overflow, 1);
-}
-
-// Depths of a batched BFS from its per-level lane masks, written once, in
-// full coalesced rows: for each lane s, depth[s][v] = the level L whose mask
-// lm[L][v] holds bit s (-1 if none). The masks of one vertex are disjoint,
-// so the level of every lane follows from six bit slices: slice j is the OR
-// of the masks of the levels whose index has bit j set.
-__global__ void k_mb_depth(const unsigned long long *const *lm, int32_t levels, int32_t n,
-                           int32_t k, int32_t *depth) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t nr = ((int64_t)n + 31) & ~31ll;  // warp-uniform bound
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nr; v += stride) {
-    unsigned long long b[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull}, reached = 0ull;
-    if (v < n) {
-      for (int32_t L = 0; L < levels; ++L) {
-        const unsigned long long m = lm[L][v];
-        reached |= m;
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
-          if ((L >> j) & 1) b[j] |= m;
-      }
-    }
-    for (int32_t s = 0; s < k; ++s) {
-      int32_t d = -1;
-      if ((reached >> s) & 1ull) {
-        d = 0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) d |= (int32_t)((b[j] >> s) & 1ull) << j;
-      }
-      if (v < n) depth[(int64_t)s * n + v] = d;
-    }
-  }
-}
-
 __global__ void k_fill_f64(double *x, int64_t n, double val) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = val;
 }
 
+// Before k_mb_do runs again after it stopped for more level arrays: a fresh
+// barrier (its generation restarts with every launch).
+__global__ void k_mb_resume(MbCtl *c) {
+  grid_barrier_reset(&c->bar);
+  c->paused = 0;
+}
+
 }  // namespace
 
+// Levels of a batched BFS kept in their own mask arrays on this graph.
+static int32_t bfs_keep_levels(const gr_graph *g) {
+  return g->max_degree <= kLowDegreeMaxBatch ? 0 : kKeepLevels;
+}
+
 size_t batch_ws_bytes(const gr_graph *g) {
-  // visit masks, the level masks of a typical traversal, the push frontier
-  return 12 * sizeof(unsigned long long) * (size_t)g->n + 512;
+  // visit masks, the level arrays of a batched BFS, the level lists
+  const size_t n = (size_t)g->n;
+  return sizeof(unsigned long long) * n * (1 + bfs_keep_levels(g) + 3) +
+         3 * sizeof(int32_t) * (2 * n + 3) + sizeof(MbCtl) + 4096;
 }
 
 gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out) {
   std::unique_ptr<BatchWorkspace> ws(new BatchWorkspace());
-  GR_TRY(ws->lmp.alloc(sizeof(unsigned long long *) * kKeepLevels, "level mask table"));
   GR_TRY(ws->visit.alloc(sizeof(unsigned long long) * (size_t)g->n, "lane visit masks"));
   GR_TRY(ws->counter.alloc(sizeof(unsigned long long) * 4, "batch counters"));
-  GR_TRY(ws->srcs.alloc(sizeof(int32_t) * 64, "batch sources"));
+  GR_TRY(ws->ctl.alloc(sizeof(MbCtl), "batch control"));
+  for (int i = 0; i < 3; ++i) {
+    GR_TRY(ws->lq[i].alloc(sizeof(int32_t) * ((size_t)g->n + 1), "batch level list"));
+    GR_TRY(ws->ls[i].alloc(sizeof(int32_t) * ((size_t)g->n + 2), "batch level list scan"));
+  }
   *out = ws.release();
   return GR_OK;
 }
@@ -759,137 +994,134 @@ static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_b
   return GR_OK;
 }
 
-// level masks, allocated as levels appear (zeroed before use)
-static gr_status level_mask(gr_graph *g, BatchWorkspace *ws, size_t L, cudaStream_t s,
-                            unsigned long long **out) {
-  while (ws->lm.size() <= L) {
-    std::unique_ptr<DevMem> m(new DevMem());
-    GR_TRY(m->alloc(sizeof(unsigned long long) * (size_t)g->n, "level lane masks"));
-    ws->lm.push_back(m.release());
+// At least `slots` level mask arrays, their device pointers in lmp. New
+// arrays are zeroed on `s` (the forward clears the arrays it reuses itself).
+static gr_status ensure_slots(gr_graph *g, BatchWorkspace *ws, int32_t slots, cudaStream_t s) {
+  const size_t bytes = sizeof(unsigned long long) * (size_t)g->n;
+  if ((int32_t)ws->lm.size() < slots) {
+    // the old table may still be read by enqueued work
+    GR_CUDA(cudaStreamSynchronize(s));
+    while ((int32_t)ws->lm.size() < slots) {
+      std::unique_ptr<DevMem> m(new DevMem());
+      GR_TRY(m->alloc(bytes, "level lane masks"));
+      GR_CUDA(cudaMemsetAsync(m->p, 0, bytes, s));
+      ws->lm.push_back(m.release());
+    }
   }
-  GR_CUDA(cudaMemsetAsync(ws->lm[L]->p, 0, sizeof(unsigned long long) * (size_t)g->n, s));
-  *out = ws->lm[L]->as<unsigned long long>();
+  if (ws->uploaded < slots || !ws->lmp.p) {
+    const int32_t cap = (int32_t)ws->lm.size();
+    std::vector<unsigned long long *> ptrs(cap);
+    for (int32_t i = 0; i < cap; ++i) ptrs[i] = ws->lm[i]->as<unsigned long long>();
+    if (ws->lmp.bytes < sizeof(void *) * (size_t)cap) {
+      GR_CUDA(cudaStreamSynchronize(s));
+      GR_TRY(ws->lmp.alloc(sizeof(void *) * (size_t)std::max<int32_t>(cap, 64), "level mask table"));
+    }
+    // pageable source: staged before the call returns, copied in stream order
+    GR_CUDA(cudaMemcpyAsync(ws->lmp.p, ptrs.data(), sizeof(void *) * (size_t)cap,
+                            cudaMemcpyHostToDevice, s));
+    ws->uploaded = cap;
+  }
   return GR_OK;
 }
 
-// Forward levels of one batch of k <= 64 sources, counting paths as `sk`
-// says. Returns the number of levels holding vertices (the sources' level
-// included); with kSigU64, *overflowed tells whether a count passed 2^64 - 1.
-static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
-                             int32_t *depth, int sk, cudaStream_t s,
-                             int32_t max_levels, int32_t *levels_out,
-                             bool *overflowed = nullptr) {
-  const bool with_sigma = sk != kSigNone;
-  const int grid = g->num_sms * 8;
-  unsigned long long *lm0;
-  GR_TRY(level_mask(g, ws, 0, s, &lm0));
-  int32_t *sig_overflow = (int32_t *)(ws->counter.as<unsigned long long>() + 3);
-  if (with_sigma) GR_CUDA(cudaMemsetAsync(sig_overflow, 0, sizeof(int32_t), s));
-  k_mb_init<<<grid, 256, 0, s>>>(ws->visit.as<unsigned long long>(), lm0,
-                                 with_sigma ? ws->sigma.as<unsigned long long>() : nullptr,
-                                 with_sigma ? ws->q.as<double>() : nullptr, g->n);
-  GR_CUDA(cudaMemcpyAsync(ws->srcs.p, h_srcs, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
-  k_mb_sources<<<1, 64, 0, s>>>(ws->srcs.as<int32_t>(), k, lm0,
-                                with_sigma ? ws->sigma.p : nullptr, sk, g->n);
-  GR_CUDA(cudaGetLastError());
+static MbArgs mb_args(gr_graph *g, BatchWorkspace *ws, int32_t k, int32_t *depth, int32_t keep,
+                      int32_t max_levels, bool with_sigma) {
   MbArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.R = g->row_off.as<int32_t>();
   a.C = g->col.as<int32_t>();
   a.n = g->n;
   a.m = g->m;
   a.all = k == 64 ? ~0ull : ((1ull << k) - 1ull);
   a.visit = ws->visit.as<unsigned long long>();
+  a.lmp = (unsigned long long *const *)ws->lmp.p;
+  a.cap = (int32_t)ws->lm.size();
+  a.keep = keep;
+  for (int i = 0; i < 3; ++i) {
+    a.lq[i] = ws->lq[i].as<int32_t>();
+    a.ls[i] = ws->ls[i].as<int32_t>();
+  }
   a.sigma = with_sigma ? ws->sigma.p : nullptr;
-  a.sig_overflow = sig_overflow;
   a.depth = depth;
   a.k = k;
-  a.count = ws->counter.as<unsigned long long>();
-  int32_t L = 0;
-  // BC keeps every level's masks for the backward pass; BFS keeps those of
-  // its first kKeepLevels levels (their depths are written in one pass) and
-  // then alternates two arrays, writing depths level by level
-  auto slot = [&](int32_t lvl) {
-    if (with_sigma || lvl < kKeepLevels) return (size_t)lvl;
-    return (size_t)(kKeepLevels + ((lvl - kKeepLevels) & 1));
-  };
-  bool depth_pass_done = false;
-  // level 0 (the sources) pushes; later levels choose by frontier edges
-  bool push = true;
-  unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
-  if (!ws->fq.p) {
-    GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "batch push frontier"));
-    GR_TRY(ws->fs.alloc(sizeof(int32_t) * ((size_t)g->n + 2), "batch push frontier scan"));
-  }
-  auto depth_pass = [&](int32_t levels) -> gr_status {
-    std::vector<unsigned long long *> ptrs(kKeepLevels, nullptr);
-    for (int32_t i = 0; i < levels; ++i) ptrs[i] = ws->lm[i]->as<unsigned long long>();
-    GR_CUDA(cudaMemcpyAsync(ws->lmp.p, ptrs.data(), sizeof(unsigned long long *) * kKeepLevels,
-                            cudaMemcpyHostToDevice, s));
-    k_mb_depth<<<grid, 256, 0, s>>>((const unsigned long long *const *)ws->lmp.p, levels, g->n,
-                                    k, depth);
-    GR_CUDA(cudaGetLastError());
-    depth_pass_done = true;
-    return GR_OK;
-  };
+  a.symmetric = g->symmetric ? 1 : 0;
+  a.max_levels = max_levels;
+  a.ctl = ws->ctl.as<MbCtl>();
+  return a;
+}
+
+static gr_status mb_launch(gr_graph *g, const MbArgs &a, int sk, cudaStream_t s) {
+  void *kern = sk == kSigU64   ? (void *)k_mb_do<kSigU64>
+               : sk == kSigF64 ? (void *)k_mb_do<kSigF64>
+                               : (void *)k_mb_do<kSigNone>;
+  const int want = sk == kSigNone ? mb_do_blocks_per_sm<kSigNone>() : mb_do_blocks_per_sm<kSigU64>();
+  int per_sm = 0;
+  GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMbThreads, 0));
+  const int blocks = std::max(1, std::min(per_sm, want)) * g->num_sms;
+  MbArgs arg = a;
+  void *args[] = {&arg};
+  GR_CUDA(cudaLaunchCooperativeKernel(kern, blocks, kMbThreads, args, 0, s));
+  return GR_OK;
+}
+
+// Forward levels of one batch of k <= 64 sources (device-driven), counting
+// paths as `sk` says. A batched BFS (depth != null) has every array it can
+// need before it starts and never synchronises; BC (levels_out != null)
+// keeps every level's array, so the kernel may stop for more and is
+// resumed, and the call synchronises to report the level count and
+// whether a uint64 path count overflowed.
+static gr_status run_forward(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
+                             int32_t *depth, int sk, cudaStream_t s, int32_t max_levels,
+                             int32_t *levels_out = nullptr, bool *overflowed = nullptr) {
+  const bool with_sigma = sk != kSigNone;
+  const int32_t keep = with_sigma ? INT32_MAX : bfs_keep_levels(g);
+  GR_TRY(ensure_slots(g, ws, with_sigma ? std::max<int32_t>(16, (int32_t)ws->lm.size())
+                                        : keep + 3, s));
+  MbArgs a = mb_args(g, ws, k, depth, keep, max_levels, with_sigma);
+  const int grid = g->num_sms * 8;
+  k_mb_init<<<grid, 256, 0, s>>>(a, with_sigma ? ws->sigma.as<unsigned long long>() : nullptr,
+                                 with_sigma ? ws->q.as<double>() : nullptr);
+  MbSources src;  // by value: no host-to-device copy
+  for (int32_t i = 0; i < 64; ++i) src.s[i] = i < k ? h_srcs[i] : 0;
+  k_mb_sources<<<1, 64, 0, s>>>(a, src, sk);
+  GR_CUDA(cudaGetLastError());
+  GR_TRY(mb_launch(g, a, sk, s));
+  if (!levels_out) return GR_OK;
   for (;;) {
-    if (depth && L == kKeepLevels) GR_TRY(depth_pass(kKeepLevels));
-    unsigned long long *nxt;
-    GR_TRY(level_mask(g, ws, slot(L + 1), s, &nxt));
-    a.cur = ws->lm[slot(L)]->as<unsigned long long>();
-    a.nxt = nxt;
-    a.level = L;
-    a.depth = (depth && L >= kKeepLevels) ? depth : nullptr;
-    GR_CUDA(cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), s));
-    if (push) {
-      int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
-      GR_CUDA(cudaMemsetAsync(fpacked, 0, sizeof(unsigned long long), s));
-      k_mb_compact<<<grid, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
-      k_mb_close<<<1, 1, 0, s>>>(fpacked, fs);
-      if (sk == kSigU64)
-        k_mb_push<kSigU64><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
-      else if (sk == kSigF64)
-        k_mb_push<kSigF64><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
-      else
-        k_mb_push<kSigNone><<<g->num_sms * 8, kMbThreads, 0, s>>>(a, fq, fs, fpacked);
-    } else if (sk == kSigU64) {
-      k_mb_forward<kSigU64><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
-    } else if (sk == kSigF64) {
-      k_mb_forward<kSigF64><<<g->num_sms * 4, kMbThreads, 0, s>>>(a);
-    } else {
-      k_mb_pull<<<g->num_sms * kMbPullBlocksPerSm, kMbThreads, 0, s>>>(a);
-    }
-    GR_CUDA(cudaGetLastError());
-    unsigned long long cnt = 0;
-    GR_CUDA(cudaMemcpyAsync(&cnt, a.count, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    MbCtl h;
+    GR_CUDA(cudaMemcpyAsync(&h, ws->ctl.p, sizeof(MbCtl), cudaMemcpyDeviceToHost, s));
     GR_CUDA(cudaStreamSynchronize(s));
-    ++L;
-    const uint32_t joined_vertices = (uint32_t)(cnt & 0xFFFFFFFFull);
-    const long long joined_edges = (long long)(cnt >> 32);
-    if (joined_vertices == 0) break;  // level L is empty; levels 0..L-1 hold vertices
-    if (L >= max_levels) return fail(GR_ETIMEOUT, "level limit reached");
-    // a pull reads v's row as v's predecessors: only a symmetric CSR has them
-    // there, so a directed graph pushes on every level
-    push = !g->symmetric || joined_edges * kPushDiv < g->m;
-  }
-  if (depth && !depth_pass_done) GR_TRY(depth_pass(L));
-  *levels_out = L;
-  if (overflowed) {
-    *overflowed = false;
-    if (sk == kSigU64) {
-      int32_t h = 0;
-      GR_CUDA(cudaMemcpyAsync(&h, sig_overflow, sizeof(h), cudaMemcpyDeviceToHost, s));
-      GR_CUDA(cudaStreamSynchronize(s));
-      *overflowed = h != 0;
+    if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
+    if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "level limit reached");
+    if (h.done) {
+      *levels_out = h.levels;
+      if (overflowed) *overflowed = h.sig_overflow != 0;
+      return GR_OK;
     }
+    if (!h.paused) return fail(GR_ECUDA, "batched forward stopped without a reason");
+    // the next levels need more arrays: double them and resume
+    GR_TRY(ensure_slots(g, ws, 2 * (int32_t)ws->lm.size(), s));
+    a = mb_args(g, ws, k, depth, keep, max_levels, with_sigma);
+    k_mb_resume<<<1, 1, 0, s>>>(a.ctl);
+    GR_CUDA(cudaGetLastError());
+    GR_TRY(mb_launch(g, a, sk, s));
   }
+}
+
+gr_status batch_read_ctl_error(BatchWorkspace *ws, cudaStream_t s) {
+  MbCtl h;
+  // pageable destination: the copy has finished when the call returns
+  GR_CUDA(cudaMemcpyAsync(&h, ws->ctl.p, sizeof(MbCtl), cudaMemcpyDeviceToHost, s));
+  if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
+  if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "level limit reached");
+  if (!h.done) return fail(GR_ECUDA, "batched BFS did not finish");
   return GR_OK;
 }
 
 // Batched BFS into a device depth array [k][n] with an explicit workspace.
 gr_status bfs_batch_run(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
                         int32_t *depth, int32_t max_levels, cudaStream_t s) {
-  int32_t levels = 0;  // every depth entry is written by run_forward
-  return run_forward(g, ws, h_srcs, k, depth, kSigNone, s, max_levels, &levels);
+  return run_forward(g, ws, h_srcs, k, depth, kSigNone, s, max_levels);
 }
 
 }  // namespace gr
@@ -919,6 +1151,21 @@ gr_status gr_bfs_batch(gr_graph *g, const int32_t *srcs, int32_t k, int32_t *dep
   GR_TRY(bfs_batch_run(g, g->batch, srcs, k, (int32_t *)d_depth, max_levels, s));
   if (cp) GR_CUDA(cudaMemcpyAsync(depth, d_depth, bytes, cudaMemcpyDeviceToHost, s));
   GR_TRY(end_call(g, s));
+  return GR_OK;
+}
+
+gr_status gr_bfs_batch_stats(gr_graph *g, int32_t *levels) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (!g->batch) return fail(GR_EINVAL, "no batched traversal has run on this graph");
+  std::lock_guard<std::mutex> lock(g->mu);
+  GR_CUDA(cudaSetDevice(g->device));
+  if (g->has_last) GR_CUDA(cudaEventSynchronize(g->last_done));
+  MbCtl h;
+  GR_CUDA(cudaMemcpy(&h, g->batch->ctl.p, sizeof(MbCtl), cudaMemcpyDeviceToHost));
+  if (h.error == kDevTimeout) return fail(GR_ETIMEOUT, "a device-side wait timed out");
+  if (h.error == kDevOverflow) return fail(GR_ETIMEOUT, "level limit reached");
+  if (levels) *levels = h.levels;
   return GR_OK;
 }
 

@@ -105,6 +105,9 @@ struct gr_graph {
   int32_t tuned_blocks_per_sm = 0;  // persistent BFS grid (0: all resident)
   int32_t tuned_sssp_mode = GR_MODE_GRAPH;
   int32_t tuned_sssp_blocks_per_sm = 0;
+  // SSSP relaxations pull once the near frontier has m / alpha edges (0:
+  // never; set by gr_autotune)
+  float tuned_sssp_alpha = 0.f;
   double tuned_bfs_ms = 0.0, tuned_sssp_ms = 0.0;  // measured by gr_autotune
   double mean_weight = 0.0;
 
@@ -180,6 +183,8 @@ gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out);
 size_t batch_ws_bytes(const gr_graph *g);
 gr_status bfs_batch_run(gr_graph *g, BatchWorkspace *ws, const int32_t *h_srcs, int32_t k,
                         int32_t *depth, int32_t max_levels, cudaStream_t s);
+// GR_ETIMEOUT when the last batched BFS on ws stopped at a device-side limit
+gr_status batch_read_ctl_error(BatchWorkspace *ws, cudaStream_t s);
 
 // Degree-statistics prior of the tuned settings (set at graph creation).
 void tune_prior(gr_graph *g);

@@ -191,7 +191,8 @@ struct SlotDev {
   // cap, a timed-out wait) fails its request
   gr_status check_device_errors() {
     const int32_t kind = rs[0].kind;
-    if (kind == GR_QUERY_BFS && !many()) return bfs_read_ctl_error(st.bfs, s);
+    if (kind == GR_QUERY_BFS) return many() ? batch_read_ctl_error(st.batch, s)
+                                            : bfs_read_ctl_error(st.bfs, s);
     if (kind == GR_QUERY_SSSP) return sssp_read_ctl_error(many() ? st.sssp_batch : st.sssp, s);
     return GR_OK;
   }

@@ -5,7 +5,7 @@
 // advance (UpdateLabel = atomicMin relaxation), filter (RemoveRedundant, an
 // output-queue stamp per vertex) and the priority-queue split until the
 // frontier is empty. Here one iteration of the device-side loop is ONE
-// kernel, k_sssp_iter, in one of two modes chosen on the device:
+// kernel, k_sssp_iter, in one of three modes chosen on the device:
 //
 //   relax  load-balanced advance over the near frontier (merge-path chunks
 //          over its vertex ends and edge ranks, Sec. 4.4); per edge
@@ -13,6 +13,13 @@
 //          the next near frontier if new < T (deduplicated by a
 //          per-iteration stamp, the RemoveRedundant filter) and the far pile
 //          otherwise (deduplicated by a per-phase stamp)
+//   pull   the relaxation in pull form (direction-optimising SSSP, which
+//          the paper names for future work in Sec. 4.5 and Sec. 7), for
+//          near frontiers holding most of the edges on a symmetric graph:
+//          every vertex takes the minimum of dist[u] + w(e) over its
+//          in-edges (= its row) and keeps it if lower, so no atomic is
+//          needed except for vertices whose row is split between threads;
+//          the improved vertices go to near / far exactly as in relax
 //   split  only when the near frontier is empty: the far pile is split by
 //          the raised threshold into near and far; entries whose distance
 //          fell below the old threshold were already expanded and are
@@ -38,19 +45,20 @@
 // threshold T and the device-side loop, so k high-diameter searches cost
 // about as many iterations as one.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 
 #include "advance.cuh"
 
 namespace gr {
 
-enum : int32_t { kSsspRelax = 0, kSsspSplit = 1 };
+enum : int32_t { kSsspRelax = 0, kSsspSplit = 1, kSsspPull = 2 };
 
 struct SsspCtl {
   uint32_t *dist;
   int32_t *pred;
   int32_t src;
-  int32_t mode;          // kSsspRelax / kSsspSplit for the current iteration
+  int32_t mode;          // kSsspRelax / kSsspSplit / kSsspPull for the current iteration
   int32_t near_parity;   // which near buffer holds the current frontier
   int32_t far_parity;    // which far buffer holds the current pile
   int32_t near_len;
@@ -74,6 +82,11 @@ struct SsspCtl {
   unsigned long long delta;
   long long near_edges;   // edges of the current near frontier
   long long relaxations;  // edges expanded (statistics)
+  // a relaxation whose near frontier has at least this many edges runs in
+  // pull form (LLONG_MAX: never; pull needs a symmetric CSR and one lane)
+  long long pull_min_edges;
+  int32_t pulls;          // relaxations run in pull form (statistics)
+  int32_t pad2_;
   // persistent kernel: counter rings and grid barrier
   unsigned long long ring_near[3];
   int32_t ring_far[3];
@@ -138,7 +151,8 @@ struct SsspSources {
 };
 
 __global__ void k_sssp_init(SsspArgs a, SsspSources src, uint32_t *dist, int32_t *pred,
-                            unsigned long long delta, int32_t max_iters) {
+                            unsigned long long delta, int32_t max_iters,
+                            long long pull_min_edges) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = tid; v < a.nv; v += stride) {
@@ -183,6 +197,8 @@ __global__ void k_sssp_init(SsspArgs a, SsspSources src, uint32_t *dist, int32_t
     c->T_old = 0;
     c->near_edges = edges;
     c->relaxations = 0;
+    c->pull_min_edges = pull_min_edges;
+    c->pulls = 0;
     for (int i = 0; i < 3; ++i) {
       c->ring_near[i] = 0ull;
       c->ring_far[i] = 0;
@@ -452,6 +468,153 @@ __device__ void relax_body_thread(const SsspArgs &a, uint32_t *dist, const SsspS
   if (lane == 0 && local_min != 0xFFFFFFFFu) atomicMin(st.fmin, local_min);
 }
 
+// Pull form of one relaxation: for every vertex v (one graph copy), the
+// smallest dist[u] + w(e) over the entries e = (v, u) of its row, which on a
+// symmetric CSR are its in-edges, replaces dist[v] if smaller. Merge-based
+// like the neighbourhood gather-reduce: a chunk's vertex end markers and its
+// edges form one sequence; the block gathers dist[C[e]] + W[e] of the
+// chunk's edges into shared memory (coalesced column and weight loads, the
+// distance gathers of the chunk in flight at once), then each thread walks
+// kSsspItems consecutive items, taking the minimum per vertex. A vertex
+// whose row lies inside one thread's items is lowered with a plain store
+// (nobody else writes it in this iteration); the pieces of a split row use
+// atomicMin. A lowered vertex joins the next near frontier (below T) or the
+// far pile, deduplicated by the same stamps as in relax.
+__device__ void pull_relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm,
+                                const SsspStep &st) {
+  constexpr int ITEMS = kSsspItems;
+  constexpr int CHUNK = kSsspChunk;
+  int32_t *Qn = pick(a.nearq, st.near_parity ^ 1);
+  int32_t *Sn = pick(a.nearS, st.near_parity ^ 1);
+  const unsigned long long T = st.T;
+  const int32_t iter = st.iter, epoch = st.far_epoch;
+  int32_t *s_end = sm.off;  // end marker of each chunk vertex, chunk-local
+  uint32_t *s_val = sm.du;  // dist[u] + w(e) of each chunk edge
+  uint32_t local_min = 0xFFFFFFFFu;
+  const long long total = (long long)a.n + a.m;
+  const long long nchunks = (total + CHUNK - 1) / CHUNK;
+  for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const long long d0 = chunk * CHUNK;
+    const long long d1 = min(d0 + CHUNK, total);
+    int32_t i0, i1;
+    block_chunk_bounds<kSsspThreads>(a.R, a.n, (int32_t)a.m, d0, d1, CHUNK, sm.sred, &i0, &i1);
+    const long long j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
+    const int32_t ne = (int32_t)(j1 - j0);
+    const int32_t len = (int32_t)(d1 - d0);
+    for (int32_t k = threadIdx.x; k < nv; k += kSsspThreads)
+      s_end[k] = (int32_t)((long long)a.R[i0 + k + 1] + i0 + k - d0);
+    {
+      int32_t col[ITEMS];
+      uint32_t wt[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = threadIdx.x + i * kSsspThreads;
+        col[i] = -1;
+        wt[i] = 0u;
+        if (k < ne && GR_IN(j0 + k, a.m, 330)) {
+          col[i] = a.C[j0 + k];
+          wt[i] = a.W[j0 + k];
+          if (!GR_IN(col[i], a.n, 331)) col[i] = -1;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = threadIdx.x + i * kSsspThreads;
+        if (k < ne) {
+          uint32_t val = 0xFFFFFFFFu;
+          if (col[i] >= 0) {
+            const unsigned long long t = (unsigned long long)dist[col[i]] + wt[i];
+            if (t < 0xFFFFFFFFull) val = (uint32_t)t;
+          }
+          s_val[k] = val;
+        }
+      }
+    }
+    __syncthreads();
+    // this thread's items [k0, k1) of the chunk: item i closes at most one
+    // vertex (slot i), and slot ITEMS holds the vertex continuing past k1
+    int32_t cv[ITEMS + 1];
+    uint32_t cd[ITEMS + 1];
+    bool cw[ITEMS + 1];  // whole: the vertex's row lies in this thread's items
+#pragma unroll
+    for (int j = 0; j <= ITEMS; ++j) {
+      cv[j] = -1;
+      cd[j] = 0xFFFFFFFFu;
+      cw[j] = false;
+    }
+    const int32_t k0 = min(len, (int32_t)threadIdx.x * ITEMS);
+    const int32_t k1 = min(len, k0 + ITEMS);
+    if (k0 < k1) {
+      int32_t lo = 0, hi = nv;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (s_end[mid] < k0) lo = mid + 1;
+        else hi = mid;
+      }
+      int32_t r = lo, e = k0 - r;
+      uint32_t best = 0xFFFFFFFFu;
+      bool first = true;  // the current vertex may have entries before k0
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int32_t k = k0 + i;
+        if (k < k1) {
+          if (r < nv && s_end[r] == k) {  // end marker of vertex i0 + r
+            cv[i] = i0 + r;
+            cd[i] = best;
+            cw[i] = !first;
+            best = 0xFFFFFFFFu;
+            first = false;
+            ++r;
+          } else {
+            best = min(best, s_val[e]);
+            ++e;
+          }
+        }
+      }
+      if (r < nv && best != 0xFFFFFFFFu) {  // continues past k1
+        cv[ITEMS] = i0 + r;
+        cd[ITEMS] = best;
+        cw[ITEMS] = false;
+      }
+    }
+    // lower, classify and emit (warp-uniform emission calls)
+#pragma unroll
+    for (int j = 0; j <= ITEMS; ++j) {
+      int code = 0;
+      int32_t dvg = 0;
+      const int32_t v = cv[j];
+      const uint32_t nd = cd[j];
+      if (v >= 0 && nd != 0xFFFFFFFFu) {
+        bool lowered;
+        if (cw[j]) {
+          lowered = nd < dist[v];
+          if (lowered) dist[v] = nd;
+        } else {
+          lowered = nd < atomicMin(dist + v, nd);
+        }
+        if (lowered) {
+          if ((unsigned long long)nd < T) {
+            if (atomicExch(a.stamp + v, iter) != iter) {
+              code = 1;
+              dvg = a.R[v + 1] - a.R[v];
+            }
+          } else {
+            local_min = min(local_min, nd);
+            code = atomicExch(a.far_stamp + v, epoch) != epoch ? 2 : 0;
+          }
+        }
+      }
+      emit_scanned(sm.nearb, code == 1, v, dvg);
+      emit_plain(sm.farb, code == 2, v);
+    }
+    flush_scanned<kSsspThreads>(sm.nearb, st.near_ctr, Qn, Sn, a.nv + 1);
+    flush_plain<kSsspThreads>(sm.farb, st.far_ctr, st.far_dest, st.far_cap);
+  }
+  for (int o = 16; o > 0; o >>= 1) local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+  if ((threadIdx.x & 31) == 0 && local_min != 0xFFFFFFFFu) atomicMin(st.fmin, local_min);
+}
+
 __device__ void split_body(const SsspArgs &a, const uint32_t *dist, SsspSmem &sm,
                            const SsspStep &st) {
   const int32_t *F = pick(a.farq, st.far_parity);
@@ -512,7 +675,8 @@ __device__ void relax_mode(const SsspArgs &a, SsspCtl *c, SsspSmem &sm) {
   st.far_dest = pick(a.farq, c->far_parity);
   st.far_cap = (long long)a.nv + 1;
   st.fmin = &c->far_min;
-  if (LOW) relax_body_thread(a, c->dist, st);
+  if (!LOW && c->mode == kSsspPull) pull_relax_body(a, c->dist, sm, st);
+  else if (LOW) relax_body_thread(a, c->dist, st);
   else relax_body(a, c->dist, sm, st);
 }
 
@@ -549,8 +713,9 @@ __device__ void sssp_end(const SsspArgs &a, SsspCtl *c) {
   const unsigned long long packed = *(volatile unsigned long long *)&c->near_next_packed;
   const int32_t qn = (int32_t)(packed & 0xFFFFFFFFull);
   const long long en = (long long)(packed >> 32);
-  if (c->mode == kSsspRelax) {
-    c->relaxations += c->near_edges;
+  if (c->mode != kSsspSplit) {
+    c->relaxations += c->mode == kSsspPull ? a.m : c->near_edges;
+    c->pulls += c->mode == kSsspPull;
     c->far_len = *(volatile int32_t *)&c->far_len;
     c->far_min = *(volatile uint32_t *)&c->far_min;
   } else {
@@ -569,7 +734,7 @@ __device__ void sssp_end(const SsspArgs &a, SsspCtl *c) {
   c->far_min_next = 0xFFFFFFFFu;
   c->iter += 1;
   if (c->near_len > 0) {
-    c->mode = kSsspRelax;
+    c->mode = c->near_edges >= c->pull_min_edges ? kSsspPull : kSsspRelax;
   } else if (c->far_len > 0) {
     c->mode = kSsspSplit;
     c->T_old = c->T;
@@ -604,7 +769,7 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm)
     sm.farb.cnt = 0;
   }
   __syncthreads();
-  if (c->mode == kSsspRelax) relax_mode<LOW>(a, c, sm);
+  if (c->mode != kSsspSplit) relax_mode<LOW>(a, c, sm);
   else split_mode(a, c, sm);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -639,7 +804,8 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
   const int32_t max_iters = c->max_iters;
   int32_t mode = kSsspRelax, near_parity = 0, far_parity = 0, near_len = c->near_len, far_len = 0;
   long long near_edges = c->near_edges, relaxations = 0;
-  int32_t iter = 0, far_epoch = 0, phases = 0, gen = 0;
+  const long long pull_min_edges = c->pull_min_edges;
+  int32_t iter = 0, far_epoch = 0, phases = 0, gen = 0, pulls = 0;
   uint32_t far_min = 0xFFFFFFFFu;
   unsigned long long T = delta, T_old = 0;
   for (;;) {
@@ -662,10 +828,11 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
     st.near_ctr = &c->ring_near[slot];
     st.far_ctr = &c->ring_far[slot];
     st.fmin = &c->ring_fmin[slot];
-    if (mode == kSsspRelax) {
+    if (mode != kSsspSplit) {
       st.far_dest = pick(a.farq, far_parity) + far_len;  // appended after the pile
       st.far_cap = (long long)a.nv + 1 - far_len;
-      if (LOW) relax_body_thread(a, dist, st);
+      if (!LOW && mode == kSsspPull) pull_relax_body(a, dist, sm, st);
+      else if (LOW) relax_body_thread(a, dist, st);
       else relax_body(a, dist, sm, st);
     } else {
       st.far_dest = pick(a.farq, far_parity ^ 1);
@@ -676,8 +843,9 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
     const unsigned long long pk = *(volatile unsigned long long *)&c->ring_near[slot];
     const int32_t fcnt = *(volatile int32_t *)&c->ring_far[slot];
     const uint32_t fmin = *(volatile uint32_t *)&c->ring_fmin[slot];
-    if (mode == kSsspRelax) {
-      relaxations += near_edges;
+    if (mode != kSsspSplit) {
+      relaxations += mode == kSsspPull ? a.m : near_edges;
+      pulls += mode == kSsspPull;
       far_len += fcnt;
       far_min = min(far_min, fmin);
     } else {
@@ -693,7 +861,7 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
     iter += 1;
     bool done = false, overflow = false;
     if (near_len > 0) {
-      mode = kSsspRelax;
+      mode = near_edges >= pull_min_edges ? kSsspPull : kSsspRelax;
     } else if (far_len > 0) {
       mode = kSsspSplit;
       T_old = T;
@@ -709,6 +877,7 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
         c->iter = iter;
         c->phases = phases;
         c->relaxations = relaxations;
+        c->pulls = pulls;
         if (overflow) c->error = kDevOverflow;
         c->done = 1;
       }
@@ -805,6 +974,23 @@ static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws, int32_t lanes = 1) {
   return a;
 }
 
+// Smallest near-frontier edge count at which a relaxation pulls. Pull reads
+// every row once where push reads the frontier's rows (and pays atomics and
+// its per-chunk chain), so it pays only where the frontier covers most of
+// the graph: at m / opts->alpha edges, else at m / the graph's tuned alpha
+// (0: never, the default until gr_autotune finds pulling faster); GR_DIR_PUSH
+// never pulls, GR_DIR_PULL pulls every relaxation. Only a symmetric CSR
+// (rows = in-neighbours) and a single search can pull.
+static long long sssp_pull_min_edges(const gr_graph *g, const gr_opts &o, int32_t lanes) {
+  if (!g->symmetric || lanes != 1 || g->max_degree <= kSsspLowDegreeMax || g->m == 0 ||
+      o.direction == GR_DIR_PUSH)
+    return LLONG_MAX;
+  if (o.direction == GR_DIR_PULL) return 1;
+  const double div = o.alpha > 0.f ? (double)o.alpha : (double)g->tuned_sssp_alpha;
+  if (div <= 0.0) return LLONG_MAX;
+  return std::max<long long>(1, (long long)((double)g->m / div));
+}
+
 static gr_status sssp_enqueue_iter(gr_graph *g, const SsspArgs &a, cudaStream_t s,
                                    cudaGraphConditionalHandle h, int use_cond) {
   if (a.low_degree)
@@ -858,6 +1044,11 @@ gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o) {
   if (src < 0 || src >= g->n) return fail(GR_EINVAL, "source out of range");
   if (o.mode < GR_MODE_AUTO || o.mode > GR_MODE_PERSISTENT)
     return fail(GR_EINVAL, "unknown mode");
+  if (o.direction < GR_DIR_AUTO || o.direction > GR_DIR_PULL)
+    return fail(GR_EINVAL, "unknown direction policy");
+  if (o.direction == GR_DIR_PULL && !g->symmetric)
+    return fail(GR_EINVAL, "pull relaxation needs a symmetric CSR (in-neighbours = out-neighbours)");
+  if (o.alpha < 0.f) return fail(GR_EINVAL, "alpha must be >= 0");
   return GR_OK;
 }
 
@@ -911,7 +1102,8 @@ gr_status sssp_run(gr_graph *g, SsspWorkspace *ws, int32_t src, uint32_t *dist, 
   SsspSources one;
   one.k = 1;
   one.s[0] = src;
-  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, one, dist, pred, delta, max_iters);
+  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, one, dist, pred, delta, max_iters,
+                                             sssp_pull_min_edges(g, o, 1));
   GR_CUDA(cudaGetLastError());
   const int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
   GR_TRY(sssp_drive(g, ws, a, mode, o, max_iters, s));
@@ -937,7 +1129,8 @@ gr_status sssp_batch_run(gr_graph *g, SsspWorkspace *ws, const int32_t *h_srcs, 
   SsspSources srcs;
   srcs.k = k;
   for (int32_t l = 0; l < kSsspMaxLanes; ++l) srcs.s[l] = l < k ? h_srcs[l] : 0;
-  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, srcs, dist, nullptr, delta, max_iters);
+  k_sssp_init<<<g->num_sms * 8, 256, 0, s>>>(a, srcs, dist, nullptr, delta, max_iters,
+                                             LLONG_MAX);
   GR_CUDA(cudaGetLastError());
   int32_t mode = o.mode != GR_MODE_AUTO ? o.mode : g->tuned_sssp_mode;
   if (mode != GR_MODE_PERSISTENT) mode = GR_MODE_LAUNCH;
@@ -1028,6 +1221,19 @@ gr_status gr_sssp_batch_stats(gr_graph *g, int32_t *iterations, int32_t *phases,
   if (iterations) *iterations = h.iter;
   if (phases) *phases = h.phases;
   if (relaxations) *relaxations = h.relaxations;
+  return GR_OK;
+}
+
+gr_status gr_sssp_pull_stats(gr_graph *g, int32_t *pulls) {
+  clear_error();
+  if (!g) return fail(GR_EINVAL, "graph must not be NULL");
+  if (!g->sssp) return fail(GR_EINVAL, "no SSSP has run on this graph");
+  std::lock_guard<std::mutex> lock(g->mu);
+  GR_CUDA(cudaSetDevice(g->device));
+  if (g->has_last) GR_CUDA(cudaEventSynchronize(g->last_done));
+  SsspCtl h;
+  GR_CUDA(cudaMemcpy(&h, g->sssp->ctl.p, sizeof(h), cudaMemcpyDeviceToHost));
+  if (pulls) *pulls = h.pulls;
   return GR_OK;
 }
 

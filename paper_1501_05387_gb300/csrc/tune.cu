@@ -141,6 +141,7 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
     struct SCand {
       int32_t mode, bps;
       uint32_t delta;
+      float alpha;  // relaxations pull at m / alpha frontier edges (0: never)
     };
     std::vector<SCand> cands;
     const double mw = std::max(1.0, g->mean_weight);
@@ -148,11 +149,19 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
     for (double f : {0.5, 1.0, 2.0, 4.0, 8.0, 32.0, 64.0})
       deltas.push_back((uint32_t)std::max(1.0, std::min(4.0e9, f * mw)));
     deltas.push_back(UINT32_MAX);
-    for (uint32_t d : deltas) {
-      cands.push_back({GR_MODE_GRAPH, 0, d});
-      cands.push_back({GR_MODE_PERSISTENT, 1, d});
-      cands.push_back({GR_MODE_PERSISTENT, 0, d});
+    // pull thresholds to try where the graph can pull (symmetric, not
+    // mesh-like): the frontier holding 80 % or half of the edges
+    std::vector<float> alphas = {0.f};
+    if (g->symmetric && g->max_degree > 16) {
+      alphas.push_back(1.25f);
+      alphas.push_back(2.f);
     }
+    for (uint32_t d : deltas)
+      for (float al : alphas) {
+        cands.push_back({GR_MODE_GRAPH, 0, d, al});
+        cands.push_back({GR_MODE_PERSISTENT, 1, d, al});
+        cands.push_back({GR_MODE_PERSISTENT, 0, d, al});
+      }
     float best = FLT_MAX;
     SCand pick = cands[0];
     const int32_t saved_sbps = g->tuned_sssp_blocks_per_sm;
@@ -160,6 +169,8 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
       gr_opts o = default_opts();
       o.delta = c.delta;
       o.mode = c.mode;
+      if (c.alpha > 0.f) o.alpha = c.alpha;
+      else o.direction = GR_DIR_PUSH;
       // the candidate's grid size goes through the graph's tuned value, as
       // it will be used afterwards (o.block = 0 would mean "tuned", and 0
       // here means "all resident blocks")
@@ -184,6 +195,7 @@ gr_status gr_autotune(gr_graph *g, const int32_t *srcs, int32_t k, int32_t what,
     }
     // UINT32_MAX selects "one bucket"; it is stored as is
     g->sssp_delta = pick.delta;
+    g->tuned_sssp_alpha = pick.alpha;
     g->tuned_sssp_mode = pick.mode;
     g->tuned_sssp_blocks_per_sm = pick.mode == GR_MODE_PERSISTENT ? pick.bps : saved_sbps;
     g->tuned_sssp_ms = best / k;

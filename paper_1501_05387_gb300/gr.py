@@ -70,8 +70,10 @@ _sig("gr_bfs_multi", [_vp, _i32, _vp, _vp, _vp, _P(gr_opts), _vp])
 _sig("gr_bfs_stats", [_vp, _P(_i32), _P(_i32)])
 _sig("gr_bfs_trace", [_vp, _i32, _vp, _vp, _vp, _vp, _P(_i32)])
 _sig("gr_sssp", [_vp, _i32, _vp, _vp, _P(gr_opts), _vp])
+_sig("gr_sssp_pull_stats", [_vp, _P(_i32)])
 _sig("gr_sssp_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("gr_bfs_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
+_sig("gr_bfs_batch_stats", [_vp, _P(_i32)])
 _sig("gr_sssp_batch", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
 _sig("gr_sssp_batch_stats", [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("gr_bc", [_vp, _vp, _i32, _vp, _P(gr_opts), _vp])
@@ -265,6 +267,13 @@ def gr_sssp_stats(g: Graph):
     return it.value, ph.value, rl.value
 
 
+def gr_sssp_pull_stats(g: Graph) -> int:
+    """Relaxations of the last gr_sssp on g that ran in pull form."""
+    p = _i32()
+    _check(_lib.gr_sssp_pull_stats(g.handle, ctypes.byref(p)), "gr_sssp_pull_stats")
+    return p.value
+
+
 def gr_sssp_batch(g: Graph, srcs, dist, opts=None, stream=None):
     """k SSSP searches (k = len(srcs), up to 64) in one run into dist[k*n]
     (uint32, source-major; torch.int32 tensors hold the same bits)."""
@@ -288,6 +297,14 @@ def gr_bfs_batch(g: Graph, srcs, depth, opts=None, stream=None):
     srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
     _check(_lib.gr_bfs_batch(g.handle, srcs.ctypes.data, int(srcs.size), _ptr(depth, np.int32),
                              _opts(opts), _stream(stream)), "gr_bfs_batch")
+
+
+def gr_bfs_batch_stats(g: Graph) -> int:
+    """Levels of the last batched BFS on g (synchronises; GrError with
+    GR_ETIMEOUT if it stopped at a device-side limit)."""
+    lv = _i32()
+    _check(_lib.gr_bfs_batch_stats(g.handle, ctypes.byref(lv)), "gr_bfs_batch_stats")
+    return lv.value
 
 
 def gr_bc(g: Graph, srcs, bc, opts=None, stream=None):

@@ -76,6 +76,28 @@ def test_batch_bfs_long_paths(cuda_lib, n):
             assert np.array_equal(d[i], np.abs(np.arange(n) - s).astype(np.int32))
 
 
+@pytest.mark.parametrize("tail", [10, 15, 16, 17, 40])
+def test_batch_bfs_kept_level_boundary(cuda_lib, tail):
+    """A hub with 20 leaves (so the graph is not mesh-like and a batch keeps
+    the lane masks of its first levels) and a path hanging off it: depths of
+    the kept levels come from the end-of-run pass, deeper ones are written as
+    they are reached; sources on the path, the hub and a leaf."""
+    edges = [(0, i) for i in range(1, 21)]
+    prev = 0
+    for i in range(tail):
+        edges.append((prev, 21 + i))
+        prev = 21 + i
+    n = 21 + tail
+    r, c = gg.from_edges(n, edges)
+    srcs = [0, 5, n - 1, 21 + tail // 2, n - 1]
+    with cuda_lib.gr_graph_create(r, c) as g:
+        d = run_batch(cuda_lib, g, srcs)
+        levels = cuda_lib.gr_bfs_batch_stats(g)
+        for i, s in enumerate(srcs):
+            assert np.array_equal(d[i], oracle.bfs(r, c, s)[0])
+    assert levels == max(int(oracle.bfs(r, c, s)[0].max()) for s in srcs) + 1
+
+
 def test_batch_bfs_bad_args(cuda_lib):
     import torch
     r, c = gg.from_edges(5, [(0, 1)])

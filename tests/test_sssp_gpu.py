@@ -32,10 +32,11 @@ def check(gr, r, c, w, g, src, o=None):
     assert np.array_equal(p, ref_p)
 
 
-def opts(gr, delta=0, mode="auto"):
+def opts(gr, delta=0, mode="auto", direction="auto", alpha=0.0):
     m = {"auto": gr.GR_MODE_AUTO, "launch": gr.GR_MODE_LAUNCH, "graph": gr.GR_MODE_GRAPH,
          "persistent": gr.GR_MODE_PERSISTENT}[mode]
-    return gr.gr_opts(delta=delta, mode=m)
+    d = {"auto": gr.GR_DIR_AUTO, "push": gr.GR_DIR_PUSH, "pull": gr.GR_DIR_PULL}[direction]
+    return gr.gr_opts(delta=delta, mode=m, direction=d, alpha=alpha)
 
 
 @pytest.fixture(scope="module")
@@ -53,6 +54,52 @@ def test_rmat_s14_delta_invariance(cuda_lib, s14w, delta, mode):
     r, c, w, g = s14w
     for src in [gg.max_degree_vertex(r)] + list(gg.sources(r, 3, seed=7)):
         check(cuda_lib, r, c, w, g, int(src), opts(cuda_lib, delta, mode))
+
+
+@pytest.mark.parametrize("delta", [0, 8, 0xFFFFFFFF])
+@pytest.mark.parametrize("mode", ["graph", "launch", "persistent"])
+@pytest.mark.parametrize("direction,alpha", [("pull", 0.0), ("auto", 2.0), ("auto", 1.25),
+                                             ("push", 0.0)])
+def test_rmat_s14_pull_relaxation(cuda_lib, s14w, delta, mode, direction, alpha):
+    """Direction-optimising SSSP: relaxations in pull form (every one, or
+    those whose near frontier holds m / alpha edges) give Dijkstra's
+    distances and the canonical predecessors, like push."""
+    r, c, w, g = s14w
+    o = opts(cuda_lib, delta, mode, direction, alpha)
+    pulls = []
+    for src in [gg.max_degree_vertex(r)] + list(gg.sources(r, 2, seed=9)):
+        check(cuda_lib, r, c, w, g, int(src), o)
+        pulls.append(cuda_lib.gr_sssp_pull_stats(g))
+    if direction == "pull":
+        assert min(pulls) > 0
+    if direction == "push":
+        assert max(pulls) == 0
+
+
+def test_pull_relaxation_edge_cases(cuda_lib):
+    """Forced pull on graphs with isolated vertices, zero weights, a
+    disconnected part and a hub whose row spans several chunks; a directed
+    CSR rejects forced pull."""
+    gr = cuda_lib
+    rng = np.random.default_rng(3)
+    hub = [(0, v) for v in range(1, 3000)]
+    extra = [(int(a), int(b)) for a, b in rng.integers(1, 3000, size=(4000, 2)) if a != b]
+    far = [(3100 + i, 3101 + i) for i in range(50)]  # a separate path
+    r, c = gg.from_edges(3200, hub + extra + far)
+    for wmin, wmax in [(0, 3), (1, 64)]:
+        w = gg.weights(r, c, seed=5, wmin=wmin, wmax=wmax)
+        with gr.gr_graph_create(r, c, w) as g:
+            for src in [0, 17, 3100, 3150, 3199]:
+                check(gr, r, c, w, g, src, opts(gr, 0, "persistent", "pull"))
+                check(gr, r, c, w, g, src, opts(gr, 0xFFFFFFFF, "graph", "pull"))
+    rd = np.array([0, 1, 2, 2], np.int32)
+    cd = np.array([1, 2], np.int32)
+    with gr.gr_graph_create(rd, cd, np.ones(2, np.uint32)) as g:
+        import torch
+        d = torch.empty(3, dtype=torch.int32, device="cuda")
+        with pytest.raises(gr.GrError) as ei:
+            gr.gr_sssp(g, 0, d, None, opts(gr, 0, "auto", "pull"))
+        assert ei.value.status == gr.GR_EINVAL
 
 
 def test_unit_weights_equal_bfs_depth_on_grid(cuda_lib):
