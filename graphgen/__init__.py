@@ -54,6 +54,9 @@ def _load():
             lib.gg_rmat_build.restype = ctypes.c_void_p
             lib.gg_rmat_build.argtypes = [i32, i32, dbl, dbl, dbl, u64, i32,
                                           P(i32), P(i64), P(i64)]
+            lib.gg_rmat_bipartite_build.restype = ctypes.c_void_p
+            lib.gg_rmat_bipartite_build.argtypes = [i32, i32, i32, dbl, dbl, dbl, u64,
+                                                    P(i32), P(i32), P(i64)]
             lib.gg_grid_build.restype = ctypes.c_void_p
             lib.gg_grid_build.argtypes = [i32, dbl, u64, P(i32), P(i64), P(i64)]
             lib.gg_csr_copy.restype = None
@@ -106,6 +109,25 @@ def rmat(scale: int, edge_factor: int = 16, seed: int = 1, abc=RMAT_ABC,
     if not h:
         raise ValueError("R-MAT build failed (bad scale or m > INT32_MAX)")
     return _take(h, n.value, m.value)
+
+
+def rmat_bipartite(scale_left: int, scale_right: int, edge_factor: int = 16, seed: int = 1,
+                   abc=RMAT_ABC):
+    """Bipartite R-MAT: 2**scale_left hubs (ids [0, n_left)) and
+    2**scale_right authorities (ids [n_left, n)), edge_factor * max(sides)
+    raw edges, each joining a hub and an authority, stored in both
+    directions (sorted, deduplicated). Returns (row_off, col, n_left)."""
+    lib = _load()
+    n = ctypes.c_int32()
+    nl = ctypes.c_int32()
+    m = ctypes.c_int64()
+    a, b, c = abc
+    h = lib.gg_rmat_bipartite_build(scale_left, scale_right, edge_factor, a, b, c, seed,
+                                    ctypes.byref(n), ctypes.byref(nl), ctypes.byref(m))
+    if not h:
+        raise ValueError("bipartite R-MAT build failed (bad scales or m > INT32_MAX)")
+    r, col = _take(h, n.value, m.value)
+    return r, col, nl.value
 
 
 def grid(side: int, p_del: float = 0.05, seed: int = 4):

@@ -53,6 +53,7 @@ constexpr uint64_t kStreamPerm = 0x200;
 constexpr uint64_t kStreamGridDel = 0x300;
 constexpr uint64_t kStreamWeight = 0x400;
 constexpr uint64_t kStreamSource = 0x500;
+constexpr uint64_t kStreamBipartite = 0x600;  // + level
 
 int num_threads() {
   const char *env = std::getenv("GG_THREADS");
@@ -209,6 +210,54 @@ void *gg_rmat_build(int32_t scale, int32_t edge_factor, double a, double b,
   *n_out = g->n;
   *m_out = g->m;
   if (raw_edges_out) *raw_edges_out = ne;
+  return g;
+}
+
+// Bipartite R-MAT: 2^scale_left hub vertices (ids [0, n_left)) and
+// 2^scale_right authority vertices (ids [n_left, n)). Edge i draws a
+// max(scale_left, scale_right)-level quadrant path like the square R-MAT
+// (its own stream tag); its row bits give the hub (the top scale_left of
+// them), its column bits the authority (the top scale_right). Every edge
+// joins a hub and an authority; the CSR holds both directions, rows sorted
+// and deduplicated.
+void *gg_rmat_bipartite_build(int32_t scale_left, int32_t scale_right, int32_t edge_factor,
+                              double a, double b, double c, uint64_t seed, int32_t *n_out,
+                              int32_t *n_left_out, int64_t *m_out) {
+  if (scale_left < 0 || scale_right < 0 || scale_left > 29 || scale_right > 29 ||
+      edge_factor < 1)
+    return nullptr;
+  const int32_t levels = std::max(scale_left, scale_right);
+  const int64_t n_left = (int64_t)1 << scale_left, n_right = (int64_t)1 << scale_right;
+  if (n_left + n_right > INT32_MAX) return nullptr;
+  const int32_t n = (int32_t)(n_left + n_right);
+  const int64_t ne = (int64_t)edge_factor * std::max(n_left, n_right);
+  const double two53 = 9007199254740992.0;
+  const uint64_t ta = (uint64_t)(a * two53 + 0.5);
+  const uint64_t tab = (uint64_t)((a + b) * two53 + 0.5);
+  const uint64_t tabc = (uint64_t)((a + b + c) * two53 + 0.5);
+  std::vector<int32_t> eu(ne), ev(ne);
+  parallel_for(ne, [&](int64_t b0, int64_t e0) {
+    for (int64_t i = b0; i < e0; ++i) {
+      uint32_t u = 0, v = 0;
+      for (int32_t l = 0; l < levels; ++l) {
+        uint64_t r = hash3(seed, kStreamBipartite + (uint64_t)l, (uint64_t)i) >> 11;
+        uint32_t ub, vb;
+        if (r < ta) { ub = 0; vb = 0; }
+        else if (r < tab) { ub = 0; vb = 1; }
+        else if (r < tabc) { ub = 1; vb = 0; }
+        else { ub = 1; vb = 1; }
+        u = (u << 1) | ub;
+        v = (v << 1) | vb;
+      }
+      eu[i] = (int32_t)(u >> (levels - scale_left));
+      ev[i] = (int32_t)(n_left + (v >> (levels - scale_right)));
+    }
+  });
+  Csr *g = new Csr(build_symmetric_csr(n, eu, ev));
+  if (g->n < 0) { delete g; return nullptr; }
+  *n_out = g->n;
+  *n_left_out = (int32_t)n_left;
+  *m_out = g->m;
   return g;
 }
 

@@ -33,8 +33,34 @@
  *                starting from r = 1/n, stopping after max_iter iterations or
  *                once sum |r' - r| < tol.
  *
+ *
+ * Beyond the five primitives (the paper's Sec. 5.5 "Bipartite graphs" and
+ * Sec. 7 "neighborhood operations"):
+ *
+ *   or_neighbor_reduce  for each vertex v of a frontier (or every vertex):
+ *                out[v] = the sum, the weighted sum (w(e) * x[u]), the
+ *                minimum or the maximum of x[u] over the entries e = (v, u)
+ *                of v's row; a vertex without entries gets the operation's
+ *                identity (0, +inf -> INT32_MAX, -inf -> INT32_MIN).
+ *   or_hits      Kleinberg's hubs and authorities on a bipartite graph
+ *                (left vertices [0, n_left) are hubs, the others
+ *                authorities): a[r] = sum of h[l] over the hubs l linked
+ *                to r, then h[l] = sum of a[r] over the authorities r linked
+ *                to l, each vector scaled to unit Euclidean length after
+ *                its update; h starts at 1/sqrt(n_left).
+ *   or_salsa     SALSA (Lempel and Moran) on the same bipartite graph: the
+ *                two random walks' alternating steps, a[r] = sum of
+ *                h[l]/deg(l), then h[l] = sum of a[r]/deg(r); h starts
+ *                uniform over the hubs that have links.
+ *   or_ppr       personalized PageRank (Haveliwala): the PageRank iteration
+ *                above with the teleport and the dangling mass sent to the
+ *                seed vertices (uniformly) instead of to all vertices.
+ *   The three rankings stop after max_iter iterations or once the summed
+ *   absolute change of their vectors falls below tol.
+ *
  * Graphs are CSR: row_off[n+1] (int32, row_off[0] = 0), col[m] (int32).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -293,5 +319,175 @@ int or_pagerank(int32_t n, const int32_t *row_off, const int32_t *col,
   }
   if (iters_out) *iters_out = it;
   free(next);
+  return 0;
+}
+
+/* ------------------------------------------------- neighbourhood reduce */
+enum { OR_REDUCE_SUM = 0, OR_REDUCE_WSUM = 1, OR_REDUCE_MIN = 2, OR_REDUCE_MAX = 3 };
+
+int or_neighbor_reduce(int32_t n, const int32_t *row_off, const int32_t *col,
+                       const uint32_t *w, int32_t op, const int32_t *frontier, int32_t q,
+                       const void *x, void *out) {
+  if (n < 1 || op < OR_REDUCE_SUM || op > OR_REDUCE_MAX) return -1;
+  if (op == OR_REDUCE_WSUM && !w) return -1;
+  const int32_t count = frontier ? q : n;
+  for (int32_t i = 0; i < count; ++i) {
+    const int32_t v = frontier ? frontier[i] : i;
+    if (v < 0 || v >= n) return -1;
+    if (op == OR_REDUCE_SUM || op == OR_REDUCE_WSUM) {
+      const double *xd = (const double *)x;
+      double acc = 0.0;
+      for (int32_t e = row_off[v]; e < row_off[v + 1]; ++e)
+        acc += (op == OR_REDUCE_WSUM ? (double)w[e] : 1.0) * xd[col[e]];
+      ((double *)out)[v] = acc;
+    } else {
+      const int32_t *xi = (const int32_t *)x;
+      int32_t acc = op == OR_REDUCE_MIN ? INT32_MAX : INT32_MIN;
+      for (int32_t e = row_off[v]; e < row_off[v + 1]; ++e) {
+        const int32_t t = xi[col[e]];
+        if (op == OR_REDUCE_MIN ? t < acc : t > acc) acc = t;
+      }
+      ((int32_t *)out)[v] = acc;
+    }
+  }
+  return 0;
+}
+
+/* ---------------------------------------------- bipartite node ranking */
+/* Every entry must join a hub (< n_left) and an authority (>= n_left). */
+static int bipartite_ok(int32_t n, int32_t n_left, const int32_t *row_off, const int32_t *col) {
+  if (n < 1 || n_left < 0 || n_left > n) return 0;
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t e = row_off[v]; e < row_off[v + 1]; ++e)
+      if ((v < n_left) == (col[e] < n_left)) return 0;
+  return 1;
+}
+
+static void scale_unit(double *x, int32_t lo, int32_t hi) {
+  double ss = 0.0;
+  for (int32_t i = lo; i < hi; ++i) ss += x[i] * x[i];
+  if (ss > 0.0) {
+    const double inv = 1.0 / sqrt(ss);
+    for (int32_t i = lo; i < hi; ++i) x[i] *= inv;
+  }
+}
+
+int or_hits(int32_t n, int32_t n_left, const int32_t *row_off, const int32_t *col,
+            int32_t max_iter, double tol, double *score, int32_t *iters_out) {
+  if (max_iter < 0 || !bipartite_ok(n, n_left, row_off, col)) return -1;
+  double *next = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!next) return -2;
+  /* score holds h on [0, n_left) and a on [n_left, n) */
+  for (int32_t v = 0; v < n; ++v) score[v] = v < n_left ? 1.0 / sqrt((double)n_left) : 0.0;
+  int32_t it = 0;
+  while (it < max_iter) {
+    for (int32_t r = n_left; r < n; ++r) {  /* authorities from hubs */
+      double acc = 0.0;
+      for (int32_t e = row_off[r]; e < row_off[r + 1]; ++e) acc += score[col[e]];
+      next[r] = acc;
+    }
+    scale_unit(next, n_left, n);
+    for (int32_t l = 0; l < n_left; ++l) {  /* hubs from the new authorities */
+      double acc = 0.0;
+      for (int32_t e = row_off[l]; e < row_off[l + 1]; ++e) acc += next[col[e]];
+      next[l] = acc;
+    }
+    scale_unit(next, 0, n_left);
+    double delta = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      delta += fabs(next[v] - score[v]);
+      score[v] = next[v];
+    }
+    ++it;
+    if (delta < tol) break;
+  }
+  free(next);
+  if (iters_out) *iters_out = it;
+  return 0;
+}
+
+int or_salsa(int32_t n, int32_t n_left, const int32_t *row_off, const int32_t *col,
+             int32_t max_iter, double tol, double *score, int32_t *iters_out) {
+  if (max_iter < 0 || !bipartite_ok(n, n_left, row_off, col)) return -1;
+  double *next = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!next) return -2;
+  int32_t linked = 0;
+  for (int32_t l = 0; l < n_left; ++l) linked += row_off[l + 1] > row_off[l];
+  for (int32_t v = 0; v < n; ++v)
+    score[v] = (v < n_left && row_off[v + 1] > row_off[v]) ? 1.0 / linked : 0.0;
+  int32_t it = 0;
+  while (it < max_iter) {
+    for (int32_t r = n_left; r < n; ++r) {  /* authority step */
+      double acc = 0.0;
+      for (int32_t e = row_off[r]; e < row_off[r + 1]; ++e) {
+        const int32_t l = col[e];
+        acc += score[l] / (row_off[l + 1] - row_off[l]);
+      }
+      next[r] = acc;
+    }
+    for (int32_t l = 0; l < n_left; ++l) {  /* hub step from the new authorities */
+      double acc = 0.0;
+      for (int32_t e = row_off[l]; e < row_off[l + 1]; ++e) {
+        const int32_t r = col[e];
+        acc += next[r] / (row_off[r + 1] - row_off[r]);
+      }
+      next[l] = acc;
+    }
+    double delta = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      delta += fabs(next[v] - score[v]);
+      score[v] = next[v];
+    }
+    ++it;
+    if (delta < tol) break;
+  }
+  free(next);
+  if (iters_out) *iters_out = it;
+  return 0;
+}
+
+int or_ppr(int32_t n, const int32_t *row_off, const int32_t *col, const int32_t *seeds,
+           int32_t ns, double damping, int32_t max_iter, double tol, double *rank,
+           int32_t *iters_out) {
+  if (n < 1 || ns < 1 || max_iter < 0 || !(damping > 0.0 && damping < 1.0)) return -1;
+  double *tele = (double *)calloc((size_t)n, sizeof(double));
+  double *next = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!tele || !next) {
+    free(tele);
+    free(next);
+    return -2;
+  }
+  for (int32_t i = 0; i < ns; ++i) {
+    if (seeds[i] < 0 || seeds[i] >= n || tele[seeds[i]] != 0.0) {  /* distinct seeds */
+      free(tele);
+      free(next);
+      return -1;
+    }
+    tele[seeds[i]] = 1.0 / ns;
+  }
+  for (int32_t v = 0; v < n; ++v) rank[v] = tele[v];
+  int32_t it = 0;
+  while (it < max_iter) {
+    double dangling = 0.0;
+    for (int32_t u = 0; u < n; ++u) {
+      next[u] = 0.0;
+      if (row_off[u + 1] == row_off[u]) dangling += rank[u];
+    }
+    for (int32_t u = 0; u < n; ++u) {
+      const int32_t deg = row_off[u + 1] - row_off[u];
+      for (int32_t e = row_off[u]; e < row_off[u + 1]; ++e) next[col[e]] += rank[u] / deg;
+    }
+    double delta = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      next[v] = (1.0 - damping) * tele[v] + damping * (next[v] + dangling * tele[v]);
+      delta += fabs(next[v] - rank[v]);
+      rank[v] = next[v];
+    }
+    ++it;
+    if (delta < tol) break;
+  }
+  free(tele);
+  free(next);
+  if (iters_out) *iters_out = it;
   return 0;
 }

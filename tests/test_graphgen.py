@@ -115,3 +115,25 @@ def test_sources_distinct_nonisolated():
     assert s.size == 16 and np.unique(s).size == 16
     assert np.all(np.diff(r)[s] > 0)
     assert np.array_equal(s, gg.sources(r, 16, seed=2))
+
+
+@pytest.mark.parametrize("sl,sr,ef", [(8, 8, 8), (10, 6, 4), (5, 9, 16)])
+def test_rmat_bipartite_shape(sl, sr, ef):
+    r, c, nl = gg.rmat_bipartite(sl, sr, ef, seed=7)
+    n = r.size - 1
+    assert nl == 1 << sl and n == (1 << sl) + (1 << sr)
+    rows = np.repeat(np.arange(n), np.diff(r))
+    assert np.all((rows < nl) != (c < nl))  # every entry joins a hub and an authority
+    keys = set(zip(rows.tolist(), c.tolist()))
+    assert all((v, u) in keys for u, v in keys)  # both directions stored
+    for v in range(0, n, max(1, n // 50)):
+        row = c[r[v]:r[v + 1]]
+        assert np.all(np.diff(row) > 0)  # sorted, no duplicates
+    assert c.size // 2 <= ef * max(1 << sl, 1 << sr)
+    r2, c2, _ = gg.rmat_bipartite(sl, sr, ef, seed=7)
+    assert np.array_equal(r, r2) and np.array_equal(c, c2)
+    r3, c3, _ = gg.rmat_bipartite(sl, sr, ef, seed=8)
+    assert not np.array_equal(c, c3)
+    # R-MAT skew: the lowest ids carry the most links on each side
+    deg = np.diff(r)
+    assert deg[:nl][: nl // 8].mean() > deg[:nl].mean()

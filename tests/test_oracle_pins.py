@@ -434,3 +434,217 @@ def test_oracle_rejects_bad_arguments():
         oracle.sssp(r, c, np.ones(c.size, np.uint32), -1)
     with pytest.raises(RuntimeError):
         oracle.pagerank(r, c, 1.5, 10, 0.0)
+
+
+# ------------------------------------------------- neighbourhood reduce
+def csr_matrix(r, c, data=None):
+    sp = pytest.importorskip("scipy.sparse")
+    n = r.size - 1
+    return sp.csr_matrix((np.ones(c.size) if data is None else data, c, r), shape=(n, n))
+
+
+def test_neighbor_reduce_sum_of_ones_is_degree():
+    r, c = gg.rmat(9, 8, seed=2)
+    out = oracle.neighbor_reduce(r, c, oracle.REDUCE_SUM, np.ones(r.size - 1))
+    assert np.array_equal(out, np.diff(r).astype(np.float64))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_neighbor_reduce_sums_vs_scipy(seed):
+    r, c = gg.rmat(10, 8, seed=seed)
+    n = r.size - 1
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(n)
+    w = gg.weights(r, c, seed=seed, wmin=1, wmax=64)
+    assert np.allclose(oracle.neighbor_reduce(r, c, oracle.REDUCE_SUM, x),
+                       csr_matrix(r, c) @ x, rtol=1e-12, atol=1e-12)
+    assert np.allclose(oracle.neighbor_reduce(r, c, oracle.REDUCE_WSUM, x, w=w),
+                       csr_matrix(r, c, w.astype(np.float64)) @ x, rtol=1e-12, atol=1e-12)
+    # unit weights: the weighted sum is the sum
+    assert np.array_equal(
+        oracle.neighbor_reduce(r, c, oracle.REDUCE_WSUM, x, w=np.ones(c.size, np.uint32)),
+        oracle.neighbor_reduce(r, c, oracle.REDUCE_SUM, x))
+
+
+def test_neighbor_reduce_min_label_propagation_gives_components():
+    """Repeated min over the closed neighbourhood reaches, at its fixed
+    point, the smallest vertex id of each component (scipy's components)."""
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    r, c = gg.grid(30, p_del=0.35, seed=5)
+    n = r.size - 1
+    label = np.arange(n, dtype=np.int32)
+    for _ in range(4 * n):
+        nb = oracle.neighbor_reduce(r, c, oracle.REDUCE_MIN, label)
+        new = np.minimum(label, nb)
+        if np.array_equal(new, label):
+            break
+        label = new
+    _, comp = csg.connected_components(csr_matrix(r, c), directed=False)
+    first = {}
+    for v in range(n):
+        first.setdefault(comp[v], v)
+    assert np.array_equal(label, np.array([first[comp[v]] for v in range(n)], np.int32))
+
+
+def test_neighbor_reduce_min_max_closed_forms_and_identity():
+    n = 9
+    r, c = gg.from_edges(n, [(i, i + 1) for i in range(n - 2)])  # path 0..7, 8 isolated
+    ids = np.arange(n, dtype=np.int32)
+    mx = oracle.neighbor_reduce(r, c, oracle.REDUCE_MAX, ids)
+    mn = oracle.neighbor_reduce(r, c, oracle.REDUCE_MIN, ids)
+    assert list(mx[:7]) == [v + 1 for v in range(7)] and mx[7] == 6
+    assert list(mn[1:8]) == [v - 1 for v in range(1, 8)] and mn[0] == 1
+    assert mx[8] == np.iinfo(np.int32).min and mn[8] == np.iinfo(np.int32).max
+    s = oracle.neighbor_reduce(r, c, oracle.REDUCE_SUM, ids.astype(np.float64))
+    assert s[8] == 0.0 and s[0] == 1.0 and s[3] == 6.0
+
+
+def test_neighbor_reduce_frontier_and_brute_force():
+    rng = np.random.default_rng(11)
+    r, c = gg.rmat(7, 6, seed=4)
+    n = r.size - 1
+    xi = rng.integers(-1000, 1000, n).astype(np.int32)
+    frontier = np.array([5, 0, 77, 5, n - 1], np.int32)
+    for op in (oracle.REDUCE_MIN, oracle.REDUCE_MAX):
+        full = oracle.neighbor_reduce(r, c, op, xi)
+        part = oracle.neighbor_reduce(r, c, op, xi, frontier=frontier)
+        ident = np.iinfo(np.int32).max if op == oracle.REDUCE_MIN else np.iinfo(np.int32).min
+        for v in range(n):
+            nb = [int(xi[u]) for u in c[r[v]:r[v + 1]]]
+            want = (min(nb) if op == oracle.REDUCE_MIN else max(nb)) if nb else ident
+            assert full[v] == want
+            assert part[v] == (want if v in set(frontier.tolist()) else ident)
+
+
+# ---------------------------------------------- bipartite node ranking
+def complete_bipartite(a, b):
+    return gg.from_edges(a + b, [(l, a + j) for l in range(a) for j in range(b)])
+
+
+def bipartite_matrix(r, c, n_left):
+    n = r.size - 1
+    A = np.zeros((n_left, n - n_left))
+    for l in range(n_left):
+        for u in c[r[l]:r[l + 1]]:
+            A[l, u - n_left] = 1.0
+    return A
+
+
+@pytest.mark.parametrize("a,b", [(1, 1), (3, 5), (6, 2)])
+def test_hits_complete_bipartite_uniform(a, b):
+    r, c = complete_bipartite(a, b)
+    s, it = oracle.hits(r, c, a, 50, 1e-14)
+    assert np.allclose(s[:a], 1.0 / np.sqrt(a), rtol=1e-14)
+    assert np.allclose(s[a:], 1.0 / np.sqrt(b), rtol=1e-14)
+    assert it <= 2
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_hits_is_the_dominant_singular_pair(seed):
+    """Authorities: the dominant eigenvector of A^T A; hubs: that of A A^T
+    (numpy eigh), on connected random bipartite graphs."""
+    rng = np.random.default_rng(seed)
+    nl, nr = 7, 9
+    edges = [(l, nl + j) for l in range(nl) for j in range(nr) if rng.random() < 0.45]
+    edges += [(l, nl + (l % nr)) for l in range(nl)] + [(j % nl, nl + j) for j in range(nr)]
+    r, c = gg.from_edges(nl + nr, edges)
+    s, _ = oracle.hits(r, c, nl, 5000, 1e-15)
+    A = bipartite_matrix(r, c, nl)
+    for M, part in ((A.T @ A, s[nl:]), (A @ A.T, s[:nl])):
+        vals, vecs = np.linalg.eigh(M)
+        v = np.abs(vecs[:, -1])
+        assert vals[-1] - vals[-2] > 1e-3  # a unique dominant direction
+        assert np.allclose(part, v / np.linalg.norm(v), atol=1e-9)
+
+
+def test_hits_first_iteration_by_hand():
+    # hubs 0, 1; authorities 2, 3, 4; links 0-2, 0-3, 1-3, 1-4
+    r, c = gg.from_edges(5, [(0, 2), (0, 3), (1, 3), (1, 4)])
+    s, it = oracle.hits(r, c, 2, 1, 0.0)
+    h0 = 1 / np.sqrt(2)
+    a = np.array([h0, 2 * h0, h0])
+    a /= np.linalg.norm(a)
+    h = np.array([a[0] + a[1], a[1] + a[2]])
+    h /= np.linalg.norm(h)
+    assert it == 1 and np.allclose(s, np.concatenate([h, a]), rtol=1e-15)
+
+
+def test_salsa_degree_closed_form_connected():
+    r, c, nl = gg.rmat_bipartite(7, 6, 8, seed=5)
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    ncomp, comp = csg.connected_components(csr_matrix(r, c), directed=False)
+    deg = np.diff(r).astype(np.float64)
+    s, it = oracle.salsa(r, c, nl, 20000, 1e-15)
+    # per component C (with links): hubs get (linked hubs of C / linked hubs)
+    # * deg / |E_C|, authorities (the same share) * deg / |E_C|
+    linked = (deg[:nl] > 0).sum()
+    want = np.zeros_like(s)
+    for k in range(ncomp):
+        vs = np.nonzero(comp == k)[0]
+        e_c = deg[vs].sum() / 2
+        if e_c == 0:
+            continue
+        share = (deg[vs[vs < nl]] > 0).sum() / linked
+        want[vs] = share * deg[vs] / e_c
+    assert np.allclose(s, want, atol=1e-12)
+    assert abs(s[:nl].sum() - 1) < 1e-12 and abs(s[nl:].sum() - 1) < 1e-12
+
+
+def test_salsa_first_iteration_by_hand():
+    r, c = gg.from_edges(5, [(0, 2), (0, 3), (1, 3), (1, 4)])
+    s, _ = oracle.salsa(r, c, 2, 1, 0.0)
+    h0 = np.array([0.5, 0.5])
+    a = np.array([h0[0] / 2, h0[0] / 2 + h0[1] / 2, h0[1] / 2])
+    h = np.array([a[0] / 1 + a[1] / 2, a[1] / 2 + a[2] / 1])
+    assert np.allclose(s, np.concatenate([h, a]), rtol=1e-15)
+
+
+def test_ppr_all_seeds_is_pagerank():
+    r, c = gg.rmat(10, 8, seed=7)
+    n = r.size - 1
+    a, ia = oracle.ppr(r, c, np.arange(n), 0.85, 60, 0.0)
+    b, ib = oracle.pagerank(r, c, 0.85, 60, 0.0)
+    assert ia == ib == 60 and np.allclose(a, b, rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ppr_exact_fixed_point(seed):
+    n = 30
+    r, c = random_graph(n, 0.1, seed)
+    deg = np.diff(r)
+    seeds = np.array(sorted({int(x) for x in np.random.default_rng(seed).integers(0, n, 3)}))
+    t = np.zeros(n)
+    t[seeds] = 1.0 / seeds.size
+    P = np.zeros((n, n))
+    for u in range(n):
+        for v in c[r[u]:r[u + 1]]:
+            P[v, u] += 1.0 / deg[u]
+    M = P + np.outer(t, (deg == 0).astype(np.float64))
+    exact = np.linalg.solve(np.eye(n) - 0.85 * M, (1 - 0.85) * t)
+    got, _ = oracle.ppr(r, c, seeds, 0.85, 3000, 1e-16)
+    assert np.allclose(got, exact, rtol=1e-11, atol=1e-15)
+    assert abs(got.sum() - 1.0) < 1e-12
+
+
+def test_ppr_vs_networkx_personalization():
+    nx = pytest.importorskip("networkx")
+    r, c, nl = gg.rmat_bipartite(8, 7, 8, seed=9)
+    n = r.size - 1
+    G = nx.DiGraph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from(zip(np.repeat(np.arange(n), np.diff(r)).tolist(), c.tolist()))
+    seeds = [int(v) for v in np.nonzero(np.diff(r)[:nl] > 0)[0][:4]]
+    ref = nx.pagerank(G, alpha=0.85, personalization={s: 1.0 for s in seeds},
+                      tol=1e-14, max_iter=2000)
+    got, _ = oracle.ppr(r, c, seeds, 0.85, 2000, 1e-15)
+    assert relative_l1(got, [ref[v] for v in range(n)]) < 1e-9
+
+
+def test_bipartite_oracles_reject_bad_input():
+    r, c = gg.from_edges(4, [(0, 1), (0, 2), (2, 3)])  # 0-2 joins two hubs when n_left = 3
+    with pytest.raises(RuntimeError):
+        oracle.hits(r, c, 3)
+    with pytest.raises(RuntimeError):
+        oracle.salsa(r, c, 3)
+    with pytest.raises(RuntimeError):
+        oracle.ppr(r, c, [1, 1])  # repeated seed
