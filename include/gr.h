@@ -253,6 +253,59 @@ gr_status gr_bfs_batch_stats(gr_graph *g, int32_t *levels);
 gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc,
                 const gr_opts *opts, void *stream);
 
+/* Neighbourhood gather-reduce (the operator Sec. 7 proposes for reductions
+ * over neighbour lists): for each vertex v of a set, out[v] = the
+ * reduction, over the entries e = (v, u) of v's row (its out-neighbours;
+ * its in-neighbours on a symmetric CSR), of
+ *   GR_REDUCE_SUM   x[u]            (x, out: double)
+ *   GR_REDUCE_WSUM  w(e) * x[u]     (double; needs edge weights)
+ *   GR_REDUCE_MIN   x[u]            (x, out: int32)
+ *   GR_REDUCE_MAX   x[u]            (int32)
+ * A vertex without entries gets the identity: 0, INT32_MAX or INT32_MIN.
+ * The set is every vertex (frontier NULL) or the q distinct vertices of
+ * frontier[q] (device int32; a repeated vertex makes its sum undefined);
+ * out entries of vertices outside the set are left as they are. x[n] must
+ * be device memory; out[n] is device or host memory. Sums are in FP64 in an
+ * order that differs from a sequential loop (rounding at the level of
+ * FP64's epsilon times the row's absolute sum); min and max are exact. */
+enum { GR_REDUCE_SUM = 0, GR_REDUCE_WSUM = 1, GR_REDUCE_MIN = 2, GR_REDUCE_MAX = 3 };
+gr_status gr_neighbor_reduce(gr_graph *g, int32_t op, const int32_t *frontier, int32_t q,
+                             const void *x, void *out, void *stream);
+
+/* Node rankings on a bipartite graph (Sec. 5.5 "Bipartite graphs": the
+ * HITS, SALSA and personalized-PageRank rankings of the who-to-follow
+ * computation the paper cites, each iteration a 2-hop traversal hub ->
+ * authority -> hub). The graph is given as a symmetric CSR whose vertices
+ * [0, n_left) are hubs and [n_left, n) authorities, every entry joining a
+ * hub and an authority (else GR_EINVAL). score[n] (double, device or host)
+ * receives the hub scores on [0, n_left) and the authority scores on
+ * [n_left, n).
+ *   gr_hits   Kleinberg: a[r] = sum of h[l] over the hubs l linked to r,
+ *             then h[l] = sum of a[r] over the authorities r linked to l,
+ *             each vector scaled to unit Euclidean length after its update
+ *             (left as is if zero); h starts at 1/sqrt(n_left), a at 0.
+ *   gr_salsa  Lempel and Moran: a[r] = sum of h[l] / deg(l), then
+ *             h[l] = sum of a[r] / deg(r); h starts at 1/(hubs with links)
+ *             on those hubs, 0 elsewhere.
+ * Both stop after max_iter iterations or once the summed absolute change of
+ * all scores in an iteration is below tol; *iters (host, may be NULL;
+ * asking for it synchronises) receives the iterations run. FP64, one
+ * cooperative kernel for the whole iteration loop. */
+gr_status gr_hits(gr_graph *g, int32_t n_left, int32_t max_iter, double tol, double *score,
+                  int32_t *iters, void *stream);
+gr_status gr_salsa(gr_graph *g, int32_t n_left, int32_t max_iter, double tol, double *score,
+                   int32_t *iters, void *stream);
+
+/* Personalized PageRank (the PageRank iteration of gr_pagerank with the
+ * teleport and the dangling mass sent uniformly to the seeds instead of all
+ * vertices): r'[v] = (1 - damping) t[v] + damping * (sum over entries (v, u)
+ * of r[u]/deg(u) + D t[v]), t = 1/num_seeds on each seed, D = the rank mass
+ * on degree-0 vertices, r0 = t. seeds[num_seeds] (host, distinct, in
+ * [0, n)). The CSR must be symmetric (the gather runs over rows). Stops as
+ * gr_hits does; rank[n] (double, device or host); FP64. */
+gr_status gr_ppr(gr_graph *g, const int32_t *seeds, int32_t num_seeds, double damping,
+                 int32_t max_iter, double tol, double *rank, int32_t *iters, void *stream);
+
 /* BFS that allocates nothing, for callers that cannot call cudaMalloc:
  * code running while a CUDA stream is being captured into a graph (an
  * allocation there breaks the capture), hosts whose device memory is owned

@@ -175,53 +175,102 @@ __device__ void lb_advance(const int32_t *R, const int32_t *C, const int32_t *Q,
 namespace gr {
 
 // --------------------------------------------------- neighbourhood reduce
-// Gather-reduce over the neighbourhoods of all vertices (the operator the
-// paper proposes in Sec. 7 for reductions over neighbour lists):
-// acc[v] += sum over edges e = (v, u) of g(u, e), for every v.
+// Gather-reduce over neighbourhoods (the operator the paper proposes in
+// Sec. 7 for reductions over neighbour lists): for each vertex v of a set,
+// acc[v] = OP over the entries e = (v, u) of v's row of g(u, e).
 //
-// Merge-based form: the vertex-end markers (R[v+1] + v) and the edge ranks
-// form one merged sequence split into equal chunks (as in lb_advance). A
-// block stages its chunk's end markers and the gathered values g(C[e], e) of
-// its edges in shared memory (coalesced column loads, all gathers of the
-// chunk in flight at once); then each thread takes ITEMS consecutive items
-// of the chunk, finds its start with one search in shared memory and walks
-// them in order, adding values and closing a vertex at each end marker. A
-// vertex whose edges lie inside one thread's items is written with a plain
-// store; the pieces of a vertex split between threads or chunks are added
-// with atomicAdd. acc must be zero beforehand.
-template <int THREADS, int ITEMS, class T, class G>
-__device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n, G &g,
-                                   T *acc) {
+// The set is either a vertex range [v0, v0 + q) (Q == nullptr; S = R + v0,
+// so S[i] is the CSR position of vertex v0 + i's row) or a frontier list
+// Q[0..q) with its exclusive degree scan S (S[0] = 0, S[q] = its entries).
+// Merge-based form: the vertices' end markers and their entries form one
+// merged sequence split into equal chunks (as in lb_advance). A block
+// stages its chunk's end markers and the gathered values g(C[e], e) of its
+// entries in shared memory (coalesced column loads for a range, all gathers
+// of the chunk in flight at once); then each thread takes ITEMS consecutive
+// items of the chunk, finds its start with one search in shared memory and
+// walks them in order, combining values and closing a vertex at each end
+// marker. A vertex whose entries lie inside one thread's items is written
+// with a plain store; the pieces of a vertex split between threads or chunks
+// are combined with OP's atomic. acc[v] must hold OP's identity beforehand
+// for every vertex of the set, and a frontier must not repeat a vertex.
+template <class T>
+struct ReduceSum {
+  static __device__ __forceinline__ T identity() { return T(0); }
+  static __device__ __forceinline__ T op(T a, T b) { return a + b; }
+  static __device__ __forceinline__ void atomic(T *p, T v) { atomicAdd(p, v); }
+};
+struct ReduceMinI32 {
+  static __device__ __forceinline__ int32_t identity() { return INT32_MAX; }
+  static __device__ __forceinline__ int32_t op(int32_t a, int32_t b) { return min(a, b); }
+  static __device__ __forceinline__ void atomic(int32_t *p, int32_t v) { atomicMin(p, v); }
+};
+struct ReduceMaxI32 {
+  static __device__ __forceinline__ int32_t identity() { return INT32_MIN; }
+  static __device__ __forceinline__ int32_t op(int32_t a, int32_t b) { return max(a, b); }
+  static __device__ __forceinline__ void atomic(int32_t *p, int32_t v) { atomicMax(p, v); }
+};
+
+template <int THREADS, int ITEMS, class T, class OP, bool FRONTIER, class G>
+__device__ void lb_gather_reduce(const int32_t *R, const int32_t *C, const int32_t *Q,
+                                 const int32_t *S, int32_t q, int32_t v0, G &g, T *acc) {
   constexpr int CHUNK = THREADS * ITEMS;
-  const long long total = (long long)n + R[n];
+  // diagonals are absolute: d + S[0] (the path starts at S[0], the first
+  // entry's CSR position for a range, 0 for a frontier)
+  const int32_t s0 = S[0];
+  const long long total = (long long)q + (S[q] - s0);
   const long long nchunks = (total + CHUNK - 1) / CHUNK;
   __shared__ int32_t s_end[CHUNK + 1];  // end marker of each vertex, chunk-local
   __shared__ T s_val[CHUNK];
+  __shared__ int32_t s_off[FRONTIER ? CHUNK + 1 : 1];  // frontier: the vertices' scan values
+  __shared__ int32_t s_row[FRONTIER ? CHUNK + 1 : 1];  // frontier: their row starts
   __shared__ int32_t s_red8[THREADS / 32];
+  (void)s_off;
+  (void)s_row;
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-    const long long d0 = chunk * CHUNK;
-    const long long d1 = min(d0 + CHUNK, total);
+    const long long d0 = chunk * CHUNK + s0;
+    const long long d1 = min(chunk * CHUNK + CHUNK, total) + s0;
     int32_t i0, i1;
-    block_chunk_bounds<THREADS>(R, n, R[n], d0, d1, CHUNK, s_red8, &i0, &i1);
-    const long long j0 = d0 - i0, j1 = d1 - i1;
-    const int32_t nv = (i0 <= n - 1) ? (min(i1, n - 1) - i0 + 1) : 0;
+    block_chunk_bounds<THREADS>(S, q, S[q], d0, d1, CHUNK, s_red8, &i0, &i1);
+    const long long j0 = d0 - i0, j1 = d1 - i1;  // entries [j0, j1) (scan positions)
+    const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     const int32_t ne = (int32_t)(j1 - j0);
     const int32_t len = (int32_t)(d1 - d0);
-    for (int32_t k = threadIdx.x; k < nv; k += THREADS)
-      s_end[k] = (int32_t)((long long)R[i0 + k + 1] + i0 + k - d0);
+    for (int32_t k = threadIdx.x; k < nv; k += THREADS) {
+      s_end[k] = (int32_t)((long long)S[i0 + k + 1] + i0 + k - d0);
+      if (FRONTIER) {
+        s_off[k] = S[i0 + k];
+        s_row[k] = R[Q[i0 + k]];
+      }
+    }
+    if (FRONTIER) __syncthreads();
     {
       // all column loads of the thread first, then all gathers: ITEMS
       // independent gathers in flight per thread
-      int32_t col[ITEMS];
+      int32_t col[ITEMS], pos[ITEMS];
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         const int32_t k = threadIdx.x + i * THREADS;
-        col[i] = k < ne ? C[j0 + k] : 0;
+        pos[i] = 0;
+        if (k < ne) {
+          if (FRONTIER) {
+            const int32_t er = (int32_t)(j0 + k);  // rank in the frontier's entries
+            int32_t lo = 0, hi = nv - 1;
+            while (lo < hi) {
+              const int32_t mid = (lo + hi + 1) >> 1;
+              if (s_off[mid] <= er) lo = mid;
+              else hi = mid - 1;
+            }
+            pos[i] = s_row[lo] + (er - s_off[lo]);
+          } else {
+            pos[i] = (int32_t)(j0 + k);
+          }
+        }
+        col[i] = k < ne ? C[pos[i]] : 0;
       }
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         const int32_t k = threadIdx.x + i * THREADS;
-        if (k < ne) s_val[k] = g(col[i], (int32_t)(j0 + k));
+        if (k < ne) s_val[k] = g(col[i], pos[i]);
       }
     }
     __syncthreads();
@@ -237,28 +286,36 @@ __device__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n
         else hi = mid;
       }
       int32_t r = lo;
-      int32_t e = k0 - r;   // chunk-local edge index
-      T sum = T(0);
-      bool first = true;    // the current vertex may have edges before k0
+      int32_t e = k0 - r;   // chunk-local entry index
+      T red = OP::identity();
+      bool first = true;    // the current vertex may have entries before k0
       for (int32_t k = k0; k < k1; ++k) {
-        if (r < nv && s_end[r] == k) {  // end marker of vertex i0 + r
-          if (first) {
-            if (sum != T(0)) atomicAdd(acc + i0 + r, sum);
-          } else if (sum != T(0)) {
-            acc[i0 + r] = sum;
+        if (r < nv && s_end[r] == k) {  // end marker of set member i0 + r
+          const int32_t v = FRONTIER ? Q[i0 + r] : v0 + i0 + r;
+          if (red != OP::identity()) {
+            if (first) OP::atomic(acc + v, red);
+            else acc[v] = red;
           }
-          sum = T(0);
+          red = OP::identity();
           first = false;
           ++r;
         } else {
-          sum += s_val[e];
+          red = OP::op(red, s_val[e]);
           ++e;
         }
       }
-      if (sum != T(0) && r < nv) atomicAdd(acc + i0 + r, sum);  // continues past k1
+      if (red != OP::identity() && r < nv)  // continues past k1
+        OP::atomic(acc + (FRONTIER ? Q[i0 + r] : v0 + i0 + r), red);
     }
     __syncthreads();
   }
+}
+
+// All vertices, summed (PageRank's gather): acc[v] += sum of g over v's row.
+template <int THREADS, int ITEMS, class T, class G>
+__device__ __forceinline__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n,
+                                                   G &g, T *acc) {
+  lb_gather_reduce<THREADS, ITEMS, T, ReduceSum<T>, false>(R, C, nullptr, R, n, 0, g, acc);
 }
 
 }  // namespace gr

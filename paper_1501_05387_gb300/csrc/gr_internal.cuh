@@ -78,6 +78,7 @@ struct SsspWorkspace;
 struct CcWorkspace;
 struct PrWorkspace;
 struct BatchWorkspace;
+struct RankWorkspace;
 
 }  // namespace gr
 
@@ -123,6 +124,7 @@ struct gr_graph {
   gr::CcWorkspace *cc = nullptr;
   gr::PrWorkspace *pr = nullptr;
   gr::BatchWorkspace *batch = nullptr;
+  gr::RankWorkspace *rank = nullptr;  // gr_neighbor_reduce, gr_hits, gr_salsa, gr_ppr
 
   gr::DevMem stage[2];  // device staging for host output pointers
 
@@ -195,6 +197,7 @@ void free_sssp(SsspWorkspace *);
 void free_cc(CcWorkspace *);
 void free_pr(PrWorkspace *);
 void free_batch(BatchWorkspace *);
+void free_rank(RankWorkspace *);
 
 // ------------------------------------------------------ bounds guards
 // In a GR_CHECKED build every data-dependent index of the kernels is checked

@@ -264,6 +264,8 @@ static void destroy_workspaces(gr_graph *g) {
   g->pr = nullptr;
   free_batch(g->batch);
   g->batch = nullptr;
+  free_rank(g->rank);
+  g->rank = nullptr;
 }
 }  // namespace gr
 

@@ -33,6 +33,7 @@ GR_DIR_AUTO, GR_DIR_PUSH, GR_DIR_PULL = 0, 1, 2
 GR_MODE_AUTO, GR_MODE_LAUNCH, GR_MODE_GRAPH, GR_MODE_PERSISTENT = 0, 1, 2, 3
 GR_QUERY_BFS, GR_QUERY_SSSP, GR_QUERY_CC = 0, 1, 2
 GR_NOALLOC_INCOMPLETE = -2
+GR_REDUCE_SUM, GR_REDUCE_WSUM, GR_REDUCE_MIN, GR_REDUCE_MAX = 0, 1, 2, 3
 GR_TUNE_BFS, GR_TUNE_SSSP = 1, 2
 
 
@@ -92,6 +93,10 @@ _sig("gr_server_stats", [_vp, _P(_i64), _P(_i64), _P(_i64), _P(ctypes.c_double),
                          _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)])
 _sig("gr_server_destroy", [_vp])
 _sig("gr_bfs_noalloc", [_i32, _i64, _vp, _vp, _i32, _vp, _vp, _vp])
+_sig("gr_neighbor_reduce", [_vp, _i32, _vp, _i32, _vp, _vp, _vp])
+_sig("gr_hits", [_vp, _i32, _i32, ctypes.c_double, _vp, _P(_i32), _vp])
+_sig("gr_salsa", [_vp, _i32, _i32, ctypes.c_double, _vp, _P(_i32), _vp])
+_sig("gr_ppr", [_vp, _vp, _i32, ctypes.c_double, _i32, ctypes.c_double, _vp, _P(_i32), _vp])
 _sig("gr_cc", [_vp, _vp, _P(_i32), _P(gr_opts), _vp])
 _sig("gr_pagerank", [_vp, ctypes.c_float, _i32, ctypes.c_double, _vp, _P(_i32),
                      _P(gr_opts), _vp])
@@ -337,6 +342,43 @@ def gr_bfs_noalloc(row_off, col, src: int, depth, parent=None, stream=None):
         raise ValueError(f"depth and parent must hold at least n = {n} entries")
     _check(_lib.gr_bfs_noalloc(n, int(col.shape[0]), _ptr(row_off), _ptr(col), int(src),
                                _ptr(depth), _ptr(parent), _stream(stream)), "gr_bfs_noalloc")
+
+
+def gr_neighbor_reduce(g: Graph, op: int, x, out, frontier=None, stream=None):
+    """out[v] = sum / weighted sum (float64) or min / max (int32) of x[u]
+    over the entries (v, u) of v's row, for every vertex or the distinct
+    vertices of a device int32 frontier tensor."""
+    q = 0 if frontier is None else int(frontier.numel())
+    _check(_lib.gr_neighbor_reduce(g.handle, int(op), _ptr(frontier), q, _ptr(x), _ptr(out),
+                                   _stream(stream)), "gr_neighbor_reduce")
+
+
+def gr_hits(g: Graph, n_left: int, score, max_iter=100, tol=1e-10, stream=None, count=True):
+    """HITS hub (on [0, n_left)) and authority scores into score[n]
+    (float64); returns the iterations run (synchronises) when count."""
+    it = _i32()
+    _check(_lib.gr_hits(g.handle, int(n_left), int(max_iter), float(tol), _ptr(score),
+                        ctypes.byref(it) if count else None, _stream(stream)), "gr_hits")
+    return it.value if count else None
+
+
+def gr_salsa(g: Graph, n_left: int, score, max_iter=100, tol=1e-10, stream=None, count=True):
+    """SALSA hub and authority scores into score[n] (float64)."""
+    it = _i32()
+    _check(_lib.gr_salsa(g.handle, int(n_left), int(max_iter), float(tol), _ptr(score),
+                         ctypes.byref(it) if count else None, _stream(stream)), "gr_salsa")
+    return it.value if count else None
+
+
+def gr_ppr(g: Graph, seeds, rank, damping=0.85, max_iter=50, tol=1e-7, stream=None,
+           count=True):
+    """Personalized PageRank from distinct seeds into rank[n] (float64)."""
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32))
+    it = _i32()
+    _check(_lib.gr_ppr(g.handle, seeds.ctypes.data, int(seeds.size), float(damping),
+                       int(max_iter), float(tol), _ptr(rank),
+                       ctypes.byref(it) if count else None, _stream(stream)), "gr_ppr")
+    return it.value if count else None
 
 
 def gr_cc(g: Graph, label, opts=None, stream=None, count=True):
