@@ -299,19 +299,25 @@ def serving_bench(gr, full=False, count=2000):
                         sl, batch, budget)
         # throughput: both paths see the whole stream at once (saturated);
         # latency: both at 0.7x their own saturated throughput
-        plain = run_serving(gr, graphs, batchable, reqs, unit, 1e9, 1, 1, budget)
-        served = run_serving(gr, graphs, batchable, reqs, unit, 1e9, slots, 64, budget)
+        # a phase may take as long as its requests run one at a time on the
+        # largest graphs (the 4096^2 grids' SSSP: about 70 ms each)
+        drain = max(300.0, 0.1 * len(reqs))
+        plain = run_serving(gr, graphs, batchable, reqs, unit, 1e9, 1, 1, budget, drain)
+        served = run_serving(gr, graphs, batchable, reqs, unit, 1e9, slots, 64, budget, drain)
         plain_lat = run_serving(gr, graphs, batchable, reqs, unit, 0.7 * plain["qps"], 1, 1,
-                                budget)
+                                budget, drain)
         served_lat = run_serving(gr, graphs, batchable, reqs, unit, 0.7 * served["qps"], slots,
-                                 64, budget)
-        # and at the plain path's latency-run load (the same arrival times)
-        served_eq = run_serving(gr, graphs, batchable, reqs, unit, 0.7 * plain["qps"], slots,
-                                64, budget)
+                                 64, budget, drain)
+        # and at the plain path's latency-run load (the same arrival times;
+        # the full pool skips it: its arrivals alone take as long as the
+        # plain latency run)
+        served_eq = None if full else run_serving(gr, graphs, batchable, reqs, unit,
+                                                  0.7 * plain["qps"], slots, 64, budget, drain)
     finally:
         for g in graphs:
             g.close()
-    pick = lambda st: {k: st[k] for k in ("qps", "p50_ms", "p99_ms", "mean_batch", "launches")}
+    pick = lambda st: None if st is None else {k: st[k] for k in ("qps", "p50_ms", "p99_ms",
+                                                                 "mean_batch", "launches")}
     return {"requests": count, "graphs": len(pool),
             "pool": "24-graph pool" if full else "6-graph subset (R-MAT s16-s20, grids 512/1024)",
             "mix": "60/30/10 BFS/SSSP/CC, Poisson arrivals seed 6",

@@ -349,6 +349,8 @@ def gr_neighbor_reduce(g: Graph, op: int, x, out, frontier=None, stream=None):
     over the entries (v, u) of v's row, for every vertex or the distinct
     vertices of a device int32 frontier tensor."""
     q = 0 if frontier is None else int(frontier.numel())
+    if frontier is not None and q == 0:
+        return  # an empty frontier reduces nothing (its data pointer may be NULL)
     _check(_lib.gr_neighbor_reduce(g.handle, int(op), _ptr(frontier), q, _ptr(x), _ptr(out),
                                    _stream(stream)), "gr_neighbor_reduce")
 
