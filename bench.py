@@ -81,7 +81,8 @@ def parse():
                     help="instead of the BFS line, measure every primitive on its workload "
                          "(SSSP s22, grid 4096^2 BFS/SSSP/CC, s23 PageRank/CC/BC/batched BFS)")
     ap.add_argument("--suite-part", default="all",
-                    choices=["all", "sssp", "grid", "rmat", "pagerank", "cc", "bfs64", "bc64"],
+                    choices=["all", "sssp", "grid", "rmat", "pagerank", "cc", "bfs64", "bc64",
+                             "reduce", "bipartite"],
                     help="run one part of the suite (profiling runs)")
     ap.add_argument("--suite-scale", type=int, default=0,
                     help="R-MAT scale of the suite part (profiling runs; 0: the specified one)")
@@ -388,8 +389,10 @@ def run_suite(args):
         suite_sssp(args, gr, gg, torch, dev, flush, peak, out, reach_bytes)
     if want("grid"):
         suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes)
-    if want("rmat", "pagerank", "cc", "bfs64", "bc64"):
+    if want("rmat", "pagerank", "cc", "bfs64", "bc64", "reduce"):
         suite_rmat(args, gr, gg, torch, dev, flush, peak, out, want)
+    if want("bipartite"):
+        suite_bipartite(args, gr, gg, torch, dev, flush, peak, out)
     print(json.dumps({"suite": out, "peak_hbm_gbs": peak}), flush=True)
 
 
@@ -520,6 +523,38 @@ def suite_grid(args, gr, gg, torch, dev, flush, peak, out, reach_bytes):
     g.close()
 
 
+def suite_bipartite(args, gr, gg, torch, dev, flush, peak, out):
+    # --- bipartite R-MAT: 2^22 hubs, 2^20 authorities, edge factor 16 (seed
+    # 7): HITS, SALSA and personalized PageRank, 20 iterations each
+    sl = args.suite_scale or 22
+    sr = sl - 2
+    r, c, nl = gg.rmat_bipartite(sl, sr, 16, seed=7)
+    n, m = r.size - 1, c.size
+    g = gr.gr_graph_create(r, c)
+    score = torch.empty(n, dtype=torch.float64, device=dev)
+    iters = 20
+    per_iter = 2 * (4 * m + 4 * (n + 1)) + 3 * 8 * n
+
+    def row(name, fn, bytes_model):
+        ms, _ = _timed_calls(fn, 2, flush)
+        out.append({"workload": f"bipartite{sl}x{sr}_{name}", "primitive": name, "calls": 2,
+                    "iterations": iters, "ms_per_call": ms, "ms_per_iteration": ms / iters,
+                    "throughput": iters * m / (ms * 1e-3) / 1e9,
+                    "unit": "G entries/s (entries x iterations)", "n": n, "n_left": nl, "m": m,
+                    "roofline": _roof(iters * per_iter, ms, peak, bytes_model)})
+
+    model = ("per iteration the two gather passes read every column entry and row offset "
+             "once; scores, sums and score/degree written and read once per vertex (8 B)")
+    row("hits", lambda: gr.gr_hits(g, nl, score, max_iter=iters, tol=0.0, count=False), model)
+    row("salsa", lambda: gr.gr_salsa(g, nl, score, max_iter=iters, tol=0.0, count=False), model)
+    seeds = [int(v) for v in gg.sources(r, 8, seed=7)]
+    per_iter = 4 * m + 4 * (n + 1) + 4 * 8 * n
+    row("ppr", lambda: gr.gr_ppr(g, seeds, score, 0.85, iters, 0.0, count=False),
+        "per iteration one gather pass over every column entry and row offset; rank, "
+        "rank/degree, sums and teleport once per vertex (8 B)")
+    g.close()
+
+
 def suite_rmat(args, gr, gg, torch, dev, flush, peak, out, want):
     # --- R-MAT s23 (seed 5): PageRank, CC, batched BFS and BC over 64 sources
     scale = args.suite_scale or 23
@@ -539,6 +574,29 @@ def suite_rmat(args, gr, gg, torch, dev, flush, peak, out, want):
                     "roofline": _roof(4 * m + 4 * (n + 1) + 8 * n, ms, peak,
                                       "4 B per column entry, 4 B per row offset, label write "
                                       "at init and after pointer jumping")})
+    if want("rmat", "reduce"):
+        # the gather-reduce operator over every vertex: FP64 sum and int32 min
+        x = torch.rand(n, dtype=torch.float64, device=dev)
+        outr = torch.empty(n, dtype=torch.float64, device=dev)
+        ms, _ = _timed_calls(lambda: gr.gr_neighbor_reduce(g, gr.GR_REDUCE_SUM, x, outr), 3,
+                             flush)
+        out.append({"workload": f"{tag}_reduce_sum", "primitive": "gather-reduce (sum, f64)",
+                    "calls": 3, "ms_per_call": ms, "throughput": m / (ms * 1e-3) / 1e9,
+                    "unit": "G entries/s",
+                    "roofline": _roof(4 * m + 4 * (n + 1) + 16 * n, ms, peak,
+                                      "4 B per column entry, 4 B per row offset, x read and "
+                                      "out written once (8 B each per vertex)")})
+        xi = torch.randint(0, 1 << 30, (n,), dtype=torch.int32, device=dev)
+        outi = torch.empty(n, dtype=torch.int32, device=dev)
+        ms, _ = _timed_calls(lambda: gr.gr_neighbor_reduce(g, gr.GR_REDUCE_MIN, xi, outi), 3,
+                             flush)
+        out.append({"workload": f"{tag}_reduce_min", "primitive": "gather-reduce (min, i32)",
+                    "calls": 3, "ms_per_call": ms, "throughput": m / (ms * 1e-3) / 1e9,
+                    "unit": "G entries/s",
+                    "roofline": _roof(4 * m + 4 * (n + 1) + 8 * n, ms, peak,
+                                      "4 B per column entry, 4 B per row offset, x read and "
+                                      "out written once (4 B each per vertex)")})
+        del x, outr, xi, outi
     lv = None
     if want("rmat", "bfs64"):
         depth64 = torch.empty(64 * n, dtype=torch.int32, device=dev)
