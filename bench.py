@@ -650,15 +650,31 @@ def suite_pagerank(gr, torch, dev, flush, peak, out, g, n, m, tag, mode="auto"):
                                   "contribution write, rank read+write (12 B per vertex)")})
 
 
+def host_cpu():
+    """The host's logical core count (nproc) and CPU model (lscpu)."""
+    info = {"host_cores": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() in ("Model name", "Vendor ID", "Architecture") and val.strip():
+                info[key.strip().lower().replace(" ", "_")] = val.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return info
+
+
 def cpu_baseline(r, c, srcs, m, k):
     import oracle
     t0 = time.perf_counter()
     for s in srcs[:k]:
         oracle.bfs(r, c, int(s))
     dt = time.perf_counter() - t0
-    return {"value": m * k / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{k} of the {NUM_SOURCES} sources, single-threaded queue BFS, "
-                      f"{dt:.2f} s wall"}
+    out = {"value": m * k / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+           "sample": f"{k} of the {NUM_SOURCES} sources, single-threaded queue BFS, "
+                     f"{dt:.2f} s wall"}
+    out.update(host_cpu())
+    return out
 
 
 def run_reference(args):
@@ -687,8 +703,8 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "graph": f"R-MAT s{SCALE} ef{EDGE_FACTOR} seed {GRAPH_SEED}",
                        "n": int(r.size - 1), "m": m,
                        "sources_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} traversals per step"},
+            "cpu_baseline": dict({"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                                  "sample": f"{per_step} traversals per step"}, **host_cpu()),
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

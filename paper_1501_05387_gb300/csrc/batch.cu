@@ -68,7 +68,7 @@ enum : int { kSigNone = 0, kSigU64 = 1, kSigF64 = 2 };
 
 
 struct BatchWorkspace {
-  DevMem visit, sigma, q, counter, lmp, ctl;
+  DevMem visit, sigma, q, qds, counter, lmp, ctl;
   DevMem fq, fs;    // BC backward: one level's vertex list and degree scan
   DevMem lq[3], ls[3];  // forward: level lists (ring by level) and degree scans
   std::vector<DevMem *> lm;  // level mask arrays ("slots")
@@ -770,15 +770,111 @@ struct BcBackArgs {
   long long m;
   const unsigned long long *lv;   // lm[L]
   const unsigned long long *lw;   // lm[L+1]
-  double *q;                      // [n][64]
+  double *q;                      // [n][64] child sums (FP64 counts: the q values too)
+  const float2 *qds;              // [n][64] q values as double-single (uint64 counts)
 };
+
+// Double-single numbers: an unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits (Dekker's extended
+// precision arithmetic; Knuth's TwoSum for exact sums, the product's error
+// from one FMA). FP32 instructions issue many times faster than FP64 on this
+// GPU, and the conversions between float and double share the FP64 pipe, so
+// BC's per-edge and per-lane arithmetic runs in this form (uint64 path
+// counts keep every value within FP32's exponent range). The _rn intrinsics
+// keep the compiler from contracting or reassociating the error terms.
+struct DS {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DS ds_two_sum(float a, float b) {  // exact: hi + lo = a + b
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+
+__device__ __forceinline__ DS ds_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DS ds_add(DS a, DS b) {
+  DS s = ds_two_sum(a.hi, b.hi);
+  const DS t = ds_two_sum(a.lo, b.lo);
+  s = ds_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return ds_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ DS ds_add_f(DS a, float b) {
+  const DS s = ds_two_sum(a.hi, b);
+  return ds_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ DS ds_mul(DS a, DS b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);  // the product's rounding error, exactly
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return ds_fast_two_sum(p, e);
+}
+
+// 1 / a: the FP32 reciprocal refined by one Newton step in double-single,
+// r + r (1 - a r), which squares its relative error (2^-24 -> about 2^-48).
+__device__ __forceinline__ DS ds_rcp(DS a) {
+  const float r = __frcp_rn(a.hi);
+  const DS ar = ds_mul(a, DS{r, 0.f});
+  const DS res = ds_add(DS{1.f, 0.f}, DS{-ar.hi, -ar.lo});
+  return ds_add_f(ds_mul(DS{r, 0.f}, res), r);
+}
+
+// A 16-bit integer as a float without a conversion instruction: 2^23 + p
+// is a float whose low mantissa bits are p.
+__device__ __forceinline__ float u16_to_float(uint32_t p) {
+  return __fsub_rn(__int_as_float(0x4B000000 | (int)p), 8388608.f);
+}
+
+// A uint64 path count as double-single (its four 16-bit pieces, each exact
+// as a float, summed without losing more than the last of 64 bits' worth).
+__device__ __forceinline__ DS ds_from_u64(unsigned long long c) {
+  DS r{__fmul_rn(u16_to_float((uint32_t)(c >> 48)), 281474976710656.f), 0.f};  // 2^48
+  r = ds_add_f(r, __fmul_rn(u16_to_float((uint32_t)(c >> 32) & 0xFFFFu), 4294967296.f));
+  r = ds_add_f(r, __fmul_rn(u16_to_float((uint32_t)(c >> 16) & 0xFFFFu), 65536.f));
+  return ds_add_f(r, u16_to_float((uint32_t)c & 0xFFFFu));
+}
+
+__device__ __forceinline__ DS ds_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+
+__device__ __forceinline__ double ds_to_double(DS a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ DS shfl_xor_ds(DS a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
 
 // Backward level L: q[v][s] += q[w][s] over edges (v, w) with v in lane s's
 // level L and w in its level L+1 (w's q is final: level L+1 was finished).
 // Only the vertices of level L (listed with their degrees by k_mb_list) are
 // visited, so the whole backward pass reads every edge about once instead of
 // once per level.
-__global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const int32_t *Q,
+// Adds an owner run's sums (lanes `lane` and `lane` + 32) to the owner's
+// child sums.
+template <bool DSQ>
+__device__ __forceinline__ void bc_flush_owner(double *qv, unsigned long long orbits, int lane,
+                                               double acc0, double acc1, DS dacc0, DS dacc1) {
+  if (DSQ) {
+    if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, ds_to_double(dacc0));
+    if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, ds_to_double(dacc1));
+  } else {
+    if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
+    if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
+  }
+}
+
+// DSQ: the q values are read as double-single (uint64 path counts) and the
+// per-owner sums accumulated that way, one FP64 atomic per owner run and lane.
+template <bool DSQ>
+__global__ void __launch_bounds__(kMbThreads, 4) k_bc_backward(BcBackArgs a, const int32_t *Q,
                                                              const int32_t *S,
                                                              const unsigned long long *fpacked) {
   __shared__ int32_t s_off[kMbChunk + 1];
@@ -834,6 +930,7 @@ __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const 
       int32_t cur_owner = -1;
       unsigned long long orbits = 0ull;
       double acc0 = 0.0, acc1 = 0.0;
+      DS dacc0{0.f, 0.f}, dacc1{0.f, 0.f};
       while (act) {
         const int j = __ffs(act) - 1;
         act &= act - 1u;
@@ -841,26 +938,35 @@ __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const 
         const int32_t wj = __shfl_sync(0xffffffffu, w, j);
         const unsigned long long bj = shfl_u64(bits, j);
         if (ov != cur_owner) {
-          if (cur_owner >= 0) {
-            double *qv = a.q + (int64_t)cur_owner * 64;
-            if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
-            if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
-          }
+          if (cur_owner >= 0)
+            bc_flush_owner<DSQ>(a.q + (int64_t)cur_owner * 64, orbits, lane, acc0, acc1, dacc0,
+                                dacc1);
           cur_owner = ov;
           orbits = 0ull;
           acc0 = acc1 = 0.0;
+          dacc0 = dacc1 = DS{0.f, 0.f};
         }
         orbits |= bj;
-        const double *qw = a.q + (int64_t)wj * 64;
-        // a half with no bits set costs the warp no FP64 add
-        if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 += qw[lane];
-        if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) acc1 += qw[lane + 32];
+        // a half with no bits set costs the warp no add
+        if (DSQ) {
+          const float2 *qw = a.qds + (int64_t)wj * 64;
+          if ((uint32_t)bj && ((bj >> lane) & 1ull)) {
+            const float2 x = qw[lane];
+            dacc0 = ds_add(dacc0, DS{x.x, x.y});
+          }
+          if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) {
+            const float2 x = qw[lane + 32];
+            dacc1 = ds_add(dacc1, DS{x.x, x.y});
+          }
+        } else {
+          const double *qw = a.q + (int64_t)wj * 64;
+          if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 += qw[lane];
+          if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) acc1 += qw[lane + 32];
+        }
       }
-      if (cur_owner >= 0) {
-        double *qv = a.q + (int64_t)cur_owner * 64;
-        if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
-        if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
-      }
+      if (cur_owner >= 0)
+        bc_flush_owner<DSQ>(a.q + (int64_t)cur_owner * 64, orbits, lane, acc0, acc1, dacc0,
+                            dacc1);
     }
     __syncthreads();
   }
@@ -903,7 +1009,8 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long
 template <int SK>
 __global__ void k_bc_finalize(const unsigned long long *lv, const int32_t *Q,
                               const unsigned long long *fpacked, const void *sigma_p,
-                              double *q, double *bc, int32_t n, int32_t *overflow) {
+                              double *q, float2 *qds, double *bc, int32_t n,
+                              int32_t *overflow) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -915,6 +1022,27 @@ __global__ void k_bc_finalize(const unsigned long long *lv, const int32_t *Q,
     const int64_t v = v0;
     const unsigned long long A = lv[v];
     if (!A) continue;
+    if (SK == kSigU64) {
+      // double-single: delta = sigma * (child sum), q = 1/sigma + child sum
+      DS part{0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int s = lane + 32 * h;
+        if ((uint32_t)(A >> (32 * h)) == 0u) continue;  // warp-uniform
+        if ((A >> s) & 1ull) {
+          const DS child = ds_from_double(q[v * 64 + s]);
+          const unsigned long long c = (unsigned long long)sigma[v * 64 + s];
+          if (c == 0ull) *overflow = 1;  // a reached lane has at least one path
+          const DS sg = ds_from_u64(c);
+          part = ds_add(part, ds_mul(sg, child));
+          const DS qv = ds_add(ds_rcp(sg), child);
+          qds[v * 64 + s] = make_float2(qv.hi, qv.lo);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) part = ds_add(part, shfl_xor_ds(part, o));
+      if (lane == 0) bc[v] += ds_to_double(part);
+      continue;
+    }
     double part = 0.0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -986,6 +1114,7 @@ static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_b
   if (need_bc && !ws->sigma.p) {
     GR_TRY(ws->sigma.alloc(sizeof(double) * 64 * (size_t)g->n, "BC path counts"));
     GR_TRY(ws->q.alloc(sizeof(double) * 64 * (size_t)g->n, "BC dependencies"));
+    GR_TRY(ws->qds.alloc(sizeof(float2) * 64 * (size_t)g->n, "BC dependencies (double-single)"));
   }
   if (need_bc && !ws->fq.p) {
     GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "BC level list"));
@@ -1211,6 +1340,7 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     ba.n = g->n;
     ba.m = g->m;
     ba.q = ws->q.as<double>();
+    ba.qds = ws->qds.as<float2>();
     unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
     int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
     for (int32_t L = levels - 1; L >= 1; --L) {
@@ -1220,16 +1350,17 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
       k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
       if (L + 1 < levels) {
         ba.lw = ws->lm[L + 1]->as<unsigned long long>();
-        k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
+        if (sk == kSigU64) k_bc_backward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
+        else k_bc_backward<false><<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
       }
       if (sk == kSigU64)
         k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
-                                                    ws->q.as<double>(), (double *)d_bc, g->n,
-                                                    overflow);
+                                                    ws->q.as<double>(), ws->qds.as<float2>(),
+                                                    (double *)d_bc, g->n, overflow);
       else
         k_bc_finalize<kSigF64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
-                                                    ws->q.as<double>(), (double *)d_bc, g->n,
-                                                    overflow);
+                                                    ws->q.as<double>(), nullptr, (double *)d_bc,
+                                                    g->n, overflow);
       GR_CUDA(cudaGetLastError());
     }
   }
