@@ -68,7 +68,7 @@ enum : int { kSigNone = 0, kSigU64 = 1, kSigF64 = 2 };
 
 
 struct BatchWorkspace {
-  DevMem visit, sigma, q, qds, counter, lmp, ctl;
+  DevMem visit, sigma, q, counter, lmp, ctl;
   DevMem fq, fs;    // BC backward: one level's vertex list and degree scan
   DevMem lq[3], ls[3];  // forward: level lists (ring by level) and degree scans
   std::vector<DevMem *> lm;  // level mask arrays ("slots")
@@ -770,18 +770,20 @@ struct BcBackArgs {
   long long m;
   const unsigned long long *lv;   // lm[L]
   const unsigned long long *lw;   // lm[L+1]
-  double *q;                      // [n][64] child sums (FP64 counts: the q values too)
-  const float2 *qds;              // [n][64] q values as double-single (uint64 counts)
+  double *q;                      // [n][64]
 };
 
 // Double-single numbers: an unevaluated sum hi + lo of two floats with
 // |lo| <= ulp(hi) / 2, about 48 significant bits (Dekker's extended
 // precision arithmetic; Knuth's TwoSum for exact sums, the product's error
 // from one FMA). FP32 instructions issue many times faster than FP64 on this
-// GPU, and the conversions between float and double share the FP64 pipe, so
-// BC's per-edge and per-lane arithmetic runs in this form (uint64 path
-// counts keep every value within FP32's exponent range). The _rn intrinsics
-// keep the compiler from contracting or reassociating the error terms.
+// GPU, so BC's per-vertex finish (a reciprocal, a product and sums per lane)
+// runs in this form (uint64 path counts keep every value within FP32's
+// exponent range): on R-MAT s23 x 64 sources it took the finalize from
+// 16.2 to 10.8 ms. The backward's per-edge sums stay in FP64: in this form
+// its warp-serial loop became issue-bound (75.7 against 53.5 ms). The _rn
+// intrinsics keep the compiler from contracting or reassociating the error
+// terms.
 struct DS {
   float hi, lo;
 };
@@ -857,24 +859,7 @@ __device__ __forceinline__ DS shfl_xor_ds(DS a, int o) {
 // Only the vertices of level L (listed with their degrees by k_mb_list) are
 // visited, so the whole backward pass reads every edge about once instead of
 // once per level.
-// Adds an owner run's sums (lanes `lane` and `lane` + 32) to the owner's
-// child sums.
-template <bool DSQ>
-__device__ __forceinline__ void bc_flush_owner(double *qv, unsigned long long orbits, int lane,
-                                               double acc0, double acc1, DS dacc0, DS dacc1) {
-  if (DSQ) {
-    if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, ds_to_double(dacc0));
-    if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, ds_to_double(dacc1));
-  } else {
-    if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
-    if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
-  }
-}
-
-// DSQ: the q values are read as double-single (uint64 path counts) and the
-// per-owner sums accumulated that way, one FP64 atomic per owner run and lane.
-template <bool DSQ>
-__global__ void __launch_bounds__(kMbThreads, 4) k_bc_backward(BcBackArgs a, const int32_t *Q,
+__global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const int32_t *Q,
                                                              const int32_t *S,
                                                              const unsigned long long *fpacked) {
   __shared__ int32_t s_off[kMbChunk + 1];
@@ -930,7 +915,6 @@ __global__ void __launch_bounds__(kMbThreads, 4) k_bc_backward(BcBackArgs a, con
       int32_t cur_owner = -1;
       unsigned long long orbits = 0ull;
       double acc0 = 0.0, acc1 = 0.0;
-      DS dacc0{0.f, 0.f}, dacc1{0.f, 0.f};
       while (act) {
         const int j = __ffs(act) - 1;
         act &= act - 1u;
@@ -938,35 +922,26 @@ __global__ void __launch_bounds__(kMbThreads, 4) k_bc_backward(BcBackArgs a, con
         const int32_t wj = __shfl_sync(0xffffffffu, w, j);
         const unsigned long long bj = shfl_u64(bits, j);
         if (ov != cur_owner) {
-          if (cur_owner >= 0)
-            bc_flush_owner<DSQ>(a.q + (int64_t)cur_owner * 64, orbits, lane, acc0, acc1, dacc0,
-                                dacc1);
+          if (cur_owner >= 0) {
+            double *qv = a.q + (int64_t)cur_owner * 64;
+            if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
+            if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
+          }
           cur_owner = ov;
           orbits = 0ull;
           acc0 = acc1 = 0.0;
-          dacc0 = dacc1 = DS{0.f, 0.f};
         }
         orbits |= bj;
-        // a half with no bits set costs the warp no add
-        if (DSQ) {
-          const float2 *qw = a.qds + (int64_t)wj * 64;
-          if ((uint32_t)bj && ((bj >> lane) & 1ull)) {
-            const float2 x = qw[lane];
-            dacc0 = ds_add(dacc0, DS{x.x, x.y});
-          }
-          if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) {
-            const float2 x = qw[lane + 32];
-            dacc1 = ds_add(dacc1, DS{x.x, x.y});
-          }
-        } else {
-          const double *qw = a.q + (int64_t)wj * 64;
-          if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 += qw[lane];
-          if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) acc1 += qw[lane + 32];
-        }
+        const double *qw = a.q + (int64_t)wj * 64;
+        // a half with no bits set costs the warp no FP64 add
+        if ((uint32_t)bj && ((bj >> lane) & 1ull)) acc0 += qw[lane];
+        if ((bj >> 32) && ((bj >> (lane + 32)) & 1ull)) acc1 += qw[lane + 32];
       }
-      if (cur_owner >= 0)
-        bc_flush_owner<DSQ>(a.q + (int64_t)cur_owner * 64, orbits, lane, acc0, acc1, dacc0,
-                            dacc1);
+      if (cur_owner >= 0) {
+        double *qv = a.q + (int64_t)cur_owner * 64;
+        if ((orbits >> lane) & 1ull) atomicAdd(qv + lane, acc0);
+        if ((orbits >> (lane + 32)) & 1ull) atomicAdd(qv + lane + 32, acc1);
+      }
     }
     __syncthreads();
   }
@@ -1009,8 +984,7 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_list(const unsigned long long
 template <int SK>
 __global__ void k_bc_finalize(const unsigned long long *lv, const int32_t *Q,
                               const unsigned long long *fpacked, const void *sigma_p,
-                              double *q, float2 *qds, double *bc, int32_t n,
-                              int32_t *overflow) {
+                              double *q, double *bc, int32_t n, int32_t *overflow) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -1035,8 +1009,7 @@ __global__ void k_bc_finalize(const unsigned long long *lv, const int32_t *Q,
           if (c == 0ull) *overflow = 1;  // a reached lane has at least one path
           const DS sg = ds_from_u64(c);
           part = ds_add(part, ds_mul(sg, child));
-          const DS qv = ds_add(ds_rcp(sg), child);
-          qds[v * 64 + s] = make_float2(qv.hi, qv.lo);
+          q[v * 64 + s] = ds_to_double(ds_add(ds_rcp(sg), child));
         }
       }
       for (int o = 16; o > 0; o >>= 1) part = ds_add(part, shfl_xor_ds(part, o));
@@ -1114,7 +1087,6 @@ static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_b
   if (need_bc && !ws->sigma.p) {
     GR_TRY(ws->sigma.alloc(sizeof(double) * 64 * (size_t)g->n, "BC path counts"));
     GR_TRY(ws->q.alloc(sizeof(double) * 64 * (size_t)g->n, "BC dependencies"));
-    GR_TRY(ws->qds.alloc(sizeof(float2) * 64 * (size_t)g->n, "BC dependencies (double-single)"));
   }
   if (need_bc && !ws->fq.p) {
     GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "BC level list"));
@@ -1340,7 +1312,6 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     ba.n = g->n;
     ba.m = g->m;
     ba.q = ws->q.as<double>();
-    ba.qds = ws->qds.as<float2>();
     unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
     int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
     for (int32_t L = levels - 1; L >= 1; --L) {
@@ -1350,17 +1321,16 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
       k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
       if (L + 1 < levels) {
         ba.lw = ws->lm[L + 1]->as<unsigned long long>();
-        if (sk == kSigU64) k_bc_backward<true><<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
-        else k_bc_backward<false><<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
+        k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
       }
       if (sk == kSigU64)
         k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
-                                                    ws->q.as<double>(), ws->qds.as<float2>(),
-                                                    (double *)d_bc, g->n, overflow);
+                                                    ws->q.as<double>(), (double *)d_bc, g->n,
+                                                    overflow);
       else
         k_bc_finalize<kSigF64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
-                                                    ws->q.as<double>(), nullptr, (double *)d_bc,
-                                                    g->n, overflow);
+                                                    ws->q.as<double>(), (double *)d_bc, g->n,
+                                                    overflow);
       GR_CUDA(cudaGetLastError());
     }
   }
