@@ -210,9 +210,13 @@ struct ReduceMaxI32 {
   static __device__ __forceinline__ void atomic(int32_t *p, int32_t v) { atomicMax(p, v); }
 };
 
+// cb (vertex ranges only; may be null): the chunk bounds precomputed by
+// k_chunk_bounds for this range and chunk size, cb[c] = the members whose
+// end marker lies before chunk c, so a chunk needs no search.
 template <int THREADS, int ITEMS, class T, class OP, bool FRONTIER, class G>
 __device__ void lb_gather_reduce(const int32_t *R, const int32_t *C, const int32_t *Q,
-                                 const int32_t *S, int32_t q, int32_t v0, G &g, T *acc) {
+                                 const int32_t *S, int32_t q, int32_t v0, G &g, T *acc,
+                                 const int32_t *cb = nullptr) {
   constexpr int CHUNK = THREADS * ITEMS;
   // diagonals are absolute: d + S[0] (the path starts at S[0], the first
   // entry's CSR position for a range, 0 for a frontier)
@@ -230,7 +234,12 @@ __device__ void lb_gather_reduce(const int32_t *R, const int32_t *C, const int32
     const long long d0 = chunk * CHUNK + s0;
     const long long d1 = min(chunk * CHUNK + CHUNK, total) + s0;
     int32_t i0, i1;
-    block_chunk_bounds<THREADS>(S, q, S[q], d0, d1, CHUNK, s_red8, &i0, &i1);
+    if (!FRONTIER && cb) {
+      i0 = cb[chunk];
+      i1 = cb[chunk + 1];
+    } else {
+      block_chunk_bounds<THREADS>(S, q, S[q], d0, d1, CHUNK, s_red8, &i0, &i1);
+    }
     const long long j0 = d0 - i0, j1 = d1 - i1;  // entries [j0, j1) (scan positions)
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     const int32_t ne = (int32_t)(j1 - j0);
@@ -314,8 +323,37 @@ __device__ void lb_gather_reduce(const int32_t *R, const int32_t *C, const int32
 // All vertices, summed (PageRank's gather): acc[v] += sum of g over v's row.
 template <int THREADS, int ITEMS, class T, class G>
 __device__ __forceinline__ void lb_neighbor_reduce(const int32_t *R, const int32_t *C, int32_t n,
-                                                   G &g, T *acc) {
-  lb_gather_reduce<THREADS, ITEMS, T, ReduceSum<T>, false>(R, C, nullptr, R, n, 0, g, acc);
+                                                   G &g, T *acc, const int32_t *cb = nullptr) {
+  lb_gather_reduce<THREADS, ITEMS, T, ReduceSum<T>, false>(R, C, nullptr, R, n, 0, g, acc, cb);
+}
+
+// Chunk bounds of the merge path over a vertex range (S = R + v0, q
+// members, entries S[0] .. S[q]) in chunks of `chunk` items:
+// cb[c] = the number of members whose end marker S[i+1] + i lies before
+// c * chunk + S[0] (the path's absolute diagonal), c in [0, chunks), and
+// cb[chunks] = q. One thread per chunk, a binary search each.
+static __global__ void k_chunk_bounds(const int32_t *S, int32_t q, int32_t chunk,
+                                      int32_t chunks, int32_t *cb) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c > chunks) return;
+  if (c == chunks) {
+    cb[c] = q;
+    return;
+  }
+  const long long d = c * (long long)chunk + S[0];
+  int32_t lo = 0, hi = q;  // first member whose end marker is not before d
+  while (lo < hi) {
+    const int32_t mid = (int32_t)(((long long)lo + hi) >> 1);
+    if ((long long)S[mid + 1] + mid < d) lo = mid + 1;
+    else hi = mid;
+  }
+  cb[c] = lo;
+}
+
+// Chunks of the merge path over q members whose entries span S[0] .. S[q].
+__host__ __device__ __forceinline__ int32_t merge_chunks(int32_t q, long long entries,
+                                                         int32_t chunk) {
+  return (int32_t)(((long long)q + entries + chunk - 1) / chunk);
 }
 
 }  // namespace gr

@@ -69,6 +69,7 @@ enum : int { kSigNone = 0, kSigU64 = 1, kSigF64 = 2 };
 
 struct BatchWorkspace {
   DevMem visit, sigma, q, counter, lmp, ctl;
+  DevMem cb_pull, cb_fwd;  // chunk bounds of the all-vertex pulls (fixed per graph)
   DevMem fq, fs;    // BC backward: one level's vertex list and degree scan
   DevMem lq[3], ls[3];  // forward: level lists (ring by level) and degree scans
   std::vector<DevMem *> lm;  // level mask arrays ("slots")
@@ -121,6 +122,10 @@ struct MbArgs {
   int32_t symmetric;
   int32_t max_levels;
   MbCtl *ctl;
+  // chunk bounds of the all-vertex merge paths of the pull levels (chunks of
+  // kMbPullChunk items for the batched BFS, kMbChunk for BC)
+  const int32_t *cb_pull;
+  const int32_t *cb_fwd;
 };
 
 __device__ __forceinline__ int32_t mb_slot(const MbArgs &a, int32_t L) {
@@ -300,8 +305,7 @@ __device__ void mb_pull_level(const MbArgs &a, MbSmem &sm, int32_t *s_red8, int3
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * CHUNK;
     const long long d1 = min(d0 + CHUNK, total);
-    int32_t i0, i1;
-    block_chunk_bounds<kMbThreads>(a.R, a.n, a.R[a.n], d0, d1, CHUNK, s_red8, &i0, &i1);
+    const int32_t i0 = a.cb_pull[chunk], i1 = a.cb_pull[chunk + 1];
     const long long j0 = d0 - i0;  // CSR position of the chunk's first edge
     const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
     const int32_t len = (int32_t)(d1 - d0);
@@ -403,8 +407,7 @@ __device__ void mb_forward_level(const MbArgs &a, MbSmem &sm, int32_t *s_red8,
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kMbChunk;
     const long long d1 = min(d0 + kMbChunk, total);
-    int32_t i0, i1;
-    block_chunk_bounds<kMbThreads>(a.R, a.n, a.R[a.n], d0, d1, kMbChunk, s_red8, &i0, &i1);
+    const int32_t i0 = a.cb_fwd[chunk], i1 = a.cb_fwd[chunk + 1];
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
     for (int32_t kk = threadIdx.x; kk < nv; kk += kMbThreads) {
@@ -1073,6 +1076,19 @@ gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out) {
   GR_TRY(ws->visit.alloc(sizeof(unsigned long long) * (size_t)g->n, "lane visit masks"));
   GR_TRY(ws->counter.alloc(sizeof(unsigned long long) * 4, "batch counters"));
   GR_TRY(ws->ctl.alloc(sizeof(MbCtl), "batch control"));
+  {
+    // the pull levels' merge paths over all vertices are the same on every
+    // level: their chunk bounds are found once
+    const int32_t *R = g->row_off.as<int32_t>();
+    const int32_t cp = merge_chunks(g->n, g->m, kMbPullChunk);
+    const int32_t cf = merge_chunks(g->n, g->m, kMbChunk);
+    GR_TRY(ws->cb_pull.alloc(sizeof(int32_t) * ((size_t)cp + 1), "batch pull chunk bounds"));
+    GR_TRY(ws->cb_fwd.alloc(sizeof(int32_t) * ((size_t)cf + 1), "BC pull chunk bounds"));
+    k_chunk_bounds<<<(cp + 256) / 256, 256>>>(R, g->n, kMbPullChunk, cp, ws->cb_pull.as<int32_t>());
+    k_chunk_bounds<<<(cf + 256) / 256, 256>>>(R, g->n, kMbChunk, cf, ws->cb_fwd.as<int32_t>());
+    GR_CUDA(cudaGetLastError());
+    GR_CUDA(cudaStreamSynchronize(0));
+  }
   for (int i = 0; i < 3; ++i) {
     GR_TRY(ws->lq[i].alloc(sizeof(int32_t) * ((size_t)g->n + 1), "batch level list"));
     GR_TRY(ws->ls[i].alloc(sizeof(int32_t) * ((size_t)g->n + 2), "batch level list scan"));
@@ -1148,6 +1164,8 @@ static MbArgs mb_args(gr_graph *g, BatchWorkspace *ws, int32_t k, int32_t *depth
   a.symmetric = g->symmetric ? 1 : 0;
   a.max_levels = max_levels;
   a.ctl = ws->ctl.as<MbCtl>();
+  a.cb_pull = ws->cb_pull.as<int32_t>();
+  a.cb_fwd = ws->cb_fwd.as<int32_t>();
   return a;
 }
 

@@ -41,6 +41,7 @@ struct PrCtl {
 
 struct PrWorkspace {
   DevMem contrib, sum, ctl;
+  DevMem cb;  // chunk bounds of the gather's merge path (fixed per graph)
   DevMem tr_off, tr_col;  // transpose (directed graphs only)
   bool has_transpose = false;
   cudaGraphExec_t exec = nullptr;
@@ -65,6 +66,7 @@ struct PrArgs {
   float *contrib;
   float *sum;
   PrCtl *ctl;
+  const int32_t *cb;  // chunk bounds of the gather
 };
 
 __global__ void k_pr_init(PrArgs a, float *rank, float damping, int32_t max_iter, double tol,
@@ -99,7 +101,7 @@ struct ContribG {
 __global__ void __launch_bounds__(kPrThreads) k_pr_gather(PrArgs a) {
   if (a.ctl->done) return;
   ContribG g{a.contrib};
-  lb_neighbor_reduce<kPrThreads, kPrItems, float>(a.R, a.C, a.n, g, a.sum);
+  lb_neighbor_reduce<kPrThreads, kPrItems, float>(a.R, a.C, a.n, g, a.sum, a.cb);
 }
 
 __global__ void __launch_bounds__(256) k_pr_update(PrArgs a) {
@@ -210,6 +212,16 @@ static gr_status ensure_pr_ws(gr_graph *g, cudaStream_t s) {
     GR_CUDA(cudaStreamSynchronize(s));
     ws->has_transpose = true;
   }
+  if (!ws->cb.p) {
+    // the gather's merge path over all vertices is the same every
+    // iteration: its chunk bounds are found once
+    const int32_t *R = g->symmetric ? g->row_off.as<int32_t>() : ws->tr_off.as<int32_t>();
+    const int32_t chunks = merge_chunks(g->n, g->m, kPrThreads * kPrItems);
+    GR_TRY(ws->cb.alloc(sizeof(int32_t) * ((size_t)chunks + 1), "PageRank chunk bounds"));
+    k_chunk_bounds<<<(chunks + 256) / 256, 256, 0, s>>>(R, g->n, kPrThreads * kPrItems, chunks,
+                                                         ws->cb.as<int32_t>());
+    GR_CUDA(cudaGetLastError());
+  }
   return GR_OK;
 }
 
@@ -223,6 +235,7 @@ static PrArgs pr_args(gr_graph *g) {
   a.contrib = ws->contrib.as<float>();
   a.sum = ws->sum.as<float>();
   a.ctl = ws->ctl.as<PrCtl>();
+  a.cb = ws->cb.as<int32_t>();
   return a;
 }
 

@@ -46,6 +46,10 @@ struct RankWorkspace {
   DevMem cur, tmp, dv, tele, ctl, seeds;
   DevMem fscan, part;   // gr_neighbor_reduce: a frontier's degree scan, block partials
   int32_t bip_left = -1;  // n_left the graph was last checked to be bipartite for
+  // chunk bounds of the gather's merge paths: all vertices (fixed per
+  // graph), and the hub and authority ranges of the last n_left
+  DevMem cb_all, cb_hub, cb_auth;
+  int32_t cb_left = -1;
 };
 
 void free_rank(RankWorkspace *ws) { delete ws; }
@@ -140,8 +144,9 @@ __global__ void k_scan_apply(const int32_t *R, const int32_t *Q, int32_t q, cons
 template <class T, class OP, bool FRONTIER, class G>
 __global__ void __launch_bounds__(kRkThreads) k_nr_gather(const int32_t *R, const int32_t *C,
                                                            const int32_t *Q, const int32_t *S,
-                                                           int32_t q, G g, T *out) {
-  lb_gather_reduce<kRkThreads, kRkItems, T, OP, FRONTIER>(R, C, Q, S, q, 0, g, out);
+                                                           int32_t q, G g, T *out,
+                                                           const int32_t *cb) {
+  lb_gather_reduce<kRkThreads, kRkItems, T, OP, FRONTIER>(R, C, Q, S, q, 0, g, out, cb);
 }
 
 // ------------------------------------------------------ ranking kernels
@@ -158,6 +163,7 @@ struct RankArgs {
   double tol;
   int32_t max_iter;
   RankCtl *ctl;
+  const int32_t *cb_all, *cb_hub, *cb_auth;  // chunk bounds of the gathers' ranges
 };
 
 // Block-wide FP64 sum, added to *dst by thread 0.
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kRkThreads, kRkBlocksPerSm) k_bipartite_do(Ran
     {
       GatherF64 gf{KIND == 0 ? a.cur : a.dv};
       lb_gather_reduce<kRkThreads, kRkItems, double, ReduceSum<double>, false>(
-          a.R, a.C, nullptr, a.R + nl, n - nl, nl, gf, a.tmp);
+          a.R, a.C, nullptr, a.R + nl, n - nl, nl, gf, a.tmp, a.cb_auth);
     }
     if (!grid_sync(&c->bar, &c->error, gen)) return;
     if (blockIdx.x == 0 && threadIdx.x < 4) c->red[(it + 1) & 1][threadIdx.x] = 0.0;
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kRkThreads, kRkBlocksPerSm) k_bipartite_do(Ran
     {
       GatherF64 gf{KIND == 0 ? a.cur : a.dv};
       lb_gather_reduce<kRkThreads, kRkItems, double, ReduceSum<double>, false>(
-          a.R, a.C, nullptr, a.R, nl, 0, gf, a.tmp);
+          a.R, a.C, nullptr, a.R, nl, 0, gf, a.tmp, a.cb_hub);
     }
     if (!grid_sync(&c->bar, &c->error, gen)) return;
     inv = 1.0;
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kRkThreads, kRkBlocksPerSm) k_ppr_do(RankArgs 
     {
       GatherF64 gf{a.dv};
       lb_gather_reduce<kRkThreads, kRkItems, double, ReduceSum<double>, false>(
-          a.R, a.C, nullptr, a.R, a.n, 0, gf, a.tmp);
+          a.R, a.C, nullptr, a.R, a.n, 0, gf, a.tmp, a.cb_all);
     }
     if (!grid_sync(&c->bar, &c->error, gen)) return;
     if (blockIdx.x == 0 && threadIdx.x < 4) c->red[(it + 1) & 1][threadIdx.x] = 0.0;
@@ -374,6 +380,29 @@ static gr_status rank_ws(gr_graph *g, RankWorkspace **out) {
   return GR_OK;
 }
 
+// Chunk bounds of the gather's merge path over the vertex range [v0, v1)
+// into buf (one search per chunk, on `s`).
+static gr_status range_bounds(gr_graph *g, int32_t v0, int32_t v1, DevMem &buf, cudaStream_t s) {
+  const int32_t *R = g->row_off.as<int32_t>();
+  int32_t r[2] = {0, 0};
+  // the range's entry count: two offsets, read once per call
+  GR_CUDA(cudaMemcpyAsync(&r[0], R + v0, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GR_CUDA(cudaMemcpyAsync(&r[1], R + v1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GR_CUDA(cudaStreamSynchronize(s));
+  const int32_t chunks = merge_chunks(v1 - v0, (long long)r[1] - r[0], kRkThreads * kRkItems);
+  if (buf.bytes < sizeof(int32_t) * ((size_t)chunks + 1))
+    GR_TRY(buf.alloc(sizeof(int32_t) * ((size_t)chunks + 1), "gather chunk bounds"));
+  k_chunk_bounds<<<(chunks + 256) / 256, 256, 0, s>>>(R + v0, v1 - v0, kRkThreads * kRkItems,
+                                                       chunks, buf.as<int32_t>());
+  GR_CUDA(cudaGetLastError());
+  return GR_OK;
+}
+
+static gr_status all_bounds(gr_graph *g, RankWorkspace *ws, cudaStream_t s) {
+  if (!ws->cb_all.p) GR_TRY(range_bounds(g, 0, g->n, ws->cb_all, s));
+  return GR_OK;
+}
+
 static gr_status rank_launch(gr_graph *g, void *kern, RankArgs &a, cudaStream_t s) {
   int per_sm = 0;
   GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRkThreads, 0));
@@ -428,12 +457,19 @@ static gr_status bipartite_run(gr_graph *g, int kind, int32_t n_left, int32_t ma
   }
   bool host = false;
   GR_TRY(output_on_host(g, score, &host));
+  if (ws->cb_left != n_left) {
+    GR_TRY(range_bounds(g, 0, n_left, ws->cb_hub, s));
+    GR_TRY(range_bounds(g, n_left, g->n, ws->cb_auth, s));
+    ws->cb_left = n_left;
+  }
   RankArgs a;
   std::memset(&a, 0, sizeof(a));
   a.R = g->row_off.as<int32_t>();
   a.C = g->col.as<int32_t>();
   a.n = g->n;
   a.n_left = n_left;
+  a.cb_hub = ws->cb_hub.as<int32_t>();
+  a.cb_auth = ws->cb_auth.as<int32_t>();
   a.cur = ws->cur.as<double>();
   a.tmp = ws->tmp.as<double>();
   a.dv = ws->dv.as<double>();
@@ -502,20 +538,26 @@ gr_status gr_neighbor_reduce(gr_graph *g, int32_t op, const int32_t *frontier, i
   }
   if (count > 0) {
     const int blocks = g->num_sms * 4;
+    const int32_t *cb = nullptr;
+    if (!frontier) {
+      if (!g->rank) g->rank = new RankWorkspace();
+      GR_TRY(all_bounds(g, g->rank, s));
+      cb = g->rank->cb_all.as<int32_t>();
+    }
     if (!frontier) {
       if (op == GR_REDUCE_SUM)
         k_nr_gather<double, ReduceSum<double>, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherF64{(const double *)x}, (double *)d_out);
+            R, C, nullptr, R, count, GatherF64{(const double *)x}, (double *)d_out, cb);
       else if (op == GR_REDUCE_WSUM)
         k_nr_gather<double, ReduceSum<double>, false><<<blocks, kRkThreads, 0, s>>>(
             R, C, nullptr, R, count, GatherWF64{(const double *)x, g->w.as<uint32_t>()},
-            (double *)d_out);
+            (double *)d_out, cb);
       else if (op == GR_REDUCE_MIN)
         k_nr_gather<int32_t, ReduceMinI32, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out);
+            R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, cb);
       else
         k_nr_gather<int32_t, ReduceMaxI32, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out);
+            R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, cb);
     } else {
       RankWorkspace *ws;
       if (!g->rank) g->rank = new RankWorkspace();
@@ -535,17 +577,17 @@ gr_status gr_neighbor_reduce(gr_graph *g, int32_t op, const int32_t *frontier, i
       k_scan_apply<<<tiles, 256, 0, s>>>(R, frontier, count, part, S);
       if (op == GR_REDUCE_SUM)
         k_nr_gather<double, ReduceSum<double>, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherF64{(const double *)x}, (double *)d_out);
+            R, C, frontier, S, count, GatherF64{(const double *)x}, (double *)d_out, nullptr);
       else if (op == GR_REDUCE_WSUM)
         k_nr_gather<double, ReduceSum<double>, true><<<blocks, kRkThreads, 0, s>>>(
             R, C, frontier, S, count, GatherWF64{(const double *)x, g->w.as<uint32_t>()},
-            (double *)d_out);
+            (double *)d_out, nullptr);
       else if (op == GR_REDUCE_MIN)
         k_nr_gather<int32_t, ReduceMinI32, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out);
+            R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, nullptr);
       else
         k_nr_gather<int32_t, ReduceMaxI32, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out);
+            R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, nullptr);
     }
     GR_CUDA(cudaGetLastError());
   }
@@ -597,6 +639,7 @@ gr_status gr_ppr(gr_graph *g, const int32_t *seeds, int32_t num_seeds, double da
                           cudaMemcpyHostToDevice, s));
   bool host = false;
   GR_TRY(output_on_host(g, rank, &host));
+  GR_TRY(all_bounds(g, ws, s));
   RankArgs a;
   std::memset(&a, 0, sizeof(a));
   a.R = g->row_off.as<int32_t>();
@@ -606,6 +649,7 @@ gr_status gr_ppr(gr_graph *g, const int32_t *seeds, int32_t num_seeds, double da
   a.tmp = ws->tmp.as<double>();
   a.dv = ws->dv.as<double>();
   a.tele = ws->tele.as<double>();
+  a.cb_all = ws->cb_all.as<int32_t>();
   a.damping = damping;
   a.tol = tol;
   a.max_iter = max_iter;
