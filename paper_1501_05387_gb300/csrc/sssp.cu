@@ -108,6 +108,7 @@ struct SsspArgs {
   int32_t *far_stamp;
   SsspCtl *ctl;
   int32_t low_degree;  // graph of small maximum degree: per-thread relaxation
+  const int32_t *cb;   // chunk bounds of the pull relaxation's all-vertex merge path
 };
 
 constexpr int kSsspThreads = 256, kSsspItems = 4;
@@ -123,6 +124,7 @@ constexpr int32_t kSsspMaxLanes = 64;
 struct SsspWorkspace {
   int32_t lanes = 1;  // copies of the graph the buffers hold (batched form)
   DevMem nearq[2], nearS[2], farq[2], stamp, far_stamp, ctl;
+  DevMem cb;  // chunk bounds of the pull relaxation (single search; fixed per graph)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   ~SsspWorkspace() {
@@ -496,8 +498,7 @@ __device__ void pull_relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm,
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * CHUNK;
     const long long d1 = min(d0 + CHUNK, total);
-    int32_t i0, i1;
-    block_chunk_bounds<kSsspThreads>(a.R, a.n, (int32_t)a.m, d0, d1, CHUNK, sm.sred, &i0, &i1);
+    const int32_t i0 = a.cb[chunk], i1 = a.cb[chunk + 1];
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= a.n - 1) ? (min(i1, a.n - 1) - i0 + 1) : 0;
     const int32_t ne = (int32_t)(j1 - j0);
@@ -948,6 +949,14 @@ gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out, int32
   GR_TRY(ws->stamp.alloc(sizeof(int32_t) * n, "SSSP near stamps"));
   GR_TRY(ws->far_stamp.alloc(sizeof(int32_t) * n, "SSSP far stamps"));
   GR_TRY(ws->ctl.alloc(sizeof(SsspCtl), "SSSP control"));
+  if (lanes == 1) {
+    // the pull relaxation's merge path over all vertices never changes
+    const int32_t chunks = merge_chunks(g->n, g->m, kSsspChunk);
+    GR_TRY(ws->cb.alloc(sizeof(int32_t) * ((size_t)chunks + 1), "SSSP pull chunk bounds"));
+    k_chunk_bounds<<<(chunks + 256) / 256, 256, 0, s>>>(g->row_off.as<int32_t>(), g->n,
+                                                         kSsspChunk, chunks, ws->cb.as<int32_t>());
+    GR_CUDA(cudaGetLastError());
+  }
   GR_CUDA(cudaMemsetAsync(ws->ctl.p, 0, sizeof(SsspCtl), s));
   GR_CUDA(cudaStreamSynchronize(s));
   *out = ws.release();
@@ -971,6 +980,7 @@ static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws, int32_t lanes = 1) {
   a.far_stamp = ws->far_stamp.as<int32_t>();
   a.ctl = ws->ctl.as<SsspCtl>();
   a.low_degree = g->max_degree <= kSsspLowDegreeMax ? 1 : 0;
+  a.cb = ws->cb.as<int32_t>();  // null for batched workspaces, which never pull
   return a;
 }
 
