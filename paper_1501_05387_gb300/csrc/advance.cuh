@@ -13,6 +13,8 @@
 // than its size whatever the degree mix (zero-degree vertices included).
 #pragma once
 
+#include <algorithm>
+
 #include "gr_internal.cuh"
 
 namespace gr {
@@ -348,6 +350,28 @@ static __global__ void k_chunk_bounds(const int32_t *S, int32_t q, int32_t chunk
     else hi = mid;
   }
   cb[c] = lo;
+}
+
+// Sets kernel f's shared-memory carveout to the smallest share of the SM's
+// unified L1/shared-memory array that holds `blocks` resident blocks of it,
+// leaving the rest to the L1 cache (the gather-reduce's random reads of
+// neighbour values hit there), and reports the resident blocks per SM that
+// the occupancy calculator then allows for `threads`-thread blocks.
+template <class K>
+static gr_status fit_carveout(K f, int threads, int blocks, int device, int *per_sm) {
+  cudaFuncAttributes fa;
+  GR_CUDA(cudaFuncGetAttributes(&fa, f));
+  int max_sm = 0, reserved = 0;
+  GR_CUDA(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  GR_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+  const long long need = (long long)blocks * ((long long)fa.sharedSizeBytes + reserved);
+  const int pct = max_sm > 0 ? (int)std::min<long long>(100, (need * 100 + max_sm - 1) / max_sm)
+                             : (int)cudaSharedmemCarveoutDefault;
+  GR_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+  GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, threads, 0));
+  if (*per_sm < 1) *per_sm = 1;
+  if (*per_sm > blocks) *per_sm = blocks;
+  return GR_OK;
 }
 
 // Chunks of the merge path over q members whose entries span S[0] .. S[q].

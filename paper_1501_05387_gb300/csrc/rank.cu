@@ -31,8 +31,12 @@
 
 namespace gr {
 
-constexpr int kRkThreads = 256, kRkItems = 8;
-constexpr int kRkBlocksPerSm = 4;
+// Gather tiles of 12 items for each of 96 threads, 8 blocks per SM, the
+// rest of the SM's shared-memory array left to L1 (R-MAT s23 gather-reduce,
+// FP64 sum: 256 x 8 at 4 blocks per SM with the default carveout 3.48 ms,
+// with the fitted carveout 1.96 ms, this tile 1.57 ms).
+constexpr int kRkThreads = 96, kRkItems = 12;
+constexpr int kRkBlocksPerSm = 8;
 
 struct RankCtl {
   GridBarrier bar;
@@ -142,7 +146,7 @@ __global__ void k_scan_apply(const int32_t *R, const int32_t *Q, int32_t q, cons
 }
 
 template <class T, class OP, bool FRONTIER, class G>
-__global__ void __launch_bounds__(kRkThreads) k_nr_gather(const int32_t *R, const int32_t *C,
+__global__ void __launch_bounds__(kRkThreads, kRkBlocksPerSm) k_nr_gather(const int32_t *R, const int32_t *C,
                                                            const int32_t *Q, const int32_t *S,
                                                            int32_t q, G g, T *out,
                                                            const int32_t *cb) {
@@ -403,10 +407,24 @@ static gr_status all_bounds(gr_graph *g, RankWorkspace *ws, cudaStream_t s) {
   return GR_OK;
 }
 
+// One gather-reduce over a range or a frontier, at the tile's resident
+// blocks per SM with the rest of the shared-memory array left to L1.
+template <class T, class OP, bool FRONTIER, class G>
+static gr_status nr_launch(gr_graph *g, cudaStream_t s, const int32_t *R, const int32_t *C,
+                           const int32_t *Q, const int32_t *S, int32_t q, G gf, T *out,
+                           const int32_t *cb) {
+  auto kern = k_nr_gather<T, OP, FRONTIER, G>;
+  int per_sm = 1;
+  GR_TRY(fit_carveout(kern, kRkThreads, kRkBlocksPerSm, g->device, &per_sm));
+  kern<<<per_sm * g->num_sms, kRkThreads, 0, s>>>(R, C, Q, S, q, gf, out, cb);
+  GR_CUDA(cudaGetLastError());
+  return GR_OK;
+}
+
 static gr_status rank_launch(gr_graph *g, void *kern, RankArgs &a, cudaStream_t s) {
-  int per_sm = 0;
-  GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRkThreads, 0));
-  const int blocks = std::max(1, std::min(per_sm, kRkBlocksPerSm)) * g->num_sms;
+  int per_sm = 1;
+  GR_TRY(fit_carveout(kern, kRkThreads, kRkBlocksPerSm, g->device, &per_sm));
+  const int blocks = per_sm * g->num_sms;
   void *args[] = {&a};
   GR_CUDA(cudaLaunchCooperativeKernel(kern, blocks, kRkThreads, args, 0, s));
   return GR_OK;
@@ -537,7 +555,6 @@ gr_status gr_neighbor_reduce(gr_graph *g, int32_t op, const int32_t *frontier, i
     GR_CUDA(cudaGetLastError());
   }
   if (count > 0) {
-    const int blocks = g->num_sms * 4;
     const int32_t *cb = nullptr;
     if (!frontier) {
       if (!g->rank) g->rank = new RankWorkspace();
@@ -546,18 +563,18 @@ gr_status gr_neighbor_reduce(gr_graph *g, int32_t op, const int32_t *frontier, i
     }
     if (!frontier) {
       if (op == GR_REDUCE_SUM)
-        k_nr_gather<double, ReduceSum<double>, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherF64{(const double *)x}, (double *)d_out, cb);
+        GR_TRY((nr_launch<double, ReduceSum<double>, false>(
+            g, s, R, C, nullptr, R, count, GatherF64{(const double *)x}, (double *)d_out, cb)));
       else if (op == GR_REDUCE_WSUM)
-        k_nr_gather<double, ReduceSum<double>, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherWF64{(const double *)x, g->w.as<uint32_t>()},
-            (double *)d_out, cb);
+        GR_TRY((nr_launch<double, ReduceSum<double>, false>(
+            g, s, R, C, nullptr, R, count, GatherWF64{(const double *)x, g->w.as<uint32_t>()},
+            (double *)d_out, cb)));
       else if (op == GR_REDUCE_MIN)
-        k_nr_gather<int32_t, ReduceMinI32, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, cb);
+        GR_TRY((nr_launch<int32_t, ReduceMinI32, false>(
+            g, s, R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, cb)));
       else
-        k_nr_gather<int32_t, ReduceMaxI32, false><<<blocks, kRkThreads, 0, s>>>(
-            R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, cb);
+        GR_TRY((nr_launch<int32_t, ReduceMaxI32, false>(
+            g, s, R, C, nullptr, R, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, cb)));
     } else {
       RankWorkspace *ws;
       if (!g->rank) g->rank = new RankWorkspace();
@@ -576,20 +593,22 @@ gr_status gr_neighbor_reduce(gr_graph *g, int32_t op, const int32_t *frontier, i
       k_scan_parts<<<1, 256, 0, s>>>(part, tiles);
       k_scan_apply<<<tiles, 256, 0, s>>>(R, frontier, count, part, S);
       if (op == GR_REDUCE_SUM)
-        k_nr_gather<double, ReduceSum<double>, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherF64{(const double *)x}, (double *)d_out, nullptr);
+        GR_TRY((nr_launch<double, ReduceSum<double>, true>(
+            g, s, R, C, frontier, S, count, GatherF64{(const double *)x}, (double *)d_out,
+            nullptr)));
       else if (op == GR_REDUCE_WSUM)
-        k_nr_gather<double, ReduceSum<double>, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherWF64{(const double *)x, g->w.as<uint32_t>()},
-            (double *)d_out, nullptr);
+        GR_TRY((nr_launch<double, ReduceSum<double>, true>(
+            g, s, R, C, frontier, S, count, GatherWF64{(const double *)x, g->w.as<uint32_t>()},
+            (double *)d_out, nullptr)));
       else if (op == GR_REDUCE_MIN)
-        k_nr_gather<int32_t, ReduceMinI32, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, nullptr);
+        GR_TRY((nr_launch<int32_t, ReduceMinI32, true>(
+            g, s, R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out,
+            nullptr)));
       else
-        k_nr_gather<int32_t, ReduceMaxI32, true><<<blocks, kRkThreads, 0, s>>>(
-            R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out, nullptr);
+        GR_TRY((nr_launch<int32_t, ReduceMaxI32, true>(
+            g, s, R, C, frontier, S, count, GatherI32{(const int32_t *)x}, (int32_t *)d_out,
+            nullptr)));
     }
-    GR_CUDA(cudaGetLastError());
   }
   if (cp) GR_CUDA(cudaMemcpyAsync(out, d_out, elem * (size_t)g->n, cudaMemcpyDeviceToHost, s));
   GR_TRY(end_call(g, s));
