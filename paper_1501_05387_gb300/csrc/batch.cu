@@ -857,11 +857,16 @@ __device__ __forceinline__ DS shfl_xor_ds(DS a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
+// resident blocks per SM of the backward pass (its carveout is fitted to
+// them, the rest of the shared-memory array left to L1 for the children's rows)
+constexpr int kBcBackBlocksPerSm = 6;
+
 // Backward level L: q[v][s] += q[w][s] over edges (v, w) with v in lane s's
 // level L and w in its level L+1 (w's q is final: level L+1 was finished).
 // Only the vertices of level L (listed with their degrees by k_mb_list) are
 // visited, so the whole backward pass reads every edge about once instead of
 // once per level.
+
 __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const int32_t *Q,
                                                              const int32_t *S,
                                                              const unsigned long long *fpacked) {
@@ -1174,9 +1179,9 @@ static gr_status mb_launch(gr_graph *g, const MbArgs &a, int sk, cudaStream_t s)
                : sk == kSigF64 ? (void *)k_mb_do<kSigF64>
                                : (void *)k_mb_do<kSigNone>;
   const int want = sk == kSigNone ? mb_do_blocks_per_sm<kSigNone>() : mb_do_blocks_per_sm<kSigU64>();
-  int per_sm = 0;
-  GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMbThreads, 0));
-  const int blocks = std::max(1, std::min(per_sm, want)) * g->num_sms;
+  int per_sm = 1;
+  GR_TRY(fit_carveout(kern, kMbThreads, want, g->device, &per_sm));
+  const int blocks = per_sm * g->num_sms;
   MbArgs arg = a;
   void *args[] = {&arg};
   GR_CUDA(cudaLaunchCooperativeKernel(kern, blocks, kMbThreads, args, 0, s));
@@ -1332,6 +1337,8 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     ba.q = ws->q.as<double>();
     unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
     int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
+    int back_per_sm = 1;
+    GR_TRY(fit_carveout(k_bc_backward, kMbThreads, kBcBackBlocksPerSm, g->device, &back_per_sm));
     for (int32_t L = levels - 1; L >= 1; --L) {
       // the vertices of level L (in any lane) with their degree scan
       ba.lv = ws->lm[L]->as<unsigned long long>();
@@ -1339,7 +1346,7 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
       k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
       if (L + 1 < levels) {
         ba.lw = ws->lm[L + 1]->as<unsigned long long>();
-        k_bc_backward<<<g->num_sms * 4, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
+        k_bc_backward<<<g->num_sms * back_per_sm, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
       }
       if (sk == kSigU64)
         k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,

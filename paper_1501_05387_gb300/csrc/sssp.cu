@@ -1066,12 +1066,13 @@ gr_status sssp_check(const gr_graph *g, int32_t src, const gr_opts &o) {
 static gr_status sssp_drive(gr_graph *g, SsspWorkspace *ws, SsspArgs a, int32_t mode,
                             const gr_opts &o, int32_t max_iters, cudaStream_t s) {
   if (mode == GR_MODE_PERSISTENT) {
-    int per_sm = 0;
     void *kern = a.low_degree ? (void *)k_sssp_do<true> : (void *)k_sssp_do<false>;
-    GR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSsspThreads, 0));
-    int bps = std::min(per_sm, kSsspBlocksPerSm);
     const int32_t want = o.block > 0 ? o.block : g->tuned_sssp_blocks_per_sm;
-    if (want > 0) bps = std::min(bps, want);
+    // the carveout fitted to the blocks that run leaves the rest to L1
+    int bps = 1;
+    GR_TRY(fit_carveout(kern, kSsspThreads, want > 0 ? std::min(want, kSsspBlocksPerSm)
+                                                      : kSsspBlocksPerSm,
+                        g->device, &bps));
     void *args[] = {&a};
     GR_CUDA(cudaLaunchCooperativeKernel(kern, std::max(1, bps) * g->num_sms,
                                         kSsspThreads, args, 0, s));
