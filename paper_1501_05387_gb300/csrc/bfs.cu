@@ -862,9 +862,13 @@ constexpr int32_t kSegPushMaxDeg = 1024;
 __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a) {
   BfsCtl *c = a.ctl;
   __shared__ LevelSmem sm;
+  // a traversal the one-cluster driver finished, or one it hands over at
+  // level c->level with the frontier in queue c->parity
+  if (*(volatile int32_t *)&c->done) return;
   const int32_t policy = c->policy, max_levels = c->max_levels;
   const float alpha = c->alpha, beta = c->beta;
-  int32_t level = 0, parity = 0, dir = kPush, q = 1, q_prev = 0, from_bitmap = 0;
+  int32_t level = c->level, parity = c->parity, dir = kPush, q = c->q_len, q_prev = 0,
+          from_bitmap = 0;
   long long mf = c->mf, mu = c->mu;
   int32_t gen = 0, pulls = 0;
   int32_t seg_maxdeg = 0;  // largest degree the last pull level found
@@ -937,6 +941,277 @@ __global__ void __launch_bounds__(kLvThreads, kDoBlocksPerSm) k_bfs_do(BfsArgs a
       break;
     }
     dir = next_direction(policy, was_pull, qn, q_prev, mfn, mu, a.m, a.n, alpha, beta);
+  }
+}
+
+// ------------------------------------------------------ one-cluster driver
+// On graphs of small maximum degree (meshes) a BFS has thousands of levels
+// of a few thousand vertices each, and a grid-wide barrier per level costs
+// more than the level's work. This driver runs those levels in ONE thread
+// block cluster: the CTAs meet at the hardware cluster barrier, and each
+// level's new frontier stays in the CTAs' shared memory, where the next level
+// reads it through distributed shared memory. Each CTA appends the vertices
+// its threads claimed, with their row bounds (so the next level needs no
+// row-offset load), to its own buffer (one per level parity); what does not
+// fit goes to the global queue of that parity, positioned by the level's
+// global counter, so the frontier of a level is the CTAs' buffers followed by
+// that queue's first entries. At the end of a level each CTA writes its
+// counts into every CTA's shared memory before the barrier, so no level
+// starts with a remote load. Once a frontier outgrows kClHandoff vertices,
+// the cluster writes it to the global queue as a plain list and leaves the
+// rest of the traversal to k_bfs_do (same stream), which resumes at that
+// level.
+constexpr int kClThreads = 1024;
+constexpr int kClMaxCtas = 16;
+constexpr int kClCap = 1024;        // buffered vertices per CTA and parity
+constexpr int kClHandoff = 32768;   // larger frontiers go to the grid kernel
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// address of `p` (this CTA's shared memory) in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cl_map(const void *p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ int4 cl_ld_v4(uint32_t addr) {
+  int4 v;
+  asm volatile("ld.shared::cluster.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void cl_st_s32(uint32_t addr, int32_t v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_st_u64(uint32_t addr, unsigned long long v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void cl_fence() {
+  asm volatile("fence.acq_rel.cluster;" ::: "memory");
+}
+// every thread of every CTA of the cluster; a relaxed arrival (the threads
+// whose writes others must see fence first), an acquiring wait
+__device__ __forceinline__ void cl_sync_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+struct ClSmem {
+  // this CTA's part of the frontier by level parity: (vertex, row start,
+  // row end, 0), so the next level reads a vertex and its row in one load
+  int4 buf[2][kClCap];
+  int32_t cnt[2];                  // vertices appended (past kClCap: global queue)
+  unsigned long long edges[2];     // their degrees' sum
+  // every CTA's cnt / edges for each parity, pushed here by that CTA
+  int32_t rc[2][kClMaxCtas];
+  unsigned long long re[2][kClMaxCtas];
+};
+
+__global__ void __launch_bounds__(kClThreads, 1) k_bfs_cluster(BfsArgs a) {
+  BfsCtl *c = a.ctl;
+  __shared__ ClSmem sm;
+  const uint32_t rank = cl_rank(), ncta = cl_size();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t max_levels = c->max_levels;
+  int32_t *depth = c->depth;
+  int32_t *parent = c->parent;
+  const int32_t q0 = c->q_len;  // level 0: the source, in global queue 0
+  const long long mf0 = c->mf;
+  if (threadIdx.x < 2 * kClMaxCtas) {
+    (&sm.rc[0][0])[threadIdx.x] = 0;
+    (&sm.re[0][0])[threadIdx.x] = 0ull;
+  }
+  if (threadIdx.x == 0) {
+    sm.cnt[0] = sm.cnt[1] = 0;
+    sm.edges[0] = sm.edges[1] = 0ull;
+  }
+  cl_sync();
+  // items are dealt to the CTAs 32 at a time, so a small frontier still
+  // spreads over every SM of the cluster
+  const int64_t first = (int64_t)warp * (32 * ncta) + rank * 32 + lane;
+  const int64_t stride = (int64_t)ncta * kClThreads;
+  int32_t q_last = 0;
+  long long mf_last = 0;
+  for (int32_t L = 0;; ++L) {
+    const int p = L & 1;
+    int32_t nb = 0, ovf = L == 0 ? q0 : 0;
+    long long mf = L == 0 ? mf0 : 0;
+    for (uint32_t r = 0; r < ncta; ++r) {
+      const int32_t cr = sm.rc[p][r];
+      nb += min(cr, kClCap);
+      ovf += max(cr - kClCap, 0);
+      mf += (long long)sm.re[p][r];
+    }
+    const int32_t q = nb + ovf;
+    if (threadIdx.x == 0) {
+      // the counters this level fills were pushed to every CTA in level L - 1
+      sm.cnt[p ^ 1] = 0;
+      sm.edges[p ^ 1] = 0ull;
+      if (rank == 0) {
+        if (L >= 1 && L - 1 < kTraceLevels) {
+          c->tr_dir[L - 1] = kPush;
+          c->tr_q[L - 1] = q_last;
+          c->tr_mf[L - 1] = mf_last;
+          c->tr_t[L - 1] = globaltimer();
+        }
+        c->cnt3[(L + 1) % 3] = 0ull;  // the global counter of level L + 1
+      }
+    }
+    __syncthreads();
+    const bool done = q == 0;
+    const bool over = !done && L >= max_levels;
+    const bool handoff = !done && !over && q > kClHandoff;
+    if (done || over || handoff) {
+      if (handoff) {
+        // the frontier as one list: the global part stays, the CTAs' buffers
+        // follow it in rank order
+        int32_t *Q = queue_of(a, p);
+        int32_t at = ovf;
+        for (uint32_t r = 0; r < rank; ++r) at += min(sm.rc[p][r], kClCap);
+        const int32_t mine = min(sm.rc[p][rank], kClCap);
+        for (int32_t k = threadIdx.x; k < mine; k += kClThreads) Q[at + k] = sm.buf[p][k].x;
+      }
+      if (rank == 0 && threadIdx.x == 0) {
+        c->level = L;
+        if (handoff) {
+          c->parity = p;
+          c->q_len = q;
+          c->mf = mf;
+          c->cnt3[L % 3] = 0ull;
+        } else {
+          c->pull_levels = 0;
+          if (over) c->error = kDevOverflow;
+          c->done = 1;
+        }
+      }
+      cl_sync();
+      return;
+    }
+    const int32_t *Qg = queue_of(a, p);
+    int32_t *Qn = queue_of(a, p ^ 1);
+    unsigned long long *gctr = &c->cnt3[L % 3];
+    const int64_t qr = ((int64_t)q + 31) & ~31ll;  // warp-uniform bound
+    for (int64_t i = first; i < qr; i += stride) {
+      int32_t u = 0, r0 = 0, r1 = 0;
+      if (i < q) {
+        if (i < nb) {
+          int32_t s = 0;
+          uint32_t r = 0;
+          for (; r + 1 < ncta; ++r) {
+            const int32_t cr = min(sm.rc[p][r], kClCap);
+            if (i < s + cr) break;
+            s += cr;
+          }
+          const int4 e = cl_ld_v4(cl_map(&sm.buf[p][i - s], r));
+          u = e.x;
+          r0 = e.y;
+          r1 = e.z;
+        } else {
+          u = Qg[i - nb];
+          if (GR_IN(u, a.n, 190)) {
+            r0 = a.R[u];
+            r1 = a.R[u + 1];
+          }
+        }
+      }
+      for (int32_t e0 = r0; __any_sync(0xffffffffu, e0 < r1); e0 += kTpvItems) {
+        int32_t v[kTpvItems], d0[kTpvItems], d1[kTpvItems];
+        uint32_t vw[kTpvItems];
+        bool won[kTpvItems];
+#pragma unroll
+        for (int j = 0; j < kTpvItems; ++j) {
+          v[j] = (e0 + j < r1 && GR_IN(e0 + j, a.m, 191)) ? a.C[e0 + j] : -1;
+          if (v[j] >= 0 && !GR_IN(v[j], a.n, 192)) v[j] = -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kTpvItems; ++j) {
+          vw[j] = 0xFFFFFFFFu;
+          d0[j] = d1[j] = 0;
+          if (v[j] >= 0) {
+            vw[j] = a.visited[v[j] >> 5];
+            d0[j] = a.R[v[j]];
+            d1[j] = a.R[v[j] + 1];
+          }
+        }
+        int32_t cnt = 0, deg = 0;
+#pragma unroll
+        for (int j = 0; j < kTpvItems; ++j) {
+          won[j] = false;
+          if (v[j] >= 0) {
+            const uint32_t mask = 1u << (v[j] & 31);
+            if (!(vw[j] & mask)) won[j] = !(atomicOr(a.visited + (v[j] >> 5), mask) & mask);
+          }
+          if (won[j]) {
+            depth[v[j]] = L + 1;
+            if (parent) parent[v[j]] = u;
+            cnt += 1;
+            deg += d1[j] - d0[j];
+          }
+        }
+        // warp-level exclusive scan of the claims, one shared-memory atomic
+        int32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+          const int32_t dsum = __reduce_add_sync(0xffffffffu, deg);
+          int32_t base = 0;
+          if (lane == 0) {
+            base = atomicAdd(&sm.cnt[p ^ 1], total);
+            atomicAdd(&sm.edges[p ^ 1], (unsigned long long)dsum);
+          }
+          base = __shfl_sync(0xffffffffu, base, 0);
+          // positions past the buffer go to the global queue, in the order
+          // of the level's global counter
+          const int32_t kfirst = max(base, kClCap);
+          const int32_t ng = max(0, base + total - kfirst);
+          unsigned long long g0 = 0ull;
+          if (lane == 0 && ng) g0 = atomicAdd(gctr, (unsigned long long)ng);
+          g0 = __shfl_sync(0xffffffffu, g0, 0);
+          int32_t k = base + (incl - cnt);
+#pragma unroll
+          for (int j = 0; j < kTpvItems; ++j)
+            if (won[j]) {
+              if (k < kClCap) {
+                sm.buf[p ^ 1][k] = make_int4(v[j], d0[j], d1[j], 0);
+              } else {
+                const long long gk = (long long)g0 + (k - kfirst);
+                if (GR_IN(gk, a.n + 1, 193)) Qn[gk] = v[j];
+              }
+              ++k;
+            }
+        }
+      }
+    }
+    q_last = q;
+    mf_last = mf;
+    // publish this CTA's counts in every CTA, then meet: the fences of the
+    // publishing threads (after the block barrier) order the CTA's appends
+    __syncthreads();
+    if (threadIdx.x < ncta) {
+      cl_st_s32(cl_map(&sm.rc[p ^ 1][rank], threadIdx.x), sm.cnt[p ^ 1]);
+      cl_st_u64(cl_map(&sm.re[p ^ 1][rank], threadIdx.x), sm.edges[p ^ 1]);
+      cl_fence();
+    }
+    cl_sync_relaxed();
   }
 }
 
@@ -1134,6 +1409,36 @@ static gr_status build_level_graph(gr_graph *g, BfsWorkspace *ws, int32_t do_bit
   return GR_OK;
 }
 
+// The one-cluster driver with the largest cluster the device co-schedules
+// (16 CTAs, else 8); when none fits nothing is launched and k_bfs_do runs
+// the whole traversal.
+static gr_status launch_cluster_bfs(const BfsArgs &a, cudaStream_t s) {
+  GR_CUDA(cudaFuncSetAttribute(k_bfs_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  for (int ctas : {kClMaxCtas, 8}) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_bfs_cluster, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (clusters < 1) continue;
+    GR_CUDA(cudaLaunchKernelEx(&cfg, k_bfs_cluster, a));
+    return GR_OK;
+  }
+  return GR_OK;
+}
+
 static int32_t resolve_policy(const gr_graph *g, const gr_opts &o) {
   if (o.direction == GR_DIR_PUSH) return GR_DIR_PUSH;
   if (o.direction == GR_DIR_PULL) return GR_DIR_PULL;
@@ -1198,6 +1503,8 @@ gr_status bfs_run(gr_graph *g, BfsWorkspace *ws, int32_t src, int32_t *depth, in
     a.seg_v = ws->seg_v.as<int32_t>();
     a.seg_d = ws->seg_d.as<int32_t>();
     a.seg_cnt = ws->seg_cnt.as<unsigned long long>();
+    // low-degree graphs: the small-frontier levels in one cluster first
+    if (a.low_degree) GR_TRY(launch_cluster_bfs(a, s));
     void *args[] = {&a};
     GR_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs_do, blocks, kLvThreads, args, 0, s));
   } else {

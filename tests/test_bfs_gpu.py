@@ -298,3 +298,61 @@ def test_trace_frontier_sizes_match_oracle_levels(cuda_lib, s14, direction, mode
         assert all(d == 1 for d, _, _, _ in tr[1:])
     times = [t for _, _, _, t in tr]
     assert all(b >= a for a, b in zip(times, times[1:]))
+
+
+def _kary_tree(k, depth):
+    # complete k-ary tree, vertices in level order: children of v are
+    # k*v + 1 .. k*v + k
+    n = sum(k ** i for i in range(depth + 1))
+    edges = [(v, k * v + j) for v in range(n) for j in range(1, k + 1) if k * v + j < n]
+    return gg.from_edges(n, edges)
+
+
+@pytest.mark.parametrize("src_kind", ["root", "leaf", "middle"])
+def test_low_degree_cluster_overflow_and_handoff(cuda_lib, src_kind):
+    # a 15-ary tree of depth 4 (max degree 16: the low-degree path): from the
+    # root the frontiers are 1, 15, 225, 3375, 50625, so a level's claims
+    # overflow the per-CTA buffers of the one-cluster driver into the global
+    # queue, and the last frontier is handed to the grid kernel
+    r, c = _kary_tree(15, 4)
+    n = r.size - 1
+    src = {"root": 0, "leaf": n - 1, "middle": 1 + 15 + 7}[src_kind]
+    with cuda_lib.gr_graph_create(r, c) as g:
+        for mode in ["persistent", "auto", "graph"]:
+            check(cuda_lib, r, c, g, src, opts(cuda_lib, "auto", mode))
+        ref, _ = oracle.bfs(r, c, src)
+        run_bfs(cuda_lib, g, src, opts(cuda_lib, "auto", "persistent"))
+        assert cuda_lib.gr_bfs_stats(g)[0] == int(ref.max()) + 1
+        tr = cuda_lib.gr_bfs_trace(g)
+        assert [f for _, f, _, _ in tr] == list(np.bincount(ref[ref >= 0]))
+        deg = np.diff(r)
+        assert [e for _, _, e, _ in tr] == [int(deg[ref == l].sum()) for l in range(len(tr))]
+
+
+def test_low_degree_random_graph_grows_past_the_cluster(cuda_lib):
+    # two random permutations as edges: degree <= 4, frontiers grow ~3x per
+    # level until they leave the cluster driver
+    n = 300_000
+    rng = np.random.default_rng(11)
+    e = np.concatenate([np.stack([np.arange(n), rng.permutation(n)], 1) for _ in range(2)])
+    r, c = gg.from_edges(n, [tuple(x) for x in e.tolist()])
+    with cuda_lib.gr_graph_create(r, c) as g:
+        for src in [0, 123_457]:
+            check(cuda_lib, r, c, g, src, opts(cuda_lib, "auto", "persistent"))
+            ref, _ = oracle.bfs(r, c, src)
+            run_bfs(cuda_lib, g, src, opts(cuda_lib, "auto", "persistent"), with_parent=False)
+            tr = cuda_lib.gr_bfs_trace(g)
+            assert [f for _, f, _, _ in tr] == list(np.bincount(ref[ref >= 0]))[:len(tr)]
+
+
+@pytest.mark.parametrize("side", [64, 300])
+def test_mesh_trace_matches_oracle_levels(cuda_lib, side):
+    r, c = gg.grid(side, p_del=0.05, seed=4)
+    with cuda_lib.gr_graph_create(r, c) as g:
+        src = side * side // 2 + side // 3
+        ref, _ = oracle.bfs(r, c, src)
+        check(cuda_lib, r, c, g, src, opts(cuda_lib, "auto", "persistent"))
+        tr = cuda_lib.gr_bfs_trace(g)
+        hist = list(np.bincount(ref[ref >= 0]))
+        assert [f for _, f, _, _ in tr] == hist[:len(tr)]
+        assert cuda_lib.gr_bfs_stats(g)[0] == len(hist)
