@@ -1020,6 +1020,9 @@ struct ClSmem {
   // every CTA's cnt / edges for each parity, pushed here by that CTA
   int32_t rc[2][kClMaxCtas];
   unsigned long long re[2][kClMaxCtas];
+  int32_t pref[kClMaxCtas];  // the current frontier: CTA r's entries start at pref[r]
+  int32_t nb, ovf;           // buffered entries, entries in the global queue
+  long long mf;              // edges leaving the frontier
 };
 
 __global__ void __launch_bounds__(kClThreads, 1) k_bfs_cluster(BfsArgs a) {
@@ -1049,15 +1052,27 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bfs_cluster(BfsArgs a) {
   long long mf_last = 0;
   for (int32_t L = 0;; ++L) {
     const int p = L & 1;
-    int32_t nb = 0, ovf = L == 0 ? q0 : 0;
-    long long mf = L == 0 ? mf0 : 0;
-    for (uint32_t r = 0; r < ncta; ++r) {
-      const int32_t cr = sm.rc[p][r];
-      nb += min(cr, kClCap);
-      ovf += max(cr - kClCap, 0);
-      mf += (long long)sm.re[p][r];
+    if (warp == 0) {
+      // the frontier's shape from the counts every CTA pushed here
+      const int32_t cr = lane < (int)ncta ? sm.rc[p][lane] : 0;
+      unsigned long long er = lane < (int)ncta ? sm.re[p][lane] : 0ull;
+      const int32_t b = min(cr, kClCap);
+      int32_t o = max(cr - kClCap, 0), incl = b;
+#pragma unroll
+      for (int k = 1; k < 32; k <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, k);
+        if (lane >= k) incl += t;
+      }
+      o = __reduce_add_sync(0xffffffffu, o);
+#pragma unroll
+      for (int k = 16; k >= 1; k >>= 1) er += __shfl_xor_sync(0xffffffffu, er, k);
+      if (lane < kClMaxCtas) sm.pref[lane] = incl - b;
+      if (lane == 31) sm.nb = incl;
+      if (lane == 0) {
+        sm.ovf = o + (L == 0 ? q0 : 0);
+        sm.mf = (long long)er + (L == 0 ? mf0 : 0);
+      }
     }
-    const int32_t q = nb + ovf;
     if (threadIdx.x == 0) {
       // the counters this level fills were pushed to every CTA in level L - 1
       sm.cnt[p ^ 1] = 0;
@@ -1073,6 +1088,9 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bfs_cluster(BfsArgs a) {
       }
     }
     __syncthreads();
+    const int32_t nb = sm.nb, ovf = sm.ovf;
+    const int32_t q = nb + ovf;
+    const long long mf = sm.mf;
     const bool done = q == 0;
     const bool over = !done && L >= max_levels;
     const bool handoff = !done && !over && q > kClHandoff;
@@ -1081,8 +1099,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bfs_cluster(BfsArgs a) {
         // the frontier as one list: the global part stays, the CTAs' buffers
         // follow it in rank order
         int32_t *Q = queue_of(a, p);
-        int32_t at = ovf;
-        for (uint32_t r = 0; r < rank; ++r) at += min(sm.rc[p][r], kClCap);
+        const int32_t at = ovf + sm.pref[rank];
         const int32_t mine = min(sm.rc[p][rank], kClCap);
         for (int32_t k = threadIdx.x; k < mine; k += kClThreads) Q[at + k] = sm.buf[p][k].x;
       }
@@ -1110,14 +1127,11 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bfs_cluster(BfsArgs a) {
       int32_t u = 0, r0 = 0, r1 = 0;
       if (i < q) {
         if (i < nb) {
-          int32_t s = 0;
-          uint32_t r = 0;
-          for (; r + 1 < ncta; ++r) {
-            const int32_t cr = min(sm.rc[p][r], kClCap);
-            if (i < s + cr) break;
-            s += cr;
-          }
-          const int4 e = cl_ld_v4(cl_map(&sm.buf[p][i - s], r));
+          uint32_t r = 0;  // the last CTA whose entries start at or before i
+#pragma unroll
+          for (uint32_t k = kClMaxCtas / 2; k >= 1; k >>= 1)
+            if (r + k < ncta && sm.pref[r + k] <= i) r += k;
+          const int4 e = cl_ld_v4(cl_map(&sm.buf[p][i - sm.pref[r]], r));
           u = e.x;
           r0 = e.y;
           r1 = e.z;
