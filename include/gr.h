@@ -68,7 +68,11 @@ enum {
   GR_MODE_GRAPH = 2,      /* one CUDA graph whose device-side while loop
                              runs one level per iteration */
   GR_MODE_PERSISTENT = 3  /* one cooperative kernel runs every level with a
-                             bounded-spin grid barrier between levels */
+                             bounded-spin grid barrier between levels; for a
+                             BFS on a graph of maximum degree <= 16 one
+                             thread-block cluster runs the levels first and
+                             hands a frontier of more than 32768 vertices to
+                             that kernel */
 };
 
 /* Options; pass NULL for tuned defaults. Zero in a field means "tuned". */
