@@ -324,3 +324,48 @@ def test_batch_bad_arguments(cuda_lib, s14w):
         with pytest.raises(cuda_lib.GrError) as ei:
             cuda_lib.gr_sssp_batch(g2, [0], d)
         assert ei.value.status == cuda_lib.GR_EINVAL
+
+
+def _kary_tree(k, depth):
+    n = sum(k ** i for i in range(depth + 1))
+    edges = [(v, k * v + j) for v in range(n) for j in range(1, k + 1) if k * v + j < n]
+    return gg.from_edges(n, edges)
+
+
+@pytest.mark.parametrize("delta", [0xFFFFFFFF, 16, 1])
+def test_low_degree_tree(cuda_lib, delta):
+    # a 15-ary tree of depth 4 (max degree 16, the per-thread relaxation):
+    # near frontiers of 1, 15, 225, 3375 and 50625 vertices with one bucket
+    r, c = _kary_tree(15, 4)
+    w = gg.weights(r, c, seed=21, wmin=1, wmax=64)
+    n = r.size - 1
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for src in [0, n - 1]:
+            check(cuda_lib, r, c, w, g, src, opts(cuda_lib, delta, "persistent"))
+
+
+def test_low_degree_random_graph_large_far_pile(cuda_lib):
+    # a random graph of degree <= 4 with bucket width 1: a far pile of
+    # hundreds of thousands of vertices, split over and over
+    n = 400_000
+    rng = np.random.default_rng(12)
+    e = np.concatenate([np.stack([np.arange(n), rng.permutation(n)], 1) for _ in range(2)])
+    r, c = gg.from_edges(n, [tuple(x) for x in e.tolist()])
+    w = gg.weights(r, c, seed=22, wmin=1, wmax=64)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        for delta in [1, 0xFFFFFFFF]:
+            check(cuda_lib, r, c, w, g, 5, opts(cuda_lib, delta, "persistent"))
+
+
+@pytest.mark.parametrize("delta", [0, 16, 300])
+def test_mesh_persistent_equals_graph_driver(cuda_lib, delta):
+    side = 300
+    r, c = gg.grid(side, p_del=0.05, seed=4)
+    w = gg.weights(r, c, seed=23, wmin=1, wmax=16)
+    with cuda_lib.gr_graph_create(r, c, w) as g:
+        src = side * side // 2 + side // 3
+        check(cuda_lib, r, c, w, g, src, opts(cuda_lib, delta, "persistent"))
+        # the same search through the CUDA-graph driver gives the same answer
+        d_graph, _ = run_sssp(cuda_lib, g, src, opts(cuda_lib, delta, "graph"))
+        d_pers, _ = run_sssp(cuda_lib, g, src, opts(cuda_lib, delta, "persistent"))
+        assert np.array_equal(d_graph, d_pers)
