@@ -389,7 +389,9 @@ gr_status gr_tuned_sssp(const gr_graph *g, int32_t *mode, int32_t *blocks_per_sm
  * gr_server_add_graph for when); likewise an SSSP request takes further
  * queued SSSP requests for its graph as lanes of one gr_sssp_batch search
  * (up to max_batch and the graph's lane limit, which keeps that search's
- * scratch within 4 GiB). Results equal those of gr_bfs / gr_sssp / gr_cc
+ * scratch within 4 GiB). The queued CC requests of a graph (whose answers
+ * are all the same) share one gr_cc run and one result buffer, up to
+ * max_batch of them. Results equal those of gr_bfs / gr_sssp / gr_cc
  * alone. Traversals use each graph's tuned driver. With max_batch = 1 the
  * server is the plain path: one query per launch sequence, in arrival
  * order, on one stream. A request whose traversal stops at a device-side

@@ -173,11 +173,13 @@ struct SlotDev {
       if (!st.sssp) GR_TRY(sssp_ws_create(g, s, &st.sssp));
       GR_TRY(sssp_run(g, st.sssp, first.src, buf.as<uint32_t>(), nullptr, o, s));
     } else {
+      // the CC requests of a batch share one run
       if (!st.cc) GR_TRY(cc_ws_create(g, &st.cc));
       GR_TRY(cc_run(g, st.cc, buf.as<int32_t>(), s));
     }
+    const bool shared = first.kind == GR_QUERY_CC;
     for (size_t i = 0; i < rs.size(); ++i)
-      GR_TRY(copy_out(rs[i], buf.as<char>() + i * nbytes, nbytes, s));
+      GR_TRY(copy_out(rs[i], buf.as<char>() + (shared ? 0 : i * nbytes), nbytes, s));
     return GR_OK;
   }
 
@@ -241,7 +243,8 @@ void Server::worker() {
       sssp_lanes = adm.graphs[first.graph].sssp_lanes;
     }
     SlotDev dev{g, (*state)[first.graph], rs, sssp_lanes, s, *buf, broken};
-    const gr_status status = serve::run_batch(dev, sizeof(int32_t) * (size_t)g->n * rs.size());
+    const gr_status status = serve::run_batch(
+        dev, sizeof(int32_t) * (size_t)g->n * serve::Admission::result_units(first.kind, rs.size()));
     std::string err;
     if (status != GR_OK)
       err = std::string(gr_last_error()) + " [batch: kind " + std::to_string(first.kind) +
@@ -264,7 +267,7 @@ void Server::worker() {
           last_error = err;
         }
       }
-      adm.release(first.graph, rs.size());
+      adm.release(first.graph, first.kind, rs.size());
       const serve::WsKind w = serve::ws_kind(first.kind, rs.size() > 1);
       const SlotGraphState &st = (*state)[first.graph];
       const void *ws = w == serve::kWsBfs ? (const void *)st.bfs

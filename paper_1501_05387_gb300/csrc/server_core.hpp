@@ -62,11 +62,18 @@ struct Admission {
 
   size_t result_bytes(int32_t graph) const { return sizeof(int32_t) * (size_t)graphs[graph].n; }
 
+  // result buffers a batch of `lanes` requests of `kind` holds: one per
+  // request, except that the CC requests of a batch (all of one graph) share
+  // one run and its one result
+  static size_t result_units(int32_t kind, size_t lanes) {
+    return kind == GR_QUERY_CC ? 1 : lanes;
+  }
+
   // bytes a batch of `lanes` requests of `kind` on `graph` adds
   size_t cost(int32_t graph, int32_t kind, size_t lanes) const {
     const GraphInfo &gi = graphs[graph];
     const WsKind w = ws_kind(kind, lanes > 1);
-    return lanes * result_bytes(graph) + (gi.have_ws[w] ? 0 : gi.ws_bytes[w]);
+    return result_units(kind, lanes) * result_bytes(graph) + (gi.have_ws[w] ? 0 : gi.ws_bytes[w]);
   }
   bool fits(size_t add) const { return resident + in_use + add <= budget; }
 
@@ -83,7 +90,7 @@ struct Admission {
       return queued >= gi.min_batch ? max_batch : 1;
     }
     if (kind == GR_QUERY_SSSP) return std::min(max_batch, gi.sssp_lanes);
-    return 1;
+    return max_batch;  // CC: every queued request of the graph shares the run
   }
 
   // Next batch (tickets) for a free slot, or empty when the queue is empty
@@ -111,7 +118,7 @@ struct Admission {
       gi.have_ws[w] = true;
       resident += gi.ws_bytes[w];
     }
-    in_use += lanes * result_bytes(lead.graph);
+    in_use += result_units(lead.kind, lanes) * result_bytes(lead.graph);
     for (size_t k = pos.size(); k-- > 0;) {
       out.push_back(queue[pos[k]]);
       pending.erase(queue[pos[k]]);
@@ -129,8 +136,10 @@ struct Admission {
     resident -= gi.ws_bytes[w];
   }
 
-  // The batch of `lanes` requests on `graph` finished (or failed).
-  void release(int32_t graph, size_t lanes) { in_use -= lanes * result_bytes(graph); }
+  // The batch of `lanes` requests of `kind` on `graph` finished (or failed).
+  void release(int32_t graph, int32_t kind, size_t lanes) {
+    in_use -= result_units(kind, lanes) * result_bytes(graph);
+  }
 };
 
 // One batch on a slot. Dev provides:

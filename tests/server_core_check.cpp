@@ -133,16 +133,16 @@ static void admission() {
     CHECK((b == std::vector<uint64_t>{1, 4, 5}));
     CHECK(a.in_use == 3 * 4000);
     CHECK(a.resident == 100000);  // the batch workspace was accounted
-    a.release(0, b.size());
+    a.release(0, GR_QUERY_BFS, b.size());
     CHECK(a.in_use == 0);
     // graph 1 has one BFS request queued, below its batching depth
     b = a.take_batch();
     CHECK((b == std::vector<uint64_t>{2}));
     CHECK(a.resident == 100000 + 10000);
-    a.release(1, 1);
+    a.release(1, GR_QUERY_BFS, 1);
     b = a.take_batch();
     CHECK((b == std::vector<uint64_t>{3}));
-    a.release(0, 1);
+    a.release(0, GR_QUERY_SSSP, 1);
     CHECK(a.queue.empty() && a.pending.empty());
   }
   // batching depth: three queued BFS requests on graph 1 batch, SSSP lanes
@@ -154,10 +154,10 @@ static void admission() {
     for (uint64_t t = 4; t <= 10; ++t) submit(a, t, 0, GR_QUERY_SSSP);
     std::vector<uint64_t> b = a.take_batch();
     CHECK(b.size() == 3);
-    a.release(1, 3);
+    a.release(1, GR_QUERY_BFS, 3);
     b = a.take_batch();
     CHECK((b == std::vector<uint64_t>{4, 5, 6, 7}));
-    a.release(0, 4);
+    a.release(0, GR_QUERY_SSSP, 4);
   }
   // a budget too small for the batch workspace falls back to single
   // requests; the oldest request is admitted alone even when nothing fits
@@ -170,7 +170,7 @@ static void admission() {
     CHECK(a.resident == 10000);
     // while that request is in flight nothing else is admitted if it does
     // not fit: 10000 + 4000 in use + 4000 more still fits here
-    a.release(0, 1);
+    a.release(0, GR_QUERY_BFS, 1);
     Admission tiny = make(100, 64);
     tiny.graphs = {g0};
     submit(tiny, 1, 0, GR_QUERY_CC);
@@ -179,7 +179,7 @@ static void admission() {
     CHECK((b == std::vector<uint64_t>{1}));  // nothing in flight: admitted
     b = tiny.take_batch();
     CHECK(b.empty());  // the first is still in flight and the budget is spent
-    tiny.release(0, 1);
+    tiny.release(0, GR_QUERY_CC, 1);
     b = tiny.take_batch();
     CHECK((b == std::vector<uint64_t>{2}));
   }
@@ -191,8 +191,27 @@ static void admission() {
     std::vector<uint64_t> b = a.take_batch();
     CHECK(a.resident == 20000);
     a.ws_not_created(0, kWsSssp);
-    a.release(0, 1);
+    a.release(0, GR_QUERY_SSSP, 1);
     CHECK(a.resident == 0 && a.in_use == 0);
+  }
+  // the CC requests of a graph share one run: one batch, one result buffer
+  {
+    Admission a = make(1 << 20, 64);
+    a.graphs = {g0, g1};
+    submit(a, 1, 0, GR_QUERY_CC);
+    submit(a, 2, 1, GR_QUERY_CC);
+    submit(a, 3, 0, GR_QUERY_BFS);
+    submit(a, 4, 0, GR_QUERY_CC);
+    submit(a, 5, 0, GR_QUERY_CC);
+    std::vector<uint64_t> b = a.take_batch();
+    CHECK((b == std::vector<uint64_t>{1, 4, 5}));
+    CHECK(a.in_use == 4000);       // one result, however many requests
+    CHECK(a.resident == 5000);     // the CC workspace
+    a.release(0, GR_QUERY_CC, b.size());
+    CHECK(a.in_use == 0);
+    b = a.take_batch();
+    CHECK((b == std::vector<uint64_t>{2}));
+    a.release(1, GR_QUERY_CC, 1);
   }
   // max_batch = 1 (the plain path) never batches
   {
@@ -200,6 +219,10 @@ static void admission() {
     a.graphs = {g0};
     for (uint64_t t = 1; t <= 4; ++t) submit(a, t, 0, GR_QUERY_BFS);
     CHECK(a.take_batch().size() == 1);
+    Admission c = make(1 << 20, 1);
+    c.graphs = {g0};
+    for (uint64_t t = 1; t <= 3; ++t) submit(c, t, 0, GR_QUERY_CC);
+    CHECK(c.take_batch().size() == 1);
   }
 }
 

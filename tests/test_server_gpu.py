@@ -133,6 +133,30 @@ def test_sssp_batching(cuda_lib, pool, gi):
         assert np.array_equal(o, alone(gr, g, gr.GR_QUERY_SSSP, s))
 
 
+@pytest.mark.parametrize("gi", [0, 3])
+def test_cc_requests_share_one_run(cuda_lib, pool, gi):
+    """Queued CC requests of a graph share one run and its one result
+    buffer; every request gets the labels of CC run alone, on the host and
+    on the device."""
+    import torch
+    gr = cuda_lib
+    g = pool[gi][0]
+    outs = [np.full(g.n, -7, np.int32) for _ in range(12)]
+    outs += [torch.full((g.n,), -7, dtype=torch.int32, device="cuda") for _ in range(4)]
+    with gr.gr_server_create(1 << 30, 1, 64) as srv:
+        gid = gr.gr_server_add_graph(srv, g, 1)
+        for o in outs:
+            gr.gr_server_submit(srv, gid, gr.GR_QUERY_CC, 0, o)
+        gr.gr_server_drain(srv, 120000)
+        st = gr.gr_server_stats(srv)
+    assert st["completed"] == len(outs) and st["failed"] == 0
+    assert st["launches"] < len(outs) and st["mean_batch"] > 1.0
+    ref = alone(gr, g, gr.GR_QUERY_CC, 0)
+    for o in outs:
+        got = o.cpu().numpy() if isinstance(o, torch.Tensor) else o
+        assert np.array_equal(got, ref)
+
+
 def test_bad_requests(cuda_lib, pool):
     gr = cuda_lib
     g = pool[0][0]
