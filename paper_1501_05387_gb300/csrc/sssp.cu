@@ -109,6 +109,7 @@ struct SsspArgs {
   SsspCtl *ctl;
   int32_t low_degree;  // graph of small maximum degree: per-thread relaxation
   const int32_t *cb;   // chunk bounds of the pull relaxation's all-vertex merge path
+  int32_t *qcb;        // room for the chunk bounds of a dense near frontier (or null)
 };
 
 constexpr int kSsspThreads = 256, kSsspItems = 4;
@@ -118,6 +119,9 @@ constexpr int kSsspBlocksPerSm = 5;
 // thread (mesh-like graphs), and the neighbours a thread loads at once.
 constexpr int32_t kSsspLowDegreeMax = 16;
 constexpr int kSsspTpvItems = 4;
+// A persistent relaxation first finds every chunk's bounds in one pass once
+// its frontier has at least this many chunks per block.
+constexpr int kSsspBoundsChunksPerBlock = 4;
 // Most sources one batched run takes.
 constexpr int32_t kSsspMaxLanes = 64;
 
@@ -125,6 +129,7 @@ struct SsspWorkspace {
   int32_t lanes = 1;  // copies of the graph the buffers hold (batched form)
   DevMem nearq[2], nearS[2], farq[2], stamp, far_stamp, ctl;
   DevMem cb;  // chunk bounds of the pull relaxation (single search; fixed per graph)
+  DevMem qcb;  // chunk bounds of a dense near frontier (persistent driver)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   ~SsspWorkspace() {
@@ -239,7 +244,32 @@ struct SsspStep {
   uint32_t *fmin;                // min distance sent to the far pile
 };
 
-__device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, const SsspStep &st) {
+// The merge-path chunk bounds of a near frontier (q members, exclusive
+// degree scan S, entries S[q]), grid-stride: cb[c] = the members whose end
+// marker S[i + 1] + i lies before c * kSsspChunk, cb[nchunks] = q.
+__device__ void frontier_chunk_bounds(const int32_t *S, int32_t q, long long nchunks,
+                                      int32_t *cb) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c <= nchunks;
+       c += (long long)gridDim.x * blockDim.x) {
+    if (c == nchunks) {
+      cb[c] = q;
+      continue;
+    }
+    const long long d = c * kSsspChunk;
+    int32_t lo = 0, hi = q;  // first member whose end marker is not before d
+    while (lo < hi) {
+      const int32_t mid = (int32_t)(((long long)lo + hi) >> 1);
+      if ((long long)S[mid + 1] + mid < d) lo = mid + 1;
+      else hi = mid;
+    }
+    cb[c] = lo;
+  }
+}
+
+// qcb (may be null): the frontier's chunk bounds, computed for this
+// iteration by frontier_chunk_bounds, so a chunk needs no search.
+__device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, const SsspStep &st,
+                           const int32_t *qcb = nullptr) {
   const int32_t np = st.near_parity;
   const int32_t *Q = pick(a.nearq, np);
   const int32_t *S = pick(a.nearS, np);
@@ -254,7 +284,12 @@ __device__ void relax_body(const SsspArgs &a, uint32_t *dist, SsspSmem &sm, cons
     const long long d0 = chunk * kSsspChunk;
     const long long d1 = min(d0 + kSsspChunk, total);
     int32_t i0, i1;
-    block_chunk_bounds<kSsspThreads>(S, q, st.q_edges, d0, d1, kSsspChunk, sm.sred, &i0, &i1);
+    if (qcb) {
+      i0 = qcb[chunk];
+      i1 = qcb[chunk + 1];
+    } else {
+      block_chunk_bounds<kSsspThreads>(S, q, st.q_edges, d0, d1, kSsspChunk, sm.sred, &i0, &i1);
+    }
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     // per chunk vertex: its scan offset, its row start and its distance (read
@@ -832,9 +867,21 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
     if (mode != kSsspSplit) {
       st.far_dest = pick(a.farq, far_parity) + far_len;  // appended after the pile
       st.far_cap = (long long)a.nv + 1 - far_len;
-      if (!LOW && mode == kSsspPull) pull_relax_body(a, dist, sm, st);
-      else if (LOW) relax_body_thread(a, dist, st);
-      else relax_body(a, dist, sm, st);
+      if (!LOW && mode == kSsspPull) {
+        pull_relax_body(a, dist, sm, st);
+      } else if (LOW) {
+        relax_body_thread(a, dist, st);
+      } else {
+        // a dense frontier's chunk bounds in one grid-wide pass (every block
+        // then starts its chunks without a search)
+        const long long nchunks = ((long long)near_len + near_edges + kSsspChunk - 1) / kSsspChunk;
+        const bool bounds = a.qcb && nchunks >= (long long)kSsspBoundsChunksPerBlock * gridDim.x;
+        if (bounds) {
+          frontier_chunk_bounds(pick(a.nearS, near_parity), near_len, nchunks, a.qcb);
+          if (!grid_sync(&c->bar, &c->error, gen)) break;
+        }
+        relax_body(a, dist, sm, st, bounds ? a.qcb : nullptr);
+      }
     } else {
       st.far_dest = pick(a.farq, far_parity ^ 1);
       st.far_cap = (long long)a.nv + 1;
@@ -922,8 +969,12 @@ __global__ void k_sssp_pred_fin(int32_t *pred, int32_t n, int32_t src) {
 
 size_t sssp_ws_bytes(const gr_graph *g, int32_t lanes) {
   const size_t n = (size_t)g->n * (size_t)std::max(lanes, 1);
+  const size_t qcb = g->max_degree > kSsspLowDegreeMax
+                         ? sizeof(int32_t) * ((n + (size_t)std::max(lanes, 1) * (size_t)g->m) /
+                                                  kSsspChunk + 3)
+                         : 0;
   return 4 * sizeof(int32_t) * (n + 1) + 2 * sizeof(int32_t) * (n + 2) +
-         2 * sizeof(int32_t) * n + sizeof(SsspCtl);
+         2 * sizeof(int32_t) * n + sizeof(SsspCtl) + qcb;
 }
 
 int32_t sssp_batch_max_lanes(const gr_graph *g) {
@@ -949,6 +1000,11 @@ gr_status sssp_ws_create(gr_graph *g, cudaStream_t s, SsspWorkspace **out, int32
   GR_TRY(ws->stamp.alloc(sizeof(int32_t) * n, "SSSP near stamps"));
   GR_TRY(ws->far_stamp.alloc(sizeof(int32_t) * n, "SSSP far stamps"));
   GR_TRY(ws->ctl.alloc(sizeof(SsspCtl), "SSSP control"));
+  if (g->max_degree > kSsspLowDegreeMax) {
+    // a frontier holds at most n vertices of each lane and their edges
+    const long long chunks = ((long long)n + (long long)lanes * g->m) / kSsspChunk + 2;
+    GR_TRY(ws->qcb.alloc(sizeof(int32_t) * ((size_t)chunks + 1), "SSSP frontier chunk bounds"));
+  }
   if (lanes == 1) {
     // the pull relaxation's merge path over all vertices never changes
     const int32_t chunks = merge_chunks(g->n, g->m, kSsspChunk);
@@ -981,6 +1037,7 @@ static SsspArgs sssp_args(gr_graph *g, SsspWorkspace *ws, int32_t lanes = 1) {
   a.ctl = ws->ctl.as<SsspCtl>();
   a.low_degree = g->max_degree <= kSsspLowDegreeMax ? 1 : 0;
   a.cb = ws->cb.as<int32_t>();  // null for batched workspaces, which never pull
+  a.qcb = ws->qcb.as<int32_t>();  // null on low-degree graphs
   return a;
 }
 
