@@ -245,10 +245,11 @@ struct SsspStep {
 };
 
 // The merge-path chunk bounds of a near frontier (q members, exclusive
-// degree scan S, entries S[q]), grid-stride: cb[c] = the members whose end
-// marker S[i + 1] + i lies before c * kSsspChunk, cb[nchunks] = q.
-__device__ void frontier_chunk_bounds(const int32_t *S, int32_t q, long long nchunks,
-                                      int32_t *cb) {
+// degree scan S[0..q), s_q entries in all: S[q] itself is not stored),
+// grid-stride: cb[c] = the members whose end marker S[i + 1] + i lies before
+// c * kSsspChunk, cb[nchunks] = q.
+__device__ void frontier_chunk_bounds(const int32_t *S, int32_t q, int32_t s_q,
+                                      long long nchunks, int32_t *cb) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c <= nchunks;
        c += (long long)gridDim.x * blockDim.x) {
     if (c == nchunks) {
@@ -259,7 +260,8 @@ __device__ void frontier_chunk_bounds(const int32_t *S, int32_t q, long long nch
     int32_t lo = 0, hi = q;  // first member whose end marker is not before d
     while (lo < hi) {
       const int32_t mid = (int32_t)(((long long)lo + hi) >> 1);
-      if ((long long)S[mid + 1] + mid < d) lo = mid + 1;
+      const int32_t sv = mid + 1 == q ? s_q : S[mid + 1];
+      if ((long long)sv + mid < d) lo = mid + 1;
       else hi = mid;
     }
     cb[c] = lo;
@@ -877,7 +879,8 @@ __global__ void __launch_bounds__(kSsspThreads, kSsspBlocksPerSm) k_sssp_do(Sssp
         const long long nchunks = ((long long)near_len + near_edges + kSsspChunk - 1) / kSsspChunk;
         const bool bounds = a.qcb && nchunks >= (long long)kSsspBoundsChunksPerBlock * gridDim.x;
         if (bounds) {
-          frontier_chunk_bounds(pick(a.nearS, near_parity), near_len, nchunks, a.qcb);
+          frontier_chunk_bounds(pick(a.nearS, near_parity), near_len, (int32_t)near_edges,
+                                nchunks, a.qcb);
           if (!grid_sync(&c->bar, &c->error, gen)) break;
         }
         relax_body(a, dist, sm, st, bounds ? a.qcb : nullptr);
