@@ -71,6 +71,7 @@ struct BatchWorkspace {
   DevMem visit, sigma, q, counter, lmp, ctl;
   DevMem cb_pull, cb_fwd;  // chunk bounds of the all-vertex pulls (fixed per graph)
   DevMem fq, fs;    // BC backward: one level's vertex list and degree scan
+  DevMem fcb;       // BC backward: that list's merge-path chunk bounds
   DevMem lq[3], ls[3];  // forward: level lists (ring by level) and degree scans
   std::vector<DevMem *> lm;  // level mask arrays ("slots")
   int32_t uploaded = 0;      // slots whose pointers are in lmp
@@ -857,6 +858,33 @@ __device__ __forceinline__ DS shfl_xor_ds(DS a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
+// Chunk bounds of a level list's merge path, the list's size and edge count
+// read from *fpacked (its scan S[0..q) does not store S[q]): cb[c] = the
+// members whose end marker S[i + 1] + i lies before c * kMbChunk,
+// cb[nchunks] = q. One thread per chunk; threads past the list's chunks
+// return.
+__global__ void k_list_bounds(const int32_t *S, const unsigned long long *fpacked, int32_t *cb) {
+  const unsigned long long fp = *fpacked;
+  const int32_t q = (int32_t)(fp & 0xFFFFFFFFull);
+  const int32_t qe = (int32_t)(fp >> 32);
+  const long long nchunks = ((long long)q + qe + kMbChunk - 1) / kMbChunk;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c > nchunks) return;
+  if (c == nchunks) {
+    cb[c] = q;
+    return;
+  }
+  const long long d = c * kMbChunk;
+  int32_t lo = 0, hi = q;  // first member whose end marker is not before d
+  while (lo < hi) {
+    const int32_t mid = (int32_t)(((long long)lo + hi) >> 1);
+    const int32_t sv = mid + 1 == q ? qe : S[mid + 1];
+    if ((long long)sv + mid < d) lo = mid + 1;
+    else hi = mid;
+  }
+  cb[c] = lo;
+}
+
 // resident blocks per SM of the backward pass (its carveout is fitted to
 // them, the rest of the shared-memory array left to L1 for the children's rows)
 constexpr int kBcBackBlocksPerSm = 6;
@@ -869,7 +897,8 @@ constexpr int kBcBackBlocksPerSm = 6;
 
 __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const int32_t *Q,
                                                              const int32_t *S,
-                                                             const unsigned long long *fpacked) {
+                                                             const unsigned long long *fpacked,
+                                                             const int32_t *cb) {
   __shared__ int32_t s_off[kMbChunk + 1];
   __shared__ int32_t s_row[kMbChunk + 1];
   __shared__ int32_t s_v[kMbChunk + 1];
@@ -884,8 +913,7 @@ __global__ void __launch_bounds__(kMbThreads) k_bc_backward(BcBackArgs a, const 
   for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const long long d0 = chunk * kMbChunk;
     const long long d1 = min(d0 + kMbChunk, total);
-    int32_t i0, i1;
-    block_chunk_bounds<kMbThreads>(S, q, qe, d0, d1, kMbChunk, s_red8, &i0, &i1);
+    const int32_t i0 = cb[chunk], i1 = cb[chunk + 1];  // k_list_bounds
     const long long j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nv = (i0 <= q - 1) ? (min(i1, q - 1) - i0 + 1) : 0;
     for (int32_t k = threadIdx.x; k < nv; k += kMbThreads) {
@@ -1102,6 +1130,11 @@ gr_status batch_ws_create(gr_graph *g, BatchWorkspace **out) {
   return GR_OK;
 }
 
+// Most merge-path chunks a BC level list can have (n vertices, m edges).
+static long long bc_list_max_chunks(const gr_graph *g) {
+  return ((long long)g->n + g->m) / kMbChunk + 1;
+}
+
 static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_bc) {
   if (!*slot) GR_TRY(batch_ws_create(g, slot));
   BatchWorkspace *ws = *slot;
@@ -1112,6 +1145,8 @@ static gr_status ensure_batch_ws(gr_graph *g, BatchWorkspace **slot, bool need_b
   if (need_bc && !ws->fq.p) {
     GR_TRY(ws->fq.alloc(sizeof(int32_t) * ((size_t)g->n + 1), "BC level list"));
     GR_TRY(ws->fs.alloc(sizeof(int32_t) * ((size_t)g->n + 2), "BC level list scan"));
+    GR_TRY(ws->fcb.alloc(sizeof(int32_t) * (size_t)(bc_list_max_chunks(g) + 1),
+                         "BC level list chunk bounds"));
   }
   return GR_OK;
 }
@@ -1337,6 +1372,7 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
     ba.q = ws->q.as<double>();
     unsigned long long *fpacked = ws->counter.as<unsigned long long>() + 2;
     int32_t *fq = ws->fq.as<int32_t>(), *fs = ws->fs.as<int32_t>();
+    const int list_bound_blocks = (int)((bc_list_max_chunks(g) + 1 + 255) / 256);
     int back_per_sm = 1;
     GR_TRY(fit_carveout(k_bc_backward, kMbThreads, kBcBackBlocksPerSm, g->device, &back_per_sm));
     for (int32_t L = levels - 1; L >= 1; --L) {
@@ -1346,7 +1382,9 @@ gr_status gr_bc(gr_graph *g, const int32_t *srcs, int32_t k, double *bc, const g
       k_mb_list<<<grid, kMbThreads, 0, s>>>(ba.lv, ba.R, g->n, fq, fs, fpacked);
       if (L + 1 < levels) {
         ba.lw = ws->lm[L + 1]->as<unsigned long long>();
-        k_bc_backward<<<g->num_sms * back_per_sm, kMbThreads, 0, s>>>(ba, fq, fs, fpacked);
+        k_list_bounds<<<list_bound_blocks, 256, 0, s>>>(fs, fpacked, ws->fcb.as<int32_t>());
+        k_bc_backward<<<g->num_sms * back_per_sm, kMbThreads, 0, s>>>(ba, fq, fs, fpacked,
+                                                                       ws->fcb.as<int32_t>());
       }
       if (sk == kSigU64)
         k_bc_finalize<kSigU64><<<grid, 256, 0, s>>>(ba.lv, fq, fpacked, ws->sigma.p,
